@@ -1,0 +1,165 @@
+/*
+ * bh.h -- C ABI of libbh.so: group-shared Barnes-Hut tree force evaluation
+ * on one GB300 (sm_103a), after Iwasawa et al., "Implementation and
+ * performance of Barnes-Hut N-body algorithm on extreme-scale heterogeneous
+ * many-core architectures" (arXiv:1907.02289).
+ *
+ * The path (Sec. 4.2, steps 3a-3d and 4): Morton keys, radix sort, octree,
+ * node moments, groups, one tree walk per group that emits its interaction
+ * list, the force kernel that sums Eq. (1) over the list particles and the
+ * centre-of-mass (+ quadrupole) term over the list cells, and the leapfrog
+ * update, with lists reused for several steps (the persistent interaction
+ * list of Sec. 4.2) and an FP32 kernel on coordinates shifted to a group
+ * origin (Sec. 4.7).
+ *
+ * Conventions
+ *  - Every function returns an int status (BH_OK = 0 or a BH_E_* code) and
+ *    never aborts; bh_last_error() gives a message for the last failure.
+ *  - Particle arrays are CALLER-OWNED DEVICE memory, structure of arrays:
+ *    x,y,z,vx,vy,vz,m (double) and id (int64), each of length n, plus the
+ *    outputs ax,ay,az (double).  A list-constructing call permutes x..id in
+ *    place into key order; id keeps particle identity.
+ *  - Tree, list and scratch buffers are LIBRARY-OWNED device memory inside
+ *    the context; they are allocated with cudaMalloc and grown on demand.
+ *  - Work is issued on the CUDA stream given to bh_create.  Calls that must
+ *    size buffers (building trees and lists) synchronise that stream; force
+ *    and step calls do not, except where stated.  Device-side error words are
+ *    checked at the next synchronising call (or bh_sync).
+ *  - bh_get_* read-back functions copy into CALLER-OWNED HOST buffers sized
+ *    from bh_get_sizes, and synchronise the stream.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BH_OK 0
+#define BH_E_INVAL 1         /* bad parameter, size or non-finite position   */
+#define BH_E_NOMEM 2         /* device allocation failed                     */
+#define BH_E_CUDA 3          /* a CUDA call failed                           */
+#define BH_E_LIST_OVERFLOW 4 /* list or node buffer too small (needed size   */
+                             /* is reported by bh_get_sizes)                 */
+#define BH_E_TIMEOUT 5       /* a bounded device wait gave up                */
+#define BH_E_STATE 6         /* call out of order (e.g. forces before lists) */
+
+#define BH_PREC_FP64 0 /* plain FP64 force kernel                              */
+#define BH_PREC_FP32 1 /* FP32 kernel, coordinates relative to a group origin */
+
+/* bh_compute_forces flags */
+#define BH_FORCE_TREE_ONLY 1 /* do not add the central-mass term */
+
+typedef struct bh_ctx bh_ctx;
+
+/* Method parameters (paper symbols where it has them).
+ *  theta      opening angle (>= 0); the paper names no criterion, this
+ *             library opens a node when side > theta * box gap (integer
+ *             boxes on the key grid, conservative), or when the gap is
+ *             within r_coll.
+ *  eps        Plummer softening added to gravity (0 for rings).
+ *  G          gravitational constant (1 in the paper).
+ *  M_central  central mass at the origin (the planet, Table 1); 0 = none.
+ *  r_coll, kappa, eta   contact distance and spring/dashpot constants of
+ *             Eq. (1) (the paper fixes only restitution 0.5).
+ *  dt         leapfrog step.
+ *  n_g        largest group (groups are the maximal tree nodes holding at
+ *             most n_g particles, Sec. 4.2).
+ *  n_leaf     largest leaf (1 <= n_leaf <= n_g).
+ *  order      1 = centre of mass only (Sec. 5.1), 2 = plus quadrupole.
+ *  precision  BH_PREC_FP64 or BH_PREC_FP32 (Sec. 4.7).
+ *  rebuild_every  force evaluation k rebuilds keys..lists iff
+ *             k % rebuild_every == 0, otherwise refreshes moments only.
+ *  key_frame  0 = Cartesian (the only value accepted).
+ *  list_capacity  reserved, 0. */
+typedef struct {
+    double theta, eps, G, M_central, r_coll, kappa, eta, dt;
+    int n_g, n_leaf, order, precision;
+    int rebuild_every, key_frame;
+    int64_t list_capacity;
+} bh_params;
+
+/* Caller-owned device arrays (see Conventions). */
+typedef struct {
+    double *x, *y, *z, *vx, *vy, *vz, *m;
+    int64_t* id;
+    double *ax, *ay, *az;
+    int64_t n;
+} bh_particles;
+
+/* Interaction and timing counters of the last force evaluation. */
+typedef struct {
+    int64_t n_groups;
+    int64_t n_pp; /* particle-particle interactions (i, list particle) incl. i = j */
+    int64_t n_pc; /* particle-cell interactions                                   */
+    int64_t n_evals;    /* force evaluations since the last list build            */
+    int64_t n_rebuilds; /* list-constructing evaluations so far                   */
+} bh_counters;
+
+/* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: BH_E_INVAL for theta < 0, n_g < 1, n_leaf < 1, n_leaf > n_g,
+ * order not 1/2, precision not 0/1, rebuild_every < 1, key_frame != 0,
+ * dt < 0. */
+int bh_create(const bh_params* p, void* stream, bh_ctx** out);
+int bh_destroy(bh_ctx* ctx);
+const char* bh_last_error(const bh_ctx* ctx);
+int bh_set_stream(bh_ctx* ctx, void* stream);
+
+/* Sec. 4.2 step 3a (list-constructing step): root box and Morton keys,
+ * stable radix sort, in-place permutation of the particle arrays into key
+ * order, level-by-level octree (BFS numbering), integer node boxes, node
+ * moments and groups.  Synchronises.  Errors: BH_E_INVAL for n < 1 or
+ * n >= 2^31 or a non-finite coordinate. */
+int bh_build_tree(bh_ctx* ctx, bh_particles* p);
+
+/* Sec. 4.2 step 3d, first half: one depth-first walk per group builds its
+ * particle list (opened leaves) and cell list (accepted nodes), both in
+ * order of first particle, and the list-reuse schedule starts.
+ * Synchronises.  BH_E_STATE without a tree. */
+int bh_make_lists(bh_ctx* ctx);
+
+/* Sec. 4.2 step 3d, second half (and the list-reusing step): refresh node
+ * moments from the current positions (same tree, groups and lists), then
+ * the force kernel writes ax,ay,az = sum over list particles of Eq. (1)
+ * + sum over list cells of the multipole term, plus the central-mass term
+ * unless flags has BH_FORCE_TREE_ONLY.  Particles must be in the order of
+ * the last bh_build_tree.  Asynchronous.  BH_E_STATE without lists. */
+int bh_compute_forces(bh_ctx* ctx, bh_particles* p, int flags);
+
+/* Sec. 4.2 step 4 with list reuse: nsteps kick-drift-kick leapfrog steps.
+ * Force evaluation k (counted over the context's life, k = 0 the first)
+ * rebuilds tree and lists iff k % rebuild_every == 0, otherwise reuses them.
+ * The first call evaluates the initial acceleration.  On return the arrays
+ * hold positions/velocities at the full step and ax..az the total
+ * acceleration there.  Synchronises on list-constructing steps. */
+int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps);
+
+/* Same as bh_step with HOST particle arrays: each call copies the arrays to
+ * library-owned device buffers, steps, and copies x..id and ax..az back.
+ * Synchronises. */
+int bh_step_host(bh_ctx* ctx, bh_particles* host, int nsteps);
+
+/* Wait for the stream and report device-side errors. */
+int bh_sync(bh_ctx* ctx);
+
+/* Sizes of the current structures (any pointer may be NULL). */
+int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp_entries,
+                 int64_t* n_pc_entries, int64_t* n_list_particles);
+
+/* Read-backs into host buffers (n, n_nodes, n_groups, ... entries). */
+int bh_get_keys(bh_ctx* ctx, uint64_t* keys, uint32_t* perm);
+int bh_get_root(bh_ctx* ctx, double* lo3, double* L);
+int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,
+                int32_t* first_child, uint8_t* nchild, uint32_t* qlo3, uint32_t* qhi3);
+int bh_get_moments(bh_ctx* ctx, double* M, double* c3, double* Q6);
+int bh_get_groups(bh_ctx* ctx, int32_t* group_nodes);
+int bh_get_lists(bh_ctx* ctx, int64_t* pp_off, int32_t* pp_ids, int64_t* pc_off, int32_t* pc_ids);
+int bh_get_counters(bh_ctx* ctx, bh_counters* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BH_H */

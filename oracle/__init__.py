@@ -114,6 +114,13 @@ def key_coords(k):
 
 
 def sort_perm(k):
+    """Stable sort by key (ties keep input order).  numpy's stable argsort is
+    used as the library primitive; orc_sort (qsort on (key, index)) is the
+    plain-C statement of the same definition and is pinned equal to it."""
+    return np.argsort(k, kind="stable").astype(np.uint32)
+
+
+def sort_perm_c(k):
     perm = np.empty(len(k), dtype=np.uint32)
     lib().orc_sort(_i64(len(k)), _p(k), _p(perm))
     return perm

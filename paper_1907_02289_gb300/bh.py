@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libbh.so (the C ABI in include/bh.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+torch is used for device memory (particle tensors) and for the current
+stream.  There is no CPU fallback: ``load()`` raises when the library is
+missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbh.so")
+
+BH_OK, BH_E_INVAL, BH_E_NOMEM, BH_E_CUDA, BH_E_LIST_OVERFLOW, BH_E_TIMEOUT, BH_E_STATE = range(7)
+BH_PREC_FP64, BH_PREC_FP32 = 0, 1
+BH_FORCE_TREE_ONLY = 1
+SYMBOLS = ("bh_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
+           "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
+           "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
+           "bh_get_counters")
+
+
+class bh_params(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("eps", ctypes.c_double), ("G", ctypes.c_double),
+                ("M_central", ctypes.c_double), ("r_coll", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("eta", ctypes.c_double), ("dt", ctypes.c_double), ("n_g", ctypes.c_int),
+                ("n_leaf", ctypes.c_int), ("order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rebuild_every", ctypes.c_int), ("key_frame", ctypes.c_int),
+                ("list_capacity", ctypes.c_int64)]
+
+
+class bh_particles(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("x", "y", "z", "vx", "vy", "vz", "m", "id", "ax", "ay", "az")] + [
+        ("n", ctypes.c_int64)]
+
+
+class bh_counters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds")]
+
+
+_lib = None
+
+
+class BHError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libbh error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load libbh.so (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: the CUDA library must be built (no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    vp = ctypes.POINTER(ctypes.c_void_p)
+    lib.bh_create.argtypes = [ctypes.POINTER(bh_params), P, vp]
+    lib.bh_destroy.argtypes = [P]
+    lib.bh_last_error.argtypes = [P]
+    lib.bh_last_error.restype = ctypes.c_char_p
+    lib.bh_set_stream.argtypes = [P, P]
+    lib.bh_build_tree.argtypes = [P, ctypes.POINTER(bh_particles)]
+    lib.bh_make_lists.argtypes = [P]
+    lib.bh_compute_forces.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.c_int]
+    lib.bh_step.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.c_int]
+    lib.bh_step_host.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.c_int]
+    lib.bh_sync.argtypes = [P]
+    lib.bh_get_sizes.argtypes = [P] + [ctypes.POINTER(ctypes.c_int64)] * 5
+    lib.bh_get_keys.argtypes = [P, P, P]
+    lib.bh_get_root.argtypes = [P, P, P]
+    lib.bh_get_tree.argtypes = [P] + [P] * 8
+    lib.bh_get_moments.argtypes = [P, P, P, P]
+    lib.bh_get_groups.argtypes = [P, P]
+    lib.bh_get_lists.argtypes = [P, P, P, P, P]
+    lib.bh_get_counters.argtypes = [P, ctypes.POINTER(bh_counters)]
+    _lib = lib
+    return lib
+
+
+def _np(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(**kw) -> bh_params:
+    p = bh_params()
+    defaults = dict(theta=0.5, eps=0.0, G=1.0, M_central=0.0, r_coll=0.0, kappa=0.0, eta=0.0, dt=1e-3, n_g=64,
+                    n_leaf=8, order=1, precision=BH_PREC_FP64, rebuild_every=4, key_frame=0, list_capacity=0)
+    for k, v in {**defaults, **{k: v for k, v in kw.items() if k in defaults}}.items():
+        setattr(p, k, v)
+    return p
+
+
+class Particles:
+    """Caller-owned device arrays (torch tensors) in the layout bh.h expects."""
+    FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "id", "ax", "ay", "az")
+
+    def __init__(self, arrays: dict, device="cuda"):
+        import torch
+        n = len(arrays["x"])
+        self.n = n
+        self.t = {}
+        for f in self.FIELDS:
+            dt = torch.int64 if f == "id" else torch.float64
+            if f in arrays:
+                self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f])).to(device=device, dtype=dt).contiguous()
+            else:
+                self.t[f] = torch.zeros(n, dtype=dt, device=device)
+        self.struct = bh_particles(*(self.t[f].data_ptr() for f in self.FIELDS), n)
+
+    def numpy(self) -> dict:
+        return {f: self.t[f].cpu().numpy() for f in self.FIELDS}
+
+
+class HostParticles:
+    """Caller-owned HOST arrays (numpy, optionally page-locked) for bh_step_host."""
+
+    def __init__(self, arrays: dict):
+        n = len(arrays["x"])
+        self.n = n
+        self.a = {}
+        for f in Particles.FIELDS:
+            dt = np.int64 if f == "id" else np.float64
+            self.a[f] = np.ascontiguousarray(arrays[f], dtype=dt).copy() if f in arrays else np.zeros(n, dt)
+        self.struct = bh_particles(*(self.a[f].ctypes.data for f in Particles.FIELDS), n)
+
+
+class Context:
+    """Owns one bh_ctx; methods mirror the C entry points of the same names."""
+
+    def __init__(self, stream=None, **params):
+        import torch
+        self.lib = load()
+        self.params = make_params(**params)
+        h = ctypes.c_void_p()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        rc = self.lib.bh_create(ctypes.byref(self.params), ctypes.c_void_p(stream), ctypes.byref(h))
+        if rc != BH_OK:
+            raise BHError(rc, "bh_create failed (see stderr)")
+        self.h = h
+
+    def _chk(self, rc):
+        if rc != BH_OK:
+            raise BHError(rc, self.lib.bh_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- entry points ----
+    def bh_build_tree(self, P: Particles):
+        return self._chk(self.lib.bh_build_tree(self.h, ctypes.byref(P.struct)))
+
+    def bh_make_lists(self):
+        return self._chk(self.lib.bh_make_lists(self.h))
+
+    def bh_compute_forces(self, P: Particles, flags: int = 0):
+        return self._chk(self.lib.bh_compute_forces(self.h, ctypes.byref(P.struct), flags))
+
+    def bh_step(self, P: Particles, nsteps: int):
+        return self._chk(self.lib.bh_step(self.h, ctypes.byref(P.struct), nsteps))
+
+    def bh_step_host(self, H: HostParticles, nsteps: int):
+        return self._chk(self.lib.bh_step_host(self.h, ctypes.byref(H.struct), nsteps))
+
+    def bh_sync(self):
+        return self._chk(self.lib.bh_sync(self.h))
+
+    def bh_get_sizes(self):
+        v = [ctypes.c_int64() for _ in range(5)]
+        self._chk(self.lib.bh_get_sizes(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("n_nodes", "n_groups", "n_pp", "n_pc", "n_jj"), (x.value for x in v)))
+
+    def bh_get_keys(self, n):
+        k = np.empty(n, np.uint64)
+        p = np.empty(n, np.uint32)
+        self._chk(self.lib.bh_get_keys(self.h, _np(k), _np(p)))
+        return k, p
+
+    def bh_get_root(self):
+        lo = np.empty(3)
+        L = np.empty(1)
+        self._chk(self.lib.bh_get_root(self.h, _np(lo), _np(L)))
+        return lo, float(L[0])
+
+    def bh_get_tree(self):
+        nn = self.bh_get_sizes()["n_nodes"]
+        t = {"level": np.empty(nn, np.uint8), "begin": np.empty(nn, np.uint32), "end": np.empty(nn, np.uint32),
+             "parent": np.empty(nn, np.int32), "first_child": np.empty(nn, np.int32),
+             "nchild": np.empty(nn, np.uint8), "qlo": np.empty((nn, 3), np.uint32),
+             "qhi": np.empty((nn, 3), np.uint32)}
+        self._chk(self.lib.bh_get_tree(self.h, *[_np(t[f]) for f in ("level", "begin", "end", "parent",
+                                                                        "first_child", "nchild", "qlo", "qhi")]))
+        return t
+
+    def bh_get_moments(self):
+        nn = self.bh_get_sizes()["n_nodes"]
+        M = np.empty(nn)
+        c = np.empty((3, nn))
+        Q = np.empty((nn, 6))
+        self._chk(self.lib.bh_get_moments(self.h, _np(M), _np(c), _np(Q)))
+        return {"M": M, "cx": c[0], "cy": c[1], "cz": c[2], "Q": Q}
+
+    def bh_get_groups(self):
+        ng = self.bh_get_sizes()["n_groups"]
+        g = np.empty(max(ng, 1), np.int32)
+        self._chk(self.lib.bh_get_groups(self.h, _np(g)))
+        return g[:ng]
+
+    def bh_get_lists(self):
+        s = self.bh_get_sizes()
+        ng = s["n_groups"]
+        L = {"pp_off": np.empty(ng + 1, np.int64), "P": np.empty(max(s["n_pp"], 1), np.int32),
+             "pc_off": np.empty(ng + 1, np.int64), "C": np.empty(max(s["n_pc"], 1), np.int32)}
+        self._chk(self.lib.bh_get_lists(self.h, _np(L["pp_off"]), _np(L["P"]), _np(L["pc_off"]), _np(L["C"])))
+        L["P"] = L["P"][: s["n_pp"]]
+        L["C"] = L["C"][: s["n_pc"]]
+        return L
+
+    def bh_get_counters(self):
+        c = bh_counters()
+        self._chk(self.lib.bh_get_counters(self.h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in bh_counters._fields_}

@@ -1,0 +1,385 @@
+// bh_api.cu -- the C ABI of libbh.so (declared in include/bh.h): context
+// life cycle, the list-constructing / list-reusing schedule of Sec. 4.2,
+// the leapfrog driver and the read-back functions.
+#include <stdarg.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "bh_internal.cuh"
+
+namespace bh {
+
+int fail(Ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int grow_raw(Ctx* c, void** p, size_t* cap, size_t need, const char* what, bool keep) {
+    if (need <= *cap && *p) return BH_OK;
+    void* q = nullptr;
+    size_t bytes = need < 256 ? 256 : need;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, BH_E_NOMEM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what,
+                    cudaGetErrorString(e));
+    }
+    if (*p) {
+        if (keep && *cap) {
+            e = cudaMemcpyAsync(q, *p, *cap, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) return fail(c, BH_E_CUDA, "copy while growing %s: %s", what, cudaGetErrorString(e));
+        }
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(c, BH_E_CUDA, "sync while growing %s: %s", what, cudaGetErrorString(e));
+        cudaFree(*p);
+    }
+    *p = q;
+    *cap = bytes;
+    return BH_OK;
+}
+
+namespace {
+
+template <typename T>
+void release(DBuf<T>& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int check_params(Ctx* c, const bh_params* p) {
+    if (!p) return fail(c, BH_E_INVAL, "params is NULL");
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return fail(c, BH_E_INVAL, "theta must be >= 0");
+    if (p->n_g < 1) return fail(c, BH_E_INVAL, "n_g must be >= 1");
+    if (p->n_leaf < 1 || p->n_leaf > p->n_g) return fail(c, BH_E_INVAL, "need 1 <= n_leaf <= n_g");
+    if (p->order != 1 && p->order != 2) return fail(c, BH_E_INVAL, "order must be 1 or 2");
+    if (p->precision != BH_PREC_FP64 && p->precision != BH_PREC_FP32)
+        return fail(c, BH_E_INVAL, "precision must be BH_PREC_FP64 or BH_PREC_FP32");
+    if (p->rebuild_every < 1) return fail(c, BH_E_INVAL, "rebuild_every must be >= 1");
+    if (p->key_frame != 0) return fail(c, BH_E_INVAL, "only the Cartesian key frame (0) is available");
+    if (!(p->eps >= 0.0) || !(p->r_coll >= 0.0) || !(p->dt >= 0.0))
+        return fail(c, BH_E_INVAL, "eps, r_coll and dt must be >= 0");
+    return BH_OK;
+}
+
+int check_particles(Ctx* c, const bh_particles* p, bool need_v) {
+    if (!p) return fail(c, BH_E_INVAL, "particles is NULL");
+    if (p->n < 1 || p->n >= ((int64_t)1 << 31)) return fail(c, BH_E_INVAL, "need 1 <= n < 2^31 (n = %lld)", (long long)p->n);
+    if (!p->x || !p->y || !p->z || !p->m || !p->ax || !p->ay || !p->az)
+        return fail(c, BH_E_INVAL, "x, y, z, m, ax, ay, az must be set");
+    if (need_v && (!p->vx || !p->vy || !p->vz)) return fail(c, BH_E_INVAL, "vx, vy, vz must be set");
+    return BH_OK;
+}
+
+int read_status(Ctx* c) {
+    int st = 0;
+    BH_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st) BH_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    if (st & kStatNonFinite) return fail(c, BH_E_INVAL, "non-finite particle coordinate");
+    if (st & kStatListOverflow) return fail(c, BH_E_LIST_OVERFLOW, "list buffer overflow");
+    if (st & kStatTimeout) return fail(c, BH_E_TIMEOUT, "device wait timed out");
+    if (st & kStatBounds) return fail(c, BH_E_STATE, "internal index check failed (access skipped)");
+    return BH_OK;
+}
+
+int build_tree(Ctx* c, bh_particles* p) {
+    BH_TRY(check_particles(c, p, true));
+    c->n = p->n;
+    c->have_tree = c->have_lists = false;
+    BH_TRY(stage_keys(c, p));
+    BH_TRY(read_status(c));
+    double box[5];
+    BH_CUDA(c, cudaMemcpyAsync(box, c->d_box, sizeof(box), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->h_lo[0] = box[0];
+    c->h_lo[1] = box[1];
+    c->h_lo[2] = box[2];
+    c->h_L = box[3];
+    c->h_S = box[4];
+    BH_TRY(stage_sort(c));
+    BH_TRY(stage_permute(c, p));
+    BH_TRY(stage_octree(c));
+    BH_TRY(stage_boxes(c));
+    BH_TRY(stage_moments(c, p));
+    BH_TRY(stage_groups(c));
+    c->have_tree = true;
+    return BH_OK;
+}
+
+int make_lists(Ctx* c) {
+    if (!c->have_tree) return fail(c, BH_E_STATE, "bh_make_lists needs a tree (call bh_build_tree)");
+    BH_TRY(stage_lists(c));
+    c->have_lists = true;
+    c->evals_since_build = 0;
+    c->n_rebuilds++;
+    return BH_OK;
+}
+
+// One force evaluation of the stepping schedule: list-constructing when
+// k_eval % rebuild_every == 0, list-reusing otherwise.
+int evaluate(Ctx* c, bh_particles* p) {
+    if (c->k_eval % c->prm.rebuild_every == 0 || !c->have_lists) {
+        BH_TRY(build_tree(c, p));
+        BH_TRY(make_lists(c));
+    } else {
+        BH_TRY(stage_moments(c, p));
+    }
+    BH_TRY(stage_force(c, p, true));
+    c->k_eval++;
+    c->evals_since_build++;
+    return BH_OK;
+}
+
+}  // namespace
+}  // namespace bh
+
+using bh::Ctx;
+
+extern "C" {
+
+int bh_create(const bh_params* p, void* stream, bh_ctx** out) {
+    if (!out) return BH_E_INVAL;
+    *out = nullptr;
+    Ctx tmp;
+    int rc = bh::check_params(&tmp, p);
+    if (rc != BH_OK) {
+        fprintf(stderr, "bh_create: %s\n", tmp.err.c_str());
+        return rc;
+    }
+    Ctx* c = new Ctx();
+    c->prm = *p;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_box, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_small, 64 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "bh_create: CUDA error: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        bh_destroy((bh_ctx*)c);
+        return BH_E_CUDA;
+    }
+    *out = (bh_ctx*)c;
+    return BH_OK;
+}
+
+int bh_destroy(bh_ctx* ctx) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_status);
+    cudaFree(c->d_box);
+    cudaFree(c->d_small);
+    using bh::release;
+    for (int b = 0; b < 2; ++b) {
+        release(c->key[b]);
+        release(c->idx[b]);
+    }
+    release(c->sort_hist); release(c->digit_hist); release(c->pscratch); release(c->scan_tmp);
+    release(c->level); release(c->nchild); release(c->begin); release(c->end); release(c->parent);
+    release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->split_cnt);
+    release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
+    release(c->cz); release(c->Q); release(c->cell32); release(c->phi); release(c->plo); release(c->gmark);
+    release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
+    release(c->cnt_c); release(c->cnt_j); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
+    release(c->hbuf); release(c->hid);
+    delete c;
+    return BH_OK;
+}
+
+const char* bh_last_error(const bh_ctx* ctx) {
+    const Ctx* c = (const Ctx*)ctx;
+    return c ? c->err.c_str() : "no context";
+}
+
+int bh_set_stream(bh_ctx* ctx, void* stream) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    c->stream = (cudaStream_t)stream;
+    return BH_OK;
+}
+
+int bh_build_tree(bh_ctx* ctx, bh_particles* p) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    return bh::build_tree(c, p);
+}
+
+int bh_make_lists(bh_ctx* ctx) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    return bh::make_lists(c);
+}
+
+int bh_compute_forces(bh_ctx* ctx, bh_particles* p, int flags) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_lists) return bh::fail(c, BH_E_STATE, "bh_compute_forces needs lists (call bh_make_lists)");
+    BH_TRY(bh::check_particles(c, p, true));
+    if (p->n != c->n) return bh::fail(c, BH_E_INVAL, "particle count changed since the tree was built");
+    BH_TRY(bh::stage_moments(c, p));
+    BH_TRY(bh::stage_force(c, p, !(flags & BH_FORCE_TREE_ONLY)));
+    c->evals_since_build++;
+    return BH_OK;
+}
+
+int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (nsteps < 0) return bh::fail(c, BH_E_INVAL, "nsteps must be >= 0");
+    BH_TRY(bh::check_particles(c, p, true));
+    if (c->have_tree && p->n != c->n) return bh::fail(c, BH_E_INVAL, "particle count changed");
+    const double dt = c->prm.dt;
+    if (!c->have_acc) {
+        BH_TRY(bh::evaluate(c, p));
+        c->have_acc = true;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        BH_TRY(bh::stage_kick_drift(c, p, 0.5 * dt, dt));
+        BH_TRY(bh::evaluate(c, p));
+        BH_TRY(bh::stage_kick(c, p, 0.5 * dt));
+    }
+    return BH_OK;
+}
+
+int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    BH_TRY(bh::check_particles(c, h, true));
+    if (!h->id) return bh::fail(c, BH_E_INVAL, "id must be set");
+    const int64_t n = h->n;
+    BH_TRY(bh::grow(c, c->hbuf, (size_t)n * 10, "host-step particle buffers"));
+    BH_TRY(bh::grow(c, c->hid, (size_t)n, "host-step ids"));
+    double* b = c->hbuf.p;
+    bh_particles d;
+    d.x = b; d.y = b + n; d.z = b + 2 * n; d.vx = b + 3 * n; d.vy = b + 4 * n; d.vz = b + 5 * n;
+    d.m = b + 6 * n; d.ax = b + 7 * n; d.ay = b + 8 * n; d.az = b + 9 * n; d.id = c->hid.p; d.n = n;
+    double* hs[10] = {h->x, h->y, h->z, h->vx, h->vy, h->vz, h->m, h->ax, h->ay, h->az};
+    double* ds[10] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.ax, d.ay, d.az};
+    const int ncopy = c->have_acc ? 10 : 7;
+    for (int a = 0; a < ncopy; ++a)
+        BH_CUDA(c, cudaMemcpyAsync(ds[a], hs[a], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    BH_CUDA(c, cudaMemcpyAsync(d.id, h->id, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    BH_TRY(bh_step(ctx, &d, nsteps));
+    for (int a = 0; a < 10; ++a)
+        BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    return bh_sync(ctx);
+}
+
+int bh_sync(bh_ctx* ctx) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    return bh::read_status(c);
+}
+
+int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp, int64_t* n_pc, int64_t* n_jj) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (n_nodes) *n_nodes = c->have_tree ? c->n_nodes : 0;
+    if (n_groups) *n_groups = c->have_tree ? c->n_groups : 0;
+    if (n_pp) *n_pp = c->have_lists ? c->n_pp : 0;
+    if (n_pc) *n_pc = c->have_lists ? c->n_pc : 0;
+    if (n_jj) *n_jj = c->have_lists ? c->n_jj : 0;
+    return BH_OK;
+}
+
+#define BH_D2H(c, dst, src, bytes)                                                                   \
+    do {                                                                                             \
+        if (dst) BH_CUDA(c, cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyDeviceToHost, c->stream)); \
+    } while (0)
+
+int bh_get_keys(bh_ctx* ctx, uint64_t* keys, uint32_t* perm) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    BH_D2H(c, keys, c->key[c->key_cur].p, c->n * sizeof(uint64_t));
+    BH_D2H(c, perm, c->idx[c->key_cur].p, c->n * sizeof(uint32_t));
+    return bh::read_status(c);
+}
+
+int bh_get_root(bh_ctx* ctx, double* lo3, double* L) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    if (lo3) for (int a = 0; a < 3; ++a) lo3[a] = c->h_lo[a];
+    if (L) *L = c->h_L;
+    return BH_OK;
+}
+
+int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,
+                int32_t* first_child, uint8_t* nchild, uint32_t* qlo3, uint32_t* qhi3) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    const size_t nn = (size_t)c->n_nodes;
+    BH_D2H(c, level, c->level.p, nn);
+    BH_D2H(c, begin, c->begin.p, nn * 4);
+    BH_D2H(c, end, c->end.p, nn * 4);
+    BH_D2H(c, parent, c->parent.p, nn * 4);
+    BH_D2H(c, first_child, c->first_child.p, nn * 4);
+    BH_D2H(c, nchild, c->nchild.p, nn);
+    BH_D2H(c, qlo3, c->qlo.p, nn * 12);
+    BH_D2H(c, qhi3, c->qhi.p, nn * 12);
+    return bh::read_status(c);
+}
+
+int bh_get_moments(bh_ctx* ctx, double* M, double* c3, double* Q6) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    const size_t nn = (size_t)c->n_nodes;
+    BH_D2H(c, M, c->M.p, nn * 8);
+    if (c3) {
+        double* cys = c3 + nn;
+        double* czs = c3 + 2 * nn;
+        BH_CUDA(c, cudaMemcpyAsync(c3, c->cx.p, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaMemcpyAsync(cys, c->cy.p, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaMemcpyAsync(czs, c->cz.p, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    BH_D2H(c, Q6, c->Q.p, nn * 48);
+    return bh::read_status(c);
+}
+
+int bh_get_groups(bh_ctx* ctx, int32_t* group_nodes) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    BH_D2H(c, group_nodes, c->groups.p, (size_t)c->n_groups * 4);
+    return bh::read_status(c);
+}
+
+int bh_get_lists(bh_ctx* ctx, int64_t* pp_off, int32_t* pp_ids, int64_t* pc_off, int32_t* pc_ids) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_lists) return bh::fail(c, BH_E_STATE, "no lists");
+    const size_t ng = (size_t)c->n_groups;
+    BH_D2H(c, pp_off, c->cnt_p.p, (ng + 1) * 8);
+    BH_D2H(c, pp_ids, c->P.p, (size_t)c->n_pp * 4);
+    BH_D2H(c, pc_off, c->cnt_c.p, (ng + 1) * 8);
+    BH_D2H(c, pc_ids, c->C.p, (size_t)c->n_pc * 4);
+    return bh::read_status(c);
+}
+
+int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !out) return BH_E_INVAL;
+    out->n_groups = c->n_groups;
+    out->n_pp = c->n_int_pp;
+    out->n_pc = c->n_int_pc;
+    out->n_evals = c->evals_since_build;
+    out->n_rebuilds = c->n_rebuilds;
+    return BH_OK;
+}
+
+}  // extern "C"

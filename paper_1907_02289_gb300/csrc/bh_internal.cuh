@@ -1,0 +1,168 @@
+// bh_internal.cuh -- context layout and helpers shared by the libbh.so
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bh.h"
+
+namespace bh {
+
+constexpr int kLevels = 21;                    // key depth: 21 octal digits, 63 bits
+constexpr uint32_t kQMax = (1u << kLevels) - 1;
+
+// Device status word bits (set by kernels, read at synchronising calls).
+constexpr int kStatNonFinite = 1;
+constexpr int kStatListOverflow = 2;
+constexpr int kStatTimeout = 4;
+constexpr int kStatBounds = 8;  // an internal index check failed (access skipped)
+
+// Device buffer that only grows.
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+};
+
+struct Ctx;
+int fail(Ctx* c, int code, const char* fmt, ...);
+
+// cudaMalloc-backed growth; returns BH_OK or BH_E_NOMEM (with message).
+int grow_raw(Ctx* c, void** p, size_t* cap, size_t bytes_needed, const char* what, bool keep);
+template <typename T>
+int grow(Ctx* c, DBuf<T>& b, size_t n, const char* what, bool keep = false) {
+    size_t cap_bytes = b.cap * sizeof(T);
+    int rc = grow_raw(c, (void**)&b.p, &cap_bytes, n * sizeof(T), what, keep);
+    b.cap = cap_bytes / sizeof(T);
+    return rc;
+}
+
+// Per-node packed record read by the walk: (qlo.xyz, level | nchild << 8),
+// (qhi.xyz, first_child).
+struct WalkNode {
+    uint4 a, b;
+};
+
+struct Ctx {
+    bh_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    std::string err;
+
+    // state
+    int64_t n = 0;
+    bool have_tree = false, have_lists = false, have_acc = false;
+    int64_t k_eval = 0;        // force evaluations done (drives the rebuild schedule)
+    int64_t evals_since_build = 0, n_rebuilds = 0;
+
+    // status and small device scalars
+    int* d_status = nullptr;
+    double* d_box = nullptr;   // lo[3], L, S, spare
+    double h_lo[3] = {0, 0, 0}, h_L = 1.0, h_S = 0.0;
+    unsigned long long* d_small = nullptr;  // scan totals etc. (64 words)
+
+    // keys and sort
+    DBuf<uint64_t> key[2];
+    DBuf<uint32_t> idx[2];
+    int key_cur = 0;           // buffer holding the sorted keys / perm
+    DBuf<uint32_t> sort_hist;
+    DBuf<uint32_t> digit_hist; // 8 x 256 global digit counts
+    DBuf<double> pscratch;     // permutation scratch (8 bytes per particle)
+    DBuf<uint8_t> scan_tmp;
+
+    // tree
+    int64_t n_nodes = 0;
+    std::vector<int64_t> lvl_start;  // node id range of each level (size depth+2)
+    DBuf<uint8_t> level, nchild;
+    DBuf<uint32_t> begin, end;
+    DBuf<int32_t> parent, first_child;
+    DBuf<uint32_t> qlo, qhi;         // 3 per node
+    DBuf<WalkNode> wnode;
+    DBuf<uint32_t> split_cnt;        // per node of a level
+    DBuf<uint32_t> split_off;
+    DBuf<uint32_t> split_bnd;        // 9 per node of a level
+
+    // moments
+    DBuf<double> M, cx, cy, cz, Q;   // Q: 6 per node
+    DBuf<float4> cell32;             // 3 per node: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz)
+    DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
+
+    // groups
+    int64_t n_groups = 0;
+    DBuf<int32_t> gmark;             // per particle: group node starting here, or -1
+    DBuf<uint32_t> gflag, gpos;
+    DBuf<int32_t> groups;            // node ids ordered by begin
+    DBuf<int32_t> order;             // force-kernel processing order of groups
+
+    // lists
+    int64_t n_pp = 0, n_pc = 0, n_jj = 0;
+    int64_t n_int_pp = 0, n_int_pc = 0;
+    DBuf<int64_t> cnt_p, cnt_c, cnt_j;   // per group counts, then offsets (ng + 1)
+    DBuf<int32_t> P, C;
+    DBuf<uint32_t> JJ;
+    DBuf<int64_t> ipp;                   // per group interaction counts (scratch)
+
+    // host-buffer stepping
+    DBuf<double> hbuf;                   // 10 arrays of n doubles
+    DBuf<int64_t> hid;
+};
+
+// ---- CUDA error plumbing -------------------------------------------------
+#define BH_CUDA(c, call)                                                              \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::bh::fail((c), BH_E_CUDA, "%s failed: %s (%s:%d)", #call,          \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+#define BH_TRY(expr)                 \
+    do {                             \
+        int r_ = (expr);             \
+        if (r_ != BH_OK) return r_;  \
+    } while (0)
+#define BH_LAUNCH(c)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            return ::bh::fail((c), BH_E_CUDA, "kernel launch failed: %s (%s:%d)",      \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+
+inline unsigned blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---- stage entry points (one translation unit each) ------------------------
+// scan.cu: exclusive prefix sums; *total written to d_total (device) if given.
+int scan_u32(Ctx* c, const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* d_total);
+int scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, unsigned long long* d_total);
+
+// sort.cu
+int stage_keys(Ctx* c, const bh_particles* p);     // root box + keys (+ status on NaN)
+int stage_sort(Ctx* c);                            // stable LSD radix sort of (key, idx)
+int stage_permute(Ctx* c, bh_particles* p);        // gather particle arrays into key order
+
+// tree.cu
+int stage_octree(Ctx* c);                          // level-by-level split; sets n_nodes
+int stage_boxes(Ctx* c);                           // integer boxes + walk records
+int stage_moments(Ctx* c, const bh_particles* p);  // M, c, Q (+ FP32 cell records)
+int stage_groups(Ctx* c);                          // groups ordered by begin
+
+// walk.cu
+int stage_lists(Ctx* c);                           // walk (count, fill) + particle expansion
+
+// force.cu
+int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of particles
+int stage_force(Ctx* c, bh_particles* p, bool add_central);
+
+// update.cu
+int stage_kick(Ctx* c, bh_particles* p, double h);
+int stage_kick_drift(Ctx* c, bh_particles* p, double h, double dt);
+
+}  // namespace bh

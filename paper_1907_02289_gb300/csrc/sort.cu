@@ -1,0 +1,332 @@
+// sort.cu -- Sec. 4.2 step 3a, first half: root box, Morton keys, the
+// stable LSD radix sort of (key, original index) and the gather of every
+// particle array into key order.
+//
+// Keys: q_a = min(floor((x_a - lo_a) * S), 2^21 - 1), S = 2^21 / L, with L the
+// largest extent of the root box (1 if 0); key bit 3b+2/3b+1/3b = bit b of
+// q_x/q_y/q_z.  The subtraction and product are done with _rn intrinsics so
+// that no multiply-add contraction changes a key.
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+constexpr int kBoxThreads = 256;
+
+__device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+}
+
+// Per-block min/max of each axis -> part[6 * block + {mn x,y,z, mx x,y,z}].
+__global__ void k_box_partial(const double* __restrict__ x, const double* __restrict__ y,
+                              const double* __restrict__ z, int64_t n, double* __restrict__ part,
+                              int* status) {
+    __shared__ double s[6][kBoxThreads / 32];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bad |= !isfinite(v[a]);
+            mn[a] = fmin(mn[a], v[a]);
+            mx[a] = fmax(mx[a], v[a]);
+        }
+    }
+    if (bad) atomicOr(status, kStatNonFinite);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        warp_minmax(mn[a], mx[a]);
+        if (lane == 0) {
+            s[a][w] = mn[a];
+            s[3 + a][w] = mx[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double r = s[threadIdx.x][0];
+        for (int k = 1; k < kBoxThreads / 32; ++k)
+            r = threadIdx.x < 3 ? fmin(r, s[threadIdx.x][k]) : fmax(r, s[threadIdx.x][k]);
+        part[6 * blockIdx.x + threadIdx.x] = r;
+    }
+}
+
+// box = {lo_x, lo_y, lo_z, L, S}
+__global__ void k_box_final(const double* __restrict__ part, int nb, double* box) {
+    __shared__ double r[6];
+    if (threadIdx.x < 6) {
+        double v = part[threadIdx.x];
+        for (int b = 1; b < nb; ++b)
+            v = threadIdx.x < 3 ? fmin(v, part[6 * b + threadIdx.x]) : fmax(v, part[6 * b + threadIdx.x]);
+        r[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ext = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            box[a] = r[a];
+            double e = __dsub_rn(r[3 + a], r[a]);
+            if (e > ext) ext = e;
+        }
+        double L = ext > 0.0 ? ext : 1.0;
+        box[3] = L;
+        box[4] = __ddiv_rn(2097152.0, L);
+    }
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & kQMax;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t quantise(double v, double lo, double S) {
+    double t = floor(__dmul_rn(__dsub_rn(v, lo), S));
+    t = fmax(t, 0.0);
+    t = fmin(t, (double)kQMax);
+    return (uint32_t)t;
+}
+
+__global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
+                       const double* __restrict__ z, int64_t n, const double* __restrict__ box,
+                       uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double S = box[4];
+    uint32_t qx = quantise(x[i], box[0], S), qy = quantise(y[i], box[1], S),
+             qz = quantise(z[i], box[2], S);
+    key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    idx[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort: 8-bit digits, passes over bits [8p, 8p+8).  Per pass:
+//   upsweep   per-tile digit histogram, stored digit-major hist[d * ntiles + t]
+//   scan      exclusive scan of hist -> global start of (digit, tile)
+//   downsweep stable in-tile ranking (warp match + per-warp counters), local
+//             reorder through shared memory, coalesced scatter.
+// Stability: ranks follow (tile, warp, round, lane) = input order.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;                       // per lane
+constexpr int kSortTile = kSortThreads * kSortItems; // 4096
+constexpr int kRadix = 256;
+
+__global__ void k_digit_hist(const uint64_t* __restrict__ key, int64_t n, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[8][kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = key[i];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xff], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x)
+        if ((&h[0][0])[i]) atomicAdd(&hist[i], (&h[0][0])[i]);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_upsweep(const uint64_t* __restrict__ key, int64_t n,
+                                                         int shift, uint32_t* __restrict__ hist,
+                                                         int ntiles) {
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; ++k) {
+        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(key[i] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+struct DownSmem {
+    uint32_t whist[kSortWarps][kRadix];
+    uint32_t tstart[kRadix];
+    uint32_t goff[kRadix];
+    uint32_t wtot[kSortWarps];
+    uint64_t skey[kSortTile];
+    uint32_t sidx[kSortTile];
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_downsweep(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin, int64_t n, int shift,
+    const uint32_t* __restrict__ offs, int ntiles, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ iout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    S.goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = tbase + (int64_t)w * (32 * kSortItems);
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t kr[kSortItems];
+    uint32_t ir[kSortItems], lr[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t pos = wbase + r * 32 + lane;
+        bool valid = pos < n;
+        uint64_t k = valid ? kin[pos] : 0;
+        uint32_t d = valid ? (uint32_t)((k >> shift) & 0xff) : 0x100u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && valid) {
+            old = S.whist[w][d];
+            S.whist[w][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        kr[r] = k;
+        ir[r] = valid ? iin[pos] : 0u;
+        lr[r] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive over warps; tile total; exclusive over digits
+    {
+        const int d = threadIdx.x;  // kSortThreads == kRadix
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            uint32_t t = S.whist[ww][d];
+            S.whist[ww][d] = run;
+            run += t;
+        }
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) S.wtot[w] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int ww = 0; ww < w; ++ww) add += S.wtot[ww];
+        S.tstart[d] = add + x - run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t pos = wbase + r * 32 + lane;
+        if (pos < n) {
+            uint32_t d = (uint32_t)((kr[r] >> shift) & 0xff);
+            uint32_t p = S.tstart[d] + S.whist[w][d] + lr[r];
+            S.skey[p] = kr[r];
+            S.sidx[p] = ir[r];
+        }
+    }
+    __syncthreads();
+    int64_t tn = n - tbase;
+    if (tn > kSortTile) tn = kSortTile;
+    for (int q = threadIdx.x; q < tn; q += kSortThreads) {
+        uint64_t k = S.skey[q];
+        uint32_t d = (uint32_t)((k >> shift) & 0xff);
+        uint64_t g = (uint64_t)S.goff[d] + (uint64_t)(q - S.tstart[d]);
+        kout[g] = k;
+        iout[g] = S.sidx[q];
+    }
+}
+
+__global__ void k_gather8(const unsigned long long* __restrict__ src, unsigned long long* __restrict__ dst,
+                          const uint32_t* __restrict__ perm, int64_t n, int* status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    if (j < n)
+        dst[i] = src[j];
+    else
+        atomicOr(status, kStatBounds);
+}
+
+}  // namespace
+
+int stage_keys(Ctx* c, const bh_particles* p) {
+    const int64_t n = c->n;
+    const int nb = c->num_sms * 4;
+    BH_TRY(grow(c, c->pscratch, (size_t)(n > 6 * nb ? n : 6 * nb), "particle scratch"));
+    double* part = c->pscratch.p;
+    k_box_partial<<<nb, kBoxThreads, 0, c->stream>>>(p->x, p->y, p->z, n, part, c->d_status);
+    BH_LAUNCH(c);
+    k_box_final<<<1, 32, 0, c->stream>>>(part, nb, c->d_box);
+    BH_LAUNCH(c);
+    for (int b = 0; b < 2; ++b) {
+        BH_TRY(grow(c, c->key[b], (size_t)n, "keys"));
+        BH_TRY(grow(c, c->idx[b], (size_t)n, "sort indices"));
+    }
+    k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(p->x, p->y, p->z, n, c->d_box, c->key[0].p, c->idx[0].p);
+    BH_LAUNCH(c);
+    c->key_cur = 0;
+    return BH_OK;
+}
+
+int stage_sort(Ctx* c) {
+    const int64_t n = c->n;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    BH_TRY(grow(c, c->digit_hist, 8 * kRadix, "digit histogram"));
+    BH_TRY(grow(c, c->sort_hist, (size_t)kRadix * ntiles, "sort histogram"));
+    BH_CUDA(c, cudaMemsetAsync(c->digit_hist.p, 0, 8 * kRadix * sizeof(uint32_t), c->stream));
+    k_digit_hist<<<c->num_sms * 2, 256, 0, c->stream>>>(c->key[c->key_cur].p, n, c->digit_hist.p);
+    BH_LAUNCH(c);
+    uint32_t h[8 * kRadix];
+    BH_CUDA(c, cudaMemcpyAsync(h, c->digit_hist.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    static bool attr_set = false;
+    const int smem = (int)sizeof(DownSmem);
+    if (!attr_set) {
+        BH_CUDA(c, cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    for (int pass = 0; pass < 8; ++pass) {
+        bool trivial = false;
+        for (int d = 0; d < kRadix; ++d)
+            if ((int64_t)h[pass * kRadix + d] == n) trivial = true;
+        if (trivial) continue;  // every key has the same digit: order unchanged
+        const int shift = 8 * pass, a = c->key_cur, b = 1 - a;
+        k_upsweep<<<ntiles, kSortThreads, 0, c->stream>>>(c->key[a].p, n, shift, c->sort_hist.p, ntiles);
+        BH_LAUNCH(c);
+        BH_TRY(scan_u32(c, c->sort_hist.p, c->sort_hist.p, (int64_t)kRadix * ntiles, nullptr));
+        k_downsweep<<<ntiles, kSortThreads, smem, c->stream>>>(c->key[a].p, c->idx[a].p, n, shift,
+                                                               c->sort_hist.p, ntiles, c->key[b].p,
+                                                               c->idx[b].p);
+        BH_LAUNCH(c);
+        c->key_cur = b;
+    }
+    return BH_OK;
+}
+
+int stage_permute(Ctx* c, bh_particles* p) {
+    const int64_t n = c->n;
+    BH_TRY(grow(c, c->pscratch, (size_t)n, "particle scratch"));
+    unsigned long long* arrs[8] = {(unsigned long long*)p->x,  (unsigned long long*)p->y,
+                                   (unsigned long long*)p->z,  (unsigned long long*)p->vx,
+                                   (unsigned long long*)p->vy, (unsigned long long*)p->vz,
+                                   (unsigned long long*)p->m,  (unsigned long long*)p->id};
+    const uint32_t* perm = c->idx[c->key_cur].p;
+    for (int a = 0; a < 8; ++a) {
+        if (!arrs[a]) continue;
+        k_gather8<<<blocks_for(n, 256), 256, 0, c->stream>>>(arrs[a], (unsigned long long*)c->pscratch.p, perm, n,
+                                                                c->d_status);
+        BH_LAUNCH(c);
+        BH_CUDA(c, cudaMemcpyAsync(arrs[a], c->pscratch.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return BH_OK;
+}
+
+}  // namespace bh

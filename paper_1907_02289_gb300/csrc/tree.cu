@@ -1,0 +1,377 @@
+// tree.cu -- Sec. 4.2 step 3a, second half, and the node refresh of the
+// list-reusing step: level-by-level octree over sorted keys, integer node
+// boxes on the key grid, node moments (mass, centre of mass, traceless
+// quadrupole) and the groups (maximal nodes with at most n_g particles).
+//
+// Numbering: breadth first, key order within a level (a node's children are
+// contiguous and in octant order).  A node at level l splits on the digit of
+// level l+1 when it holds more than n_leaf particles and l < 21.
+//
+// Moments follow one fixed operation order (leaves: particles in order;
+// internal nodes: children in octant order) with _rn intrinsics, so they do
+// not depend on thread scheduling or on multiply-add contraction.
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x00000000001fffffull;
+    return (uint32_t)x;
+}
+
+__global__ void k_root(uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent, uint32_t n) {
+    level[0] = 0;
+    begin[0] = 0;
+    end[0] = n;
+    parent[0] = -1;
+}
+
+// Child boundaries of each node of one level: bnd[9 t + o] = first particle
+// with octant digit >= o (o = 0..8), found by binary search.
+__global__ void k_split_count(const uint64_t* __restrict__ key, const uint32_t* __restrict__ begin,
+                              const uint32_t* __restrict__ end, int64_t ls, int64_t cnt, int lev,
+                              int n_leaf, uint32_t* __restrict__ nch_out, uint32_t* __restrict__ bnd) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const uint32_t b = begin[ls + t], e = end[ls + t];
+    uint32_t nch = 0;
+    if (e - b > (uint32_t)n_leaf && lev < kLevels) {
+        const int shift = 3 * (kLevels - 1 - lev);
+        uint32_t lo = b, prev = b;
+        bnd[9 * t] = b;
+        for (int o = 1; o < 8; ++o) {
+            uint32_t hi = e;
+            while (lo < hi) {
+                uint32_t mid = lo + ((hi - lo) >> 1);
+                if ((int)((key[mid] >> shift) & 7u) < o)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            bnd[9 * t + o] = lo;
+            nch += (lo > prev);
+            prev = lo;
+        }
+        bnd[9 * t + 8] = e;
+        nch += (e > prev);
+    }
+    nch_out[t] = nch;
+}
+
+__global__ void k_split_write(const uint32_t* __restrict__ nch_in, const uint32_t* __restrict__ off,
+                              const uint32_t* __restrict__ bnd, int64_t ls, int64_t cnt, int64_t le,
+                              int lev, uint8_t* level, uint32_t* begin, uint32_t* end,
+                              int32_t* parent, int32_t* first_child, uint8_t* nchild) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t node = ls + t;
+    const uint32_t nch = nch_in[t];
+    if (nch == 0) {
+        first_child[node] = -1;
+        nchild[node] = 0;
+        return;
+    }
+    const int64_t fc = le + off[t];
+    first_child[node] = (int32_t)fc;
+    nchild[node] = (uint8_t)nch;
+    int k = 0;
+    for (int o = 0; o < 8; ++o) {
+        uint32_t b0 = bnd[9 * t + o], b1 = bnd[9 * t + o + 1];
+        if (b1 > b0) {
+            int64_t ch = fc + k++;
+            level[ch] = (uint8_t)(lev + 1);
+            begin[ch] = b0;
+            end[ch] = b1;
+            parent[ch] = (int32_t)node;
+        }
+    }
+}
+
+// Integer tight boxes (grid coordinates recovered from the keys) and the
+// packed records the walk reads.
+__global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cnt,
+                        const uint8_t* __restrict__ level, const uint32_t* __restrict__ begin,
+                        const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
+                        const uint8_t* __restrict__ nchild, uint32_t* qlo, uint32_t* qhi,
+                        WalkNode* wnode) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t k = ls + t;
+    uint32_t lo[3] = {kQMax, kQMax, kQMax}, hi[3] = {0, 0, 0};
+    const int nc = nchild[k];
+    if (nc == 0) {
+        for (uint32_t i = begin[k]; i < end[k]; ++i) {
+            uint64_t kk = key[i];
+            uint32_t q[3] = {compact3(kk >> 2), compact3(kk >> 1), compact3(kk)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = min(lo[a], q[a]);
+                hi[a] = max(hi[a], q[a]);
+            }
+        }
+    } else {
+        const int64_t f = first_child[k];
+        for (int c = 0; c < nc; ++c)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = min(lo[a], qlo[3 * (f + c) + a]);
+                hi[a] = max(hi[a], qhi[3 * (f + c) + a]);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        qlo[3 * k + a] = lo[a];
+        qhi[3 * k + a] = hi[a];
+    }
+    WalkNode w;
+    w.a = make_uint4(lo[0], lo[1], lo[2], (uint32_t)level[k] | ((uint32_t)nc << 8));
+    w.b = make_uint4(hi[0], hi[1], hi[2], (uint32_t)first_child[k]);
+    wnode[k] = w;
+}
+
+__device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
+
+// Moments of the nodes of one level (children already done).
+template <int ORDER, bool CELL32>
+__global__ void k_moments(int64_t ls, int64_t cnt, const uint32_t* __restrict__ begin,
+                          const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
+                          const uint8_t* __restrict__ nchild, const double* __restrict__ x,
+                          const double* __restrict__ y, const double* __restrict__ z,
+                          const double* __restrict__ m, double* M, double* cx, double* cy,
+                          double* cz, double* Q, float4* cell32) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t k = ls + t;
+    const int nc = nchild[k];
+    double Mk = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, c0, c1, c2;
+    double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (nc == 0) {
+        const uint32_t b = begin[k], e = end[k];
+        for (uint32_t i = b; i < e; ++i) {
+            const double mi = m[i];
+            Mk = __dadd_rn(Mk, mi);
+            sx = __dadd_rn(sx, __dmul_rn(mi, x[i]));
+            sy = __dadd_rn(sy, __dmul_rn(mi, y[i]));
+            sz = __dadd_rn(sz, __dmul_rn(mi, z[i]));
+        }
+        if (Mk > 0.0) {
+            c0 = __ddiv_rn(sx, Mk);
+            c1 = __ddiv_rn(sy, Mk);
+            c2 = __ddiv_rn(sz, Mk);
+        } else {
+            c0 = x[b];
+            c1 = y[b];
+            c2 = z[b];
+        }
+        if (ORDER >= 2)
+            for (uint32_t i = b; i < e; ++i) {
+                const double mi = m[i];
+                const double dx = __dsub_rn(x[i], c0), dy = __dsub_rn(y[i], c1), dz = __dsub_rn(z[i], c2);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                const double tx = __dmul_rn(3.0, dx), ty = __dmul_rn(3.0, dy), tz = __dmul_rn(3.0, dz);
+                q[0] = __dadd_rn(q[0], __dmul_rn(mi, __dsub_rn(__dmul_rn(tx, dx), d2)));
+                q[1] = __dadd_rn(q[1], __dmul_rn(mi, __dsub_rn(__dmul_rn(ty, dy), d2)));
+                q[2] = __dadd_rn(q[2], __dmul_rn(mi, __dsub_rn(__dmul_rn(tz, dz), d2)));
+                q[3] = __dadd_rn(q[3], __dmul_rn(mi, __dmul_rn(tx, dy)));
+                q[4] = __dadd_rn(q[4], __dmul_rn(mi, __dmul_rn(tx, dz)));
+                q[5] = __dadd_rn(q[5], __dmul_rn(mi, __dmul_rn(ty, dz)));
+            }
+    } else {
+        const int64_t f = first_child[k];
+        for (int c = 0; c < nc; ++c) {
+            const double Mc = M[f + c];
+            Mk = __dadd_rn(Mk, Mc);
+            sx = __dadd_rn(sx, __dmul_rn(Mc, cx[f + c]));
+            sy = __dadd_rn(sy, __dmul_rn(Mc, cy[f + c]));
+            sz = __dadd_rn(sz, __dmul_rn(Mc, cz[f + c]));
+        }
+        if (Mk > 0.0) {
+            c0 = __ddiv_rn(sx, Mk);
+            c1 = __ddiv_rn(sy, Mk);
+            c2 = __ddiv_rn(sz, Mk);
+        } else {
+            c0 = cx[f];
+            c1 = cy[f];
+            c2 = cz[f];
+        }
+        if (ORDER >= 2)
+            for (int c = 0; c < nc; ++c) {
+                const double Mc = M[f + c];
+                const double dx = __dsub_rn(cx[f + c], c0), dy = __dsub_rn(cy[f + c], c1),
+                             dz = __dsub_rn(cz[f + c], c2);
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                const double tx = __dmul_rn(3.0, dx), ty = __dmul_rn(3.0, dy), tz = __dmul_rn(3.0, dz);
+                const double* qc = Q + 6 * (f + c);
+                q[0] = __dadd_rn(__dadd_rn(q[0], qc[0]), __dmul_rn(Mc, __dsub_rn(__dmul_rn(tx, dx), d2)));
+                q[1] = __dadd_rn(__dadd_rn(q[1], qc[1]), __dmul_rn(Mc, __dsub_rn(__dmul_rn(ty, dy), d2)));
+                q[2] = __dadd_rn(__dadd_rn(q[2], qc[2]), __dmul_rn(Mc, __dsub_rn(__dmul_rn(tz, dz), d2)));
+                q[3] = __dadd_rn(__dadd_rn(q[3], qc[3]), __dmul_rn(Mc, __dmul_rn(tx, dy)));
+                q[4] = __dadd_rn(__dadd_rn(q[4], qc[4]), __dmul_rn(Mc, __dmul_rn(tx, dz)));
+                q[5] = __dadd_rn(__dadd_rn(q[5], qc[5]), __dmul_rn(Mc, __dmul_rn(ty, dz)));
+            }
+    }
+    M[k] = Mk;
+    cx[k] = c0;
+    cy[k] = c1;
+    cz[k] = c2;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Q[6 * k + a] = q[a];
+    if (CELL32) {
+        float h0, h1, h2, l0, l1, l2;
+        split_f32(c0, h0, l0);
+        split_f32(c1, h1, l1);
+        split_f32(c2, h2, l2);
+        cell32[3 * k + 0] = make_float4(h0, h1, h2, __double2float_rn(Mk));
+        cell32[3 * k + 1] = make_float4(l0, l1, l2, __double2float_rn(q[0]));
+        cell32[3 * k + 2] = make_float4(__double2float_rn(q[3]), __double2float_rn(q[4]),
+                                        __double2float_rn(q[1]), __double2float_rn(q[5]));
+    }
+}
+
+__global__ void k_group_mark(int64_t nn, const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end,
+                             const int32_t* __restrict__ parent, const uint8_t* __restrict__ nchild,
+                             int n_g, int32_t* __restrict__ gmark) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nn) return;
+    const uint32_t cnt = end[k] - begin[k];
+    const bool small = cnt <= (uint32_t)n_g || nchild[k] == 0;
+    bool top = (k == 0);
+    if (!top) {
+        const int32_t p = parent[k];
+        top = (end[p] - begin[p]) > (uint32_t)n_g;
+    }
+    if (small && top) gmark[begin[k]] = (int32_t)k;
+}
+
+__global__ void k_group_flag(const int32_t* __restrict__ gmark, int64_t n, uint32_t* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = gmark[i] >= 0 ? 1u : 0u;
+}
+
+__global__ void k_group_compact(const int32_t* __restrict__ gmark, const uint32_t* __restrict__ pos,
+                                int64_t n, int32_t* __restrict__ groups) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && gmark[i] >= 0) groups[pos[i]] = gmark[i];
+}
+
+int grow_nodes(Ctx* c, size_t need) {
+    if (need <= c->level.cap) return BH_OK;
+    size_t cap = need + need / 2 + 1024;
+    BH_TRY(grow(c, c->level, cap, "node level", true));
+    BH_TRY(grow(c, c->nchild, cap, "node nchild", true));
+    BH_TRY(grow(c, c->begin, cap, "node begin", true));
+    BH_TRY(grow(c, c->end, cap, "node end", true));
+    BH_TRY(grow(c, c->parent, cap, "node parent", true));
+    BH_TRY(grow(c, c->first_child, cap, "node first_child", true));
+    return BH_OK;
+}
+
+}  // namespace
+
+int stage_octree(Ctx* c) {
+    const int64_t n = c->n;
+    const uint64_t* key = c->key[c->key_cur].p;
+    BH_TRY(grow_nodes(c, (size_t)(n / 2 + 64)));
+    k_root<<<1, 1, 0, c->stream>>>(c->level.p, c->begin.p, c->end.p, c->parent.p, (uint32_t)n);
+    BH_LAUNCH(c);
+    c->lvl_start.assign({0, 1});
+    for (int lev = 0;; ++lev) {
+        const int64_t ls = c->lvl_start[lev], le = c->lvl_start[lev + 1], cnt = le - ls;
+        BH_TRY(grow(c, c->split_cnt, (size_t)cnt, "split counts"));
+        BH_TRY(grow(c, c->split_off, (size_t)cnt, "split offsets"));
+        BH_TRY(grow(c, c->split_bnd, (size_t)cnt * 9, "split bounds"));
+        k_split_count<<<blocks_for(cnt, 128), 128, 0, c->stream>>>(key, c->begin.p, c->end.p, ls, cnt, lev,
+                                                                   c->prm.n_leaf, c->split_cnt.p, c->split_bnd.p);
+        BH_LAUNCH(c);
+        BH_TRY(scan_u32(c, c->split_cnt.p, c->split_off.p, cnt, c->d_small));
+        unsigned long long total = 0;
+        BH_CUDA(c, cudaMemcpyAsync(&total, c->d_small, sizeof(total), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        BH_TRY(grow_nodes(c, (size_t)(le + total)));
+        k_split_write<<<blocks_for(cnt, 128), 128, 0, c->stream>>>(
+            c->split_cnt.p, c->split_off.p, c->split_bnd.p, ls, cnt, le, lev, c->level.p, c->begin.p,
+            c->end.p, c->parent.p, c->first_child.p, c->nchild.p);
+        BH_LAUNCH(c);
+        if (total == 0) break;
+        c->lvl_start.push_back(le + (int64_t)total);
+    }
+    c->n_nodes = c->lvl_start.back();
+    return BH_OK;
+}
+
+int stage_boxes(Ctx* c) {
+    const int64_t nn = c->n_nodes;
+    BH_TRY(grow(c, c->qlo, (size_t)nn * 3, "node qlo"));
+    BH_TRY(grow(c, c->qhi, (size_t)nn * 3, "node qhi"));
+    BH_TRY(grow(c, c->wnode, (size_t)nn, "walk records"));
+    const int depth = (int)c->lvl_start.size() - 1;
+    for (int lev = depth - 1; lev >= 0; --lev) {
+        const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
+        k_boxes<<<blocks_for(cnt, 128), 128, 0, c->stream>>>(c->key[c->key_cur].p, ls, cnt, c->level.p,
+                                                             c->begin.p, c->end.p, c->first_child.p,
+                                                             c->nchild.p, c->qlo.p, c->qhi.p, c->wnode.p);
+        BH_LAUNCH(c);
+    }
+    return BH_OK;
+}
+
+int stage_moments(Ctx* c, const bh_particles* p) {
+    const int64_t nn = c->n_nodes;
+    BH_TRY(grow(c, c->M, (size_t)nn, "moments M"));
+    BH_TRY(grow(c, c->cx, (size_t)nn, "moments cx"));
+    BH_TRY(grow(c, c->cy, (size_t)nn, "moments cy"));
+    BH_TRY(grow(c, c->cz, (size_t)nn, "moments cz"));
+    BH_TRY(grow(c, c->Q, (size_t)nn * 6, "moments Q"));
+    const bool f32 = c->prm.precision == BH_PREC_FP32;
+    if (f32) BH_TRY(grow(c, c->cell32, (size_t)nn * 3, "FP32 cell records"));
+    const int depth = (int)c->lvl_start.size() - 1;
+    for (int lev = depth - 1; lev >= 0; --lev) {
+        const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
+        const unsigned nb = blocks_for(cnt, 128);
+#define BH_MOM(O, F)                                                                               \
+    k_moments<O, F><<<nb, 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p, c->first_child.p,     \
+                                               c->nchild.p, p->x, p->y, p->z, p->m, c->M.p, c->cx.p, \
+                                               c->cy.p, c->cz.p, c->Q.p, c->cell32.p)
+        if (c->prm.order >= 2) {
+            if (f32) BH_MOM(2, true); else BH_MOM(2, false);
+        } else {
+            if (f32) BH_MOM(1, true); else BH_MOM(1, false);
+        }
+#undef BH_MOM
+        BH_LAUNCH(c);
+    }
+    return BH_OK;
+}
+
+int stage_groups(Ctx* c) {
+    const int64_t n = c->n, nn = c->n_nodes;
+    BH_TRY(grow(c, c->gmark, (size_t)n, "group marks"));
+    BH_TRY(grow(c, c->gflag, (size_t)n, "group flags"));
+    BH_TRY(grow(c, c->gpos, (size_t)n, "group positions"));
+    BH_CUDA(c, cudaMemsetAsync(c->gmark.p, 0xff, n * sizeof(int32_t), c->stream));
+    k_group_mark<<<blocks_for(nn, 256), 256, 0, c->stream>>>(nn, c->begin.p, c->end.p, c->parent.p,
+                                                             c->nchild.p, c->prm.n_g, c->gmark.p);
+    BH_LAUNCH(c);
+    k_group_flag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->gmark.p, n, c->gflag.p);
+    BH_LAUNCH(c);
+    BH_TRY(scan_u32(c, c->gflag.p, c->gpos.p, n, c->d_small));
+    unsigned long long ng = 0;
+    BH_CUDA(c, cudaMemcpyAsync(&ng, c->d_small, sizeof(ng), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    BH_TRY(grow(c, c->groups, (size_t)ng + 1, "groups"));
+    k_group_compact<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->gmark.p, c->gpos.p, n, c->groups.p);
+    BH_LAUNCH(c);
+    c->n_groups = (int64_t)ng;
+    return BH_OK;
+}
+
+}  // namespace bh

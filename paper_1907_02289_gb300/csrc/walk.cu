@@ -1,0 +1,206 @@
+// walk.cu -- Sec. 4.2 step 3d, first half: one tree traversal per group
+// builds the group's interaction list (Barnes' group walk): opened leaves
+// become particle entries, accepted nodes become cell entries.  The walk is
+// depth first in octant order, so both lists come out ordered by first
+// particle.  A count pass sizes the lists, a fill pass writes them, and the
+// particle entries are then expanded into the particle indices the force
+// kernel reads.
+//
+// Opening test (integer boxes on the key grid, exact): per axis the gap in
+// whole cells is delta = max(0, clo - ghi - 1, glo - chi - 1), d2 = sum of
+// delta^2.  A node of level l (side 2^(21-l) cells) is opened iff
+// fl(theta^2 * d2) < 4^(21-l), or d2 <= (r_coll * S)^2.  Both comparisons
+// are monotone in the integer d2, so the host turns them into integer
+// thresholds once per build: open iff d2 < D[l] or d2 <= RCQ.
+#include <cmath>
+
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+struct WalkParams {
+    long long D[kLevels + 1];
+    long long rcq;
+};
+
+template <bool FILL>
+__global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
+                                              const WalkNode* __restrict__ wn,
+                                              const uint32_t* __restrict__ begin,
+                                              const uint32_t* __restrict__ end, WalkParams wp,
+                                              int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
+                                              int64_t* __restrict__ nj_io, int32_t* __restrict__ P,
+                                              int32_t* __restrict__ C, unsigned long long* inter,
+                                              int64_t nn, int* status) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = k < ng;
+    int64_t np = 0, nc = 0, nj = 0, ni = 0;
+    if (active) {
+        const int32_t g = groups[k];
+        const WalkNode G = wn[g];
+        const int glo0 = (int)G.a.x, glo1 = (int)G.a.y, glo2 = (int)G.a.z;
+        const int ghi0 = (int)G.b.x, ghi1 = (int)G.b.y, ghi2 = (int)G.b.z;
+        ni = (int64_t)(end[g] - begin[g]);
+        int64_t pbase = 0, cbase = 0;
+        if (FILL) {
+            pbase = np_io[k];
+            cbase = nc_io[k];
+        }
+        int sn[kLevels + 3], se[kLevels + 3];
+        int sp = 0;
+        int node = 0;
+        for (;;) {
+            const WalkNode R = wn[node];
+            const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
+            const int d0 = max(0, max((int)R.a.x - ghi0 - 1, glo0 - (int)R.b.x - 1));
+            const int d1 = max(0, max((int)R.a.y - ghi1 - 1, glo1 - (int)R.b.y - 1));
+            const int d2i = max(0, max((int)R.a.z - ghi2 - 1, glo2 - (int)R.b.z - 1));
+            const long long d2 = (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2i * d2i;
+            const bool open = d2 < wp.D[lev] || d2 <= wp.rcq;
+            if (open) {
+                if (nch == 0) {
+                    if (FILL) P[pbase + np] = node;
+                    ++np;
+                    nj += (int64_t)(end[node] - begin[node]);
+                } else {
+                    sn[sp] = (int)R.b.w;
+                    se[sp] = (int)R.b.w + nch;
+                    ++sp;
+                }
+            } else {
+                if (FILL) C[cbase + nc] = node;
+                ++nc;
+            }
+            if (sp == 0) break;
+            node = sn[sp - 1]++;
+            if (sn[sp - 1] == se[sp - 1]) --sp;
+            if (node < 0 || node >= nn || sp > kLevels + 1) {  // never taken for a valid tree
+                atomicOr(status, kStatBounds);
+                break;
+            }
+        }
+        if (!FILL) {
+            np_io[k] = np;
+            nc_io[k] = nc;
+            nj_io[k] = nj;
+        }
+    }
+    if (!FILL) {
+        // interaction counts: n_i * (list particles) and n_i * (list cells)
+        unsigned long long ipp = (unsigned long long)(ni * nj), ipc = (unsigned long long)(ni * nc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
+            ipc += __shfl_xor_sync(0xffffffffu, ipc, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&inter[0], ipp);
+            atomicAdd(&inter[1], ipc);
+        }
+    }
+}
+
+// One warp per group: particle entries -> particle indices.
+__global__ void k_expand(int64_t ng, const int64_t* __restrict__ pp_off, const int32_t* __restrict__ P,
+                         const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end,
+                         const int64_t* __restrict__ jj_off, uint32_t* __restrict__ JJ) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= ng) return;
+    const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
+    int64_t jo = jj_off[k];
+    for (int64_t e = e0; e < e1; e += 32) {
+        uint32_t b = 0, cnt = 0;
+        if (e + lane < e1) {
+            const int32_t leaf = P[e + lane];
+            b = begin[leaf];
+            cnt = end[leaf] - b;
+        }
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
+        const int64_t pos = jo + (x - cnt);
+        for (uint32_t t = 0; t < cnt; ++t) JJ[pos + t] = b + t;
+        jo += tot;
+    }
+}
+
+__global__ void k_set_last(int64_t* off, int64_t ng, const unsigned long long* total) {
+    off[ng] = (int64_t)*total;
+}
+
+WalkParams walk_params(const Ctx* c) {
+    WalkParams w;
+    const double th2 = c->prm.theta * c->prm.theta;
+    const long long big = (long long)1 << 53;
+    for (int l = 0; l <= kLevels; ++l) {
+        const double s = std::ldexp(1.0, kLevels - l);
+        const double s2 = s * s;
+        if (th2 == 0.0) {
+            w.D[l] = big;
+            continue;
+        }
+        const double est = std::floor(s2 / th2);
+        if (!(est < (double)big)) {
+            w.D[l] = big;
+            continue;
+        }
+        long long d = (long long)est;
+        while (d > 0 && th2 * (double)(d - 1) >= s2) --d;
+        while (!(th2 * (double)d >= s2)) ++d;
+        w.D[l] = d;
+    }
+    const double rcq = c->prm.r_coll * c->h_S;
+    const double rcq2 = rcq * rcq;
+    w.rcq = (rcq2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(rcq2);
+    return w;
+}
+
+}  // namespace
+
+int stage_lists(Ctx* c) {
+    const int64_t ng = c->n_groups;
+    BH_TRY(grow(c, c->cnt_p, (size_t)ng + 1, "list offsets P"));
+    BH_TRY(grow(c, c->cnt_c, (size_t)ng + 1, "list offsets C"));
+    BH_TRY(grow(c, c->cnt_j, (size_t)ng + 1, "list offsets J"));
+    const WalkParams wp = walk_params(c);
+    unsigned long long* inter = c->d_small + 8;
+    BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));
+    const unsigned nb = blocks_for(ng, 128);
+    k_walk<false><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
+                                             c->cnt_c.p, c->cnt_j.p, nullptr, nullptr, inter,
+                                             c->n_nodes, c->d_status);
+    BH_LAUNCH(c);
+    DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
+    for (int a = 0; a < 3; ++a) {
+        BH_TRY(scan_i64(c, arr[a]->p, arr[a]->p, ng, c->d_small + a));
+        k_set_last<<<1, 1, 0, c->stream>>>(arr[a]->p, ng, c->d_small + a);
+        BH_LAUNCH(c);
+    }
+    unsigned long long h[16];
+    BH_CUDA(c, cudaMemcpyAsync(h, c->d_small, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->n_pp = (int64_t)h[0];
+    c->n_pc = (int64_t)h[1];
+    c->n_jj = (int64_t)h[2];
+    c->n_int_pp = (int64_t)h[8];
+    c->n_int_pc = (int64_t)h[9];
+    BH_TRY(grow(c, c->P, (size_t)c->n_pp + 1, "particle lists"));
+    BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
+    BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));
+    k_walk<true><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
+                                            c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
+                                            c->n_nodes, c->d_status);
+    BH_LAUNCH(c);
+    k_expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->cnt_p.p, c->P.p, c->begin.p, c->end.p,
+                                                             c->cnt_j.p, c->JJ.p);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+
+}  // namespace bh

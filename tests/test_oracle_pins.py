@@ -58,6 +58,7 @@ def test_sort_is_stable_permutation():
     rng = np.random.default_rng(1)
     k = rng.integers(0, 50, 5000).astype(np.uint64)  # many ties
     p = orc.sort_perm(k).astype(np.int64)
+    assert np.array_equal(p, orc.sort_perm_c(k))
     assert np.array_equal(np.sort(p), np.arange(len(k)))
     sk = k[p]
     assert np.all(sk[1:] >= sk[:-1])
