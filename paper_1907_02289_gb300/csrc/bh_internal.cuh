@@ -91,6 +91,8 @@ struct Ctx {
     DBuf<double> M, cx, cy, cz, Q;   // Q: 6 per node
     DBuf<float4> cell32;             // 3 per node: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz)
     DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
+    DBuf<unsigned long long> contacts;  // (i, j) contact candidates for the FP64 pass
+    int64_t n_contacts = 0;
 
     // groups
     int64_t n_groups = 0;

@@ -1,0 +1,641 @@
+// force32.cu -- the FP32 group-relative force kernel (Sec. 4.7: positions
+// and velocities shifted to an origin inside the group, then single
+// precision).  Origin: the centre of mass of the group node, taken from the
+// node's FP32 hi/lo record.
+//
+// Shift: every FP64 coordinate is split once per evaluation into FP32 hi/lo
+// parts; the shifted coordinate (x_hi - o_hi) + (x_lo - o_lo) is within one
+// FP32 rounding of the FP64-shifted value, so no FP64 arithmetic (1/64 of the
+// FP32 rate on this GPU) runs per list entry.
+//
+// Near pairs: the FP32 separation of two particles carries an absolute error
+// of ~2^-23 x (group extent), which matters only when they are much closer
+// than the group is wide.  Pairs closer than max(2 r_coll, 0.05 x group
+// extent) are masked out of the fast loop and queued per warp.  Queued pairs
+// are evaluated in batches (one pair per lane) from the hi/lo parts
+// directly, whose difference is exact to ~2^-48 (gravity), or -- when they
+// may be in contact -- appended to a global list that a separate kernel
+// evaluates in FP64 in the oracle's operation order (contact term of Eq. (1)
+// and the r <= r_coll decision).
+//
+// Summation: each lane keeps FP32 partial sums per tile (even and odd list
+// entries apart) and folds them after every tile into a compensated
+// (TwoSum) hi/lo accumulator in shared memory.
+//
+// Mapping: one warp per group.  A group of n_i = 32 R + t particles gives
+// every lane R full i-slots; the t remaining particles go to a "tail" slot
+// shared by J = 32 / T lanes (T = t rounded up to a power of two) that split
+// the list between them, so a 65-particle group costs 2 + 1/32 slots rather
+// than 3.  List entries are staged in pairs in shared memory and broadcast;
+// the pair (j, j+1) is evaluated with packed f32x2 instructions (FADD2,
+// FFMA2, FMUL2), which halves the issue slots per interaction.  The group's
+// own particles are evaluated first in a phase that excludes i = j; the
+// expanded list holds only the other particles.
+#include <cmath>
+
+#include "force_common.cuh"
+
+namespace bh {
+namespace {
+
+#ifndef BH_F32_MINB
+#define BH_F32_MINB 3  // resident blocks per SM the register budget is sized for
+#endif
+constexpr int kW32 = 4;      // warps per block
+constexpr int kTileJ = 128;  // list particles per tile (64 pairs)
+constexpr int kTileC = 64;   // list cells per tile (32 pairs)
+constexpr int kSlots = 4;    // i-slots per lane (full slots + tail)
+constexpr int kNearCap = 32 + 2 * kSlots * 32;
+
+struct JPair {  // two list particles, coordinates relative to the group origin
+    float2 x, y, z, m;
+};
+struct CPair {  // two cells: centre relative to the origin, mass, negated quadrupole
+    float2 x, y, z, m, qxx, qxy, qxz, qyy, qyz, qzz;
+};
+
+struct Smem32 {
+    union {
+        struct {
+            JPair jp[kTileJ / 2];
+            uint32_t jid[kTileJ];
+        } p;
+        CPair cp[kTileC / 2];
+    } t;
+    uint32_t near_i[kNearCap];
+    uint32_t near_j[kNearCap];
+    uint8_t near_s[kNearCap];
+    float nacc[32 * kSlots][3];  // near-pair accelerations (G included)
+    float ahi[32 * kSlots][3];   // compensated fast-loop sums (G-free), hi part
+    float alo[32 * kSlots][3];   // ... low part
+};
+
+struct Args {
+    int64_t ng;
+    const int32_t* groups;
+    const uint32_t* begin;
+    const uint32_t* end;
+    const int64_t* jj_off;
+    const uint32_t* JJ;
+    const int64_t* pc_off;
+    const int32_t* C;
+    const float4* phi;
+    const float4* plo;
+    const float4* cell32;
+    const WalkNode* wnode;
+    const double *x, *y, *z;
+    double *ax, *ay, *az;
+    uint2* contacts;              // (i, j) pairs for the FP64 contact pass
+    unsigned long long* ncontact; // its counter
+    int64_t contact_cap;
+    uint32_t n;
+    int64_t nn;
+    int* status;
+    ForceParams fp;
+    bool add_central;
+};
+
+__device__ __forceinline__ float rel(float hi, float lo, float ohi, float olo) {
+    return __fadd_rn(__fsub_rn(hi, ohi), __fsub_rn(lo, olo));
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Central mass, FP64: r^-1 from the FP32 estimate refined by two Newton
+// steps y <- y (3 - r2 y^2) / 2 (each roughly doubles the correct bits).
+__device__ __forceinline__ void central_newton(double G_Mc, double x, double y, double z, double* a) {
+    const double r2 = fma(x, x, fma(y, y, z * z));
+    double yv = (double)rsqrtf((float)r2);
+    yv = yv * fma(-0.5 * r2, yv * yv, 1.5);
+    yv = yv * fma(-0.5 * r2, yv * yv, 1.5);
+    const double f = -G_Mc * (yv * yv * yv);
+    a[0] = fma(f, x, a[0]);
+    a[1] = fma(f, y, a[1]);
+    a[2] = fma(f, z, a[2]);
+}
+
+// One near pair (i, j): gravity from the exact hi/lo difference, or hand the
+// pair to the FP64 contact pass.  Returns the acceleration in out (G included).
+__device__ __forceinline__ void near_pair(const Args& A, uint32_t i, uint32_t j, float* out, bool& contact) {
+    const ForceParams& fp = A.fp;
+    const float4 hi = A.phi[i], li = A.plo[i], hj = A.phi[j], lj = A.plo[j];
+    const float dx = __fadd_rn(__fsub_rn(hj.x, hi.x), __fsub_rn(lj.x, li.x));
+    const float dy = __fadd_rn(__fsub_rn(hj.y, hi.y), __fsub_rn(lj.y, li.y));
+    const float dz = __fadd_rn(__fsub_rn(hj.z, hi.z), __fsub_rn(lj.z, li.z));
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    contact = fp.rc2f > 0.f && !(r2 > fp.rc2f * 1.00001f);
+    if (contact || r2 == 0.f) {  // contact candidate (FP64 pass) or coincident (no force)
+        out[0] = out[1] = out[2] = 0.f;
+        return;
+    }
+    const float s2 = r2 + fp.eps2f;
+    const float rs = rsqrtf(s2);
+    const float f = fp.Gf * hj.w * (rs * rs * rs);
+    out[0] = f * dx;
+    out[1] = f * dy;
+    out[2] = f * dz;
+}
+
+__device__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
+    for (int base = 0; base < ncount; base += 32) {
+        const int u = base + lane;
+        bool contact = false;
+        uint32_t i = 0, j = 0;
+        if (u < ncount) {
+            const int s = S.near_s[u];
+            i = S.near_i[u];
+            j = S.near_j[u];
+            float a[3];
+            near_pair(A, i, j, a, contact);
+            if (!contact) {
+                atomicAdd(&S.nacc[s][0], a[0]);
+                atomicAdd(&S.nacc[s][1], a[1]);
+                atomicAdd(&S.nacc[s][2], a[2]);
+            }
+        }
+        const unsigned msk = __ballot_sync(0xffffffffu, contact);
+        if (msk) {
+            unsigned long long base_pos = 0;
+            if (lane == 0) base_pos = atomicAdd(A.ncontact, (unsigned long long)__popc(msk));
+            base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
+            if (contact) {
+                const unsigned long long pos = base_pos + __popc(msk & ((1u << lane) - 1u));
+                if ((int64_t)pos < A.contact_cap) A.contacts[pos] = make_uint2(i, j);
+            }
+        }
+    }
+    __syncwarp();
+    ncount = 0;
+}
+
+// Queue the near pairs of j-pair q (flags recomputed here; rare path).
+// Slots: full slot r holds particle i0 + 32 r + lane; the tail slot holds
+// i0 + 32 R + (lane % T) and sees the j-pairs q with q % J == lane / T.
+template <int NSLOT, bool SELF>
+__device__ __forceinline__ void queue_pair(const Args& A, Smem32& S, int& ncount, const JPair& P,
+                                           const uint32_t* jid, const float2* nx, const float2* ny,
+                                           const float2* nz, const uint32_t* iv, const bool* vl, const int* sidx,
+                                           float rnear2, int lane) {
+    const float2 eps2 = f2(A.fp.eps2f);
+    unsigned bits = 0;
+#pragma unroll
+    for (int r = 0; r < NSLOT; ++r) {
+        const float2 dx = __fadd2_rn(P.x, nx[r]), dy = __fadd2_rn(P.y, ny[r]), dz = __fadd2_rn(P.z, nz[r]);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+        if (vl[r] && r2.x < rnear2 && (!SELF || jid[0] != iv[r])) bits |= 1u << (2 * r);
+        if (vl[r] && r2.y < rnear2 && (!SELF || jid[1] != iv[r])) bits |= 2u << (2 * r);
+    }
+    const int c = __popc(bits);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    int pos = ncount + x - c;
+#pragma unroll
+    for (int r = 0; r < NSLOT; ++r)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (bits & (1u << (2 * r + h))) {
+                S.near_i[pos] = iv[r];
+                S.near_j[pos] = jid[h];
+                S.near_s[pos] = (uint8_t)sidx[r];
+                ++pos;
+            }
+    ncount += total;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void fold(Smem32& S, int s, float2& gx, float2& gy, float2& gz) {
+    const float t[3] = {__fadd_rn(gx.x, gx.y), __fadd_rn(gy.x, gy.y), __fadd_rn(gz.x, gz.y)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float hi = S.ahi[s][c];
+        const float s1 = __fadd_rn(hi, t[c]);
+        const float bp = __fsub_rn(s1, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t[c], bp));
+        S.ahi[s][c] = s1;
+        S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
+    }
+    gx = gy = gz = make_float2(0.f, 0.f);
+}
+
+// Fast particle-particle term for one slot and one j-pair; returns whether a
+// near pair was masked out (self excluded when SELF).
+template <bool SELF>
+__device__ __forceinline__ bool pp_body(const JPair& P, const uint32_t* jid, uint32_t i, float2 nx, float2 ny,
+                                        float2 nz, float2& gx, float2& gy, float2& gz, float2 eps2,
+                                        float rnear2) {
+    const float2 dx = __fadd2_rn(P.x, nx);
+    const float2 dy = __fadd2_rn(P.y, ny);
+    const float2 dz = __fadd2_rn(P.z, nz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), ri2);
+    const bool n0 = r2.x < rnear2, n1 = r2.y < rnear2;
+    f.x = n0 ? 0.f : f.x;
+    f.y = n1 ? 0.f : f.y;
+    gx = __ffma2_rn(f, dx, gx);
+    gy = __ffma2_rn(f, dy, gy);
+    gz = __ffma2_rn(f, dz, gz);
+    if (SELF) return (n0 && jid[0] != i) || (n1 && jid[1] != i);
+    return n0 || n1;
+}
+
+template <int ORDER>
+__device__ __forceinline__ void pc_body(const CPair& Cp, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
+                                        float2& gz, float2 eps2) {
+    const float2 dx = __fadd2_rn(Cp.x, nx);
+    const float2 dy = __fadd2_rn(Cp.y, ny);
+    const float2 dz = __fadd2_rn(Cp.z, nz);
+    const float2 R2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 ri3 = __fmul2_rn(ri, ri2);
+    if (ORDER >= 2) {
+        // q = -Q d, dqd = d.(-Q d); a += (M/R^3 + 5/2 (dQd)/R^7) d - Q d / R^5
+        const float2 qx = __ffma2_rn(Cp.qxx, dx, __ffma2_rn(Cp.qxy, dy, __fmul2_rn(Cp.qxz, dz)));
+        const float2 qy = __ffma2_rn(Cp.qxy, dx, __ffma2_rn(Cp.qyy, dy, __fmul2_rn(Cp.qyz, dz)));
+        const float2 qz = __ffma2_rn(Cp.qxz, dx, __ffma2_rn(Cp.qyz, dy, __fmul2_rn(Cp.qzz, dz)));
+        const float2 dqd = __ffma2_rn(dx, qx, __ffma2_rn(dy, qy, __fmul2_rn(dz, qz)));
+        const float2 ri5 = __fmul2_rn(ri3, ri2);
+        const float2 ri7 = __fmul2_rn(ri5, ri2);
+        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(Cp.m, ri3));
+        gx = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, gx));
+        gy = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, gy));
+        gz = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, gz));
+    } else {
+        const float2 s = __fmul2_rn(Cp.m, ri3);
+        gx = __ffma2_rn(s, dx, gx);
+        gy = __ffma2_rn(s, dy, gy);
+        gz = __ffma2_rn(s, dz, gz);
+    }
+}
+
+__device__ __forceinline__ void stage_particle(const Args& A, Smem32& S, int slot, uint32_t j, bool real,
+                                               const float (&oh)[3], const float (&ol)[3]) {
+    float px, py, pz, pm;
+    if (real) {
+        const float4 h = A.phi[j], l = A.plo[j];
+        px = rel(h.x, l.x, oh[0], ol[0]);
+        py = rel(h.y, l.y, oh[1], ol[1]);
+        pz = rel(h.z, l.z, oh[2], ol[2]);
+        pm = h.w;
+    } else {  // padding entry: far away, massless
+        px = py = pz = 1e15f;
+        pm = 0.f;
+        j = 0xffffffffu;
+    }
+    float* base = reinterpret_cast<float*>(&S.t.p.jp[slot >> 1]);
+    const int hh = slot & 1;
+    base[0 + hh] = px;
+    base[2 + hh] = py;
+    base[4 + hh] = pz;
+    base[6 + hh] = pm;
+    S.t.p.jid[slot] = j;
+}
+
+// Per-chunk state: R full slots (+1 tail slot when T > 0).
+template <int R>
+struct Chunk {
+    static constexpr int NS = R + 1;
+    float2 nx[NS], ny[NS], nz[NS], gx[NS], gy[NS], gz[NS];
+    uint32_t iv[NS];
+    bool vl[NS];
+    int sidx[NS];
+};
+
+template <int R, bool SELF>
+__device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R>& K, int npair, int T, int J, int tj,
+                                        float rnear2, int& ncount, int lane) {
+    const float2 eps2 = f2(A.fp.eps2f);
+    for (int q = 0; q < npair; ++q) {
+        const JPair P = S.t.p.jp[q];
+        const uint32_t* jid = &S.t.p.jid[2 * q];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            any |= pp_body<SELF>(P, jid, K.iv[r], K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2,
+                                 rnear2);
+        if (__any_sync(0xffffffffu, any))
+            queue_pair<R, SELF>(A, S, ncount, P, jid, K.nx, K.ny, K.nz, K.iv, K.vl, K.sidx, rnear2, lane);
+        if (ncount >= 32) flush_near(A, S, ncount, lane);
+    }
+    if (T > 0) {
+        const int trips = (npair + J - 1) / J;
+        for (int u = 0; u < trips; ++u) {
+            const int q = u * J + tj;
+            bool any = false;
+            JPair P;
+            const uint32_t* jid = &S.t.p.jid[0];
+            if (q < npair) {
+                P = S.t.p.jp[q];
+                jid = &S.t.p.jid[2 * q];
+                any = pp_body<SELF>(P, jid, K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2,
+                                    rnear2);
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                if (q >= npair) P = S.t.p.jp[0];
+                const float2 tnx[1] = {K.nx[R]}, tny[1] = {K.ny[R]}, tnz[1] = {K.nz[R]};
+                const uint32_t tiv[1] = {K.iv[R]};
+                const bool tvl[1] = {K.vl[R] && q < npair};
+                const int tsi[1] = {K.sidx[R]};
+                queue_pair<1, SELF>(A, S, ncount, P, jid, tnx, tny, tnz, tiv, tvl, tsi, rnear2, lane);
+            }
+            if (ncount >= 32) flush_near(A, S, ncount, lane);
+        }
+    }
+}
+
+template <int R, int ORDER>
+__device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R>& K, int npair, int T, int J, int tj) {
+    const float2 eps2 = f2(A.fp.eps2f);
+    for (int q = 0; q < npair; ++q) {
+        const CPair& Cp = S.t.cp[q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
+    }
+    if (T > 0)
+        for (int q = tj; q < npair; q += J)
+            pc_body<ORDER>(S.t.cp[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
+}
+
+template <int R>
+__device__ __forceinline__ void fold_all(Smem32& S, Chunk<R>& K, int T) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) fold(S, K.sidx[r], K.gx[r], K.gy[r], K.gz[r]);
+    if (T > 0) fold(S, K.sidx[R], K.gx[R], K.gy[R], K.gz[R]);
+}
+
+template <int R, int ORDER>
+__device__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e, uint32_t i0, int T,
+                            const float (&oh)[3], const float (&ol)[3], float rnear2, int lane) {
+    Chunk<R> K;
+    const int J = T > 0 ? 32 / T : 1;
+    const int ti = T > 0 ? lane % T : 0, tj = T > 0 ? lane / T : 0;
+#pragma unroll
+    for (int r = 0; r < R + 1; ++r) {
+        const bool tail = (r == R);
+        const uint32_t i = tail ? i0 + 32 * R + ti : i0 + 32 * r + lane;
+        K.vl[r] = tail ? (T > 0 && i < e) : (i < e);
+        K.iv[r] = K.vl[r] ? i : b;
+        K.sidx[r] = 32 * r + lane;
+        const float4 h = A.phi[K.iv[r]], l = A.plo[K.iv[r]];
+        K.nx[r] = f2(-rel(h.x, l.x, oh[0], ol[0]));
+        K.ny[r] = f2(-rel(h.y, l.y, oh[1], ol[1]));
+        K.nz[r] = f2(-rel(h.z, l.z, oh[2], ol[2]));
+        K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
+        if (!tail || T > 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) S.nacc[K.sidx[r]][c] = S.ahi[K.sidx[r]][c] = S.alo[K.sidx[r]][c] = 0.f;
+    }
+    int ncount = 0;
+    __syncwarp();
+
+    // (1) the group's own particles, i = j excluded
+    for (uint32_t t0 = b; t0 < e; t0 += kTileJ) {
+        const int nt = (int)min((uint32_t)kTileJ, e - t0);
+        const int npair = (nt + 1) >> 1;
+#pragma unroll
+        for (int s = 0; s < kTileJ / 32; ++s) {
+            const int u = lane + 32 * s;
+            if (u < 2 * npair) stage_particle(A, S, u, t0 + u, u < nt, oh, ol);
+        }
+        __syncwarp();
+        pp_tile<R, true>(A, S, K, npair, T, J, tj, rnear2, ncount, lane);
+        fold_all<R>(S, K, T);
+        __syncwarp();
+    }
+    // (2) the other list particles
+    const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
+    for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
+        const int nt = (int)min((int64_t)kTileJ, j1 - t0);
+        const int npair = (nt + 1) >> 1;
+#pragma unroll
+        for (int s = 0; s < kTileJ / 32; ++s) {
+            const int u = lane + 32 * s;
+            if (u < 2 * npair) {
+                uint32_t j = 0;
+                if (u < nt) {
+                    j = A.JJ[t0 + u];
+                    if (j >= A.n) {
+                        atomicOr(A.status, kStatBounds);
+                        j = b;
+                    }
+                }
+                stage_particle(A, S, u, j, u < nt, oh, ol);
+            }
+        }
+        __syncwarp();
+        pp_tile<R, false>(A, S, K, npair, T, J, tj, rnear2, ncount, lane);
+        fold_all<R>(S, K, T);
+        __syncwarp();
+    }
+    if (ncount > 0) flush_near(A, S, ncount, lane);
+    // (3) list cells
+    const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
+    for (int64_t t0 = c0; t0 < c1; t0 += kTileC) {
+        const int nt = (int)min((int64_t)kTileC, c1 - t0);
+        const int npair = (nt + 1) >> 1;
+#pragma unroll
+        for (int s = 0; s < kTileC / 32; ++s) {
+            const int u = lane + 32 * s;
+            if (u < 2 * npair) {
+                float v[10];
+                if (u < nt) {
+                    int32_t cc = A.C[t0 + u];
+                    if (cc < 0 || cc >= A.nn) {
+                        atomicOr(A.status, kStatBounds);
+                        cc = 0;
+                    }
+                    const float4 r0 = A.cell32[3 * (int64_t)cc], r1 = A.cell32[3 * (int64_t)cc + 1];
+                    v[0] = rel(r0.x, r1.x, oh[0], ol[0]);
+                    v[1] = rel(r0.y, r1.y, oh[1], ol[1]);
+                    v[2] = rel(r0.z, r1.z, oh[2], ol[2]);
+                    v[3] = r0.w;
+                    if (ORDER >= 2) {
+                        const float4 r2v = A.cell32[3 * (int64_t)cc + 2];  // Qxy, Qxz, Qyy, Qyz
+                        v[4] = -r1.w;
+                        v[5] = -r2v.x;
+                        v[6] = -r2v.y;
+                        v[7] = -r2v.z;
+                        v[8] = -r2v.w;
+                        v[9] = r1.w + r2v.z;  // -Qzz = Qxx + Qyy (traceless)
+                    }
+                } else {
+                    v[0] = v[1] = v[2] = 1e15f;
+                    v[3] = 0.f;
+#pragma unroll
+                    for (int a = 4; a < 10; ++a) v[a] = 0.f;
+                }
+                float* base = reinterpret_cast<float*>(&S.t.cp[u >> 1]);
+                const int hh = u & 1;
+#pragma unroll
+                for (int a = 0; a < (ORDER >= 2 ? 10 : 4); ++a) base[2 * a + hh] = v[a];
+            }
+        }
+        __syncwarp();
+        pc_tile<R, ORDER>(A, S, K, npair, T, J, tj);
+        fold_all<R>(S, K, T);
+        __syncwarp();
+    }
+    __syncwarp();
+    // (4) outputs: full slots directly, the tail slot after a reduction over its J lanes
+#pragma unroll
+    for (int r = 0; r < R + 1; ++r) {
+        const bool tail = (r == R);
+        if (tail && T == 0) break;
+        const int s = K.sidx[r];
+        double a[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]) + (double)S.nacc[s][c];
+        if (tail)
+            for (int o = T; o < 32; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+        if (K.vl[r] && (!tail || tj == 0)) {
+            const uint32_t i = K.iv[r];
+            if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
+            A.ax[i] = a[0];
+            A.ay[i] = a[1];
+            A.az[i] = a[2];
+        }
+    }
+    __syncwarp();
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem32* sm = reinterpret_cast<Smem32*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * kW32 + w;
+    if (k >= A.ng) return;
+    Smem32& S = sm[w];
+    const int32_t g = A.groups[k];
+    const uint32_t b = A.begin[g], e = A.end[g];
+    // origin: the group node's centre of mass as an FP32 hi/lo pair
+    const float4 o0 = A.cell32[3 * (int64_t)g], o1 = A.cell32[3 * (int64_t)g + 1];
+    const float oh[3] = {o0.x, o0.y, o0.z}, ol[3] = {o1.x, o1.y, o1.z};
+    // group extent from its integer box -> near-pair radius
+    const WalkNode G = A.wnode[g];
+    const uint32_t ext = max(G.b.x - G.a.x, max(G.b.y - G.a.y, G.b.z - G.a.z)) + 1u;
+    const float rn = A.fp.near_frac * (float)ext * A.fp.h;
+    const float rnear2 = fmaxf(A.fp.rnear_min2, rn * rn) + A.fp.eps2f;
+    for (uint32_t i0 = b; i0 < e; i0 += 32 * kSlots) {
+        const uint32_t cnt = min((uint32_t)(32 * kSlots), e - i0);
+        int R = (int)(cnt >> 5), t = (int)(cnt & 31), T = 0;
+        if (t > 16) {
+            ++R;  // more than half a slot left: a full slot
+        } else if (t > 0) {
+            T = 1;
+            while (T < t) T <<= 1;
+        }
+        switch (R) {
+            case 0: group_chunk<0, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
+            case 1: group_chunk<1, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
+            case 2: group_chunk<2, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
+            case 3: group_chunk<3, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
+            default: group_chunk<4, ORDER>(A, S, k, b, e, i0, 0, oh, ol, rnear2, lane); break;
+        }
+    }
+}
+
+// FP64 pass over the contact candidates: Eq. (1) in the oracle's operation
+// order (gravity at r_coll + spring + dashpot, or plain gravity if the FP64
+// decision says r > r_coll), added to the acceleration of i.
+__global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
+                             int64_t cap, ForceParams fp, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ z,
+                             const double* __restrict__ vx, const double* __restrict__ vy,
+                             const double* __restrict__ vz, const double* __restrict__ m, double* ax, double* ay,
+                             double* az) {
+    int64_t np = (int64_t)*count;
+    if (np > cap) np = cap;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 pr = pairs[u];
+        const uint32_t i = pr.x, j = pr.y;
+        double a[3] = {0.0, 0.0, 0.0};
+        exact_pair64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j], vz[j], m[j], a);
+        atomicAdd(&ax[i], a[0]);
+        atomicAdd(&ay[i], a[1]);
+        atomicAdd(&az[i], a[2]);
+    }
+}
+
+}  // namespace
+
+int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_central) {
+    Args A;
+    A.ng = c->n_groups;
+    A.groups = c->groups.p;
+    A.begin = c->begin.p;
+    A.end = c->end.p;
+    A.jj_off = c->cnt_j.p;
+    A.JJ = c->JJ.p;
+    A.pc_off = c->cnt_c.p;
+    A.C = c->C.p;
+    A.phi = c->phi.p;
+    A.plo = c->plo.p;
+    A.cell32 = c->cell32.p;
+    A.wnode = c->wnode.p;
+    A.x = p->x;
+    A.y = p->y;
+    A.z = p->z;
+    A.ax = p->ax;
+    A.ay = p->ay;
+    A.az = p->az;
+    const int64_t cap = c->n > 65536 ? c->n : 65536;
+    if (c->contacts.cap < (size_t)cap) BH_TRY(grow(c, c->contacts, (size_t)cap, "contact pairs"));
+    A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
+    A.contact_cap = (int64_t)c->contacts.cap;
+    A.ncontact = c->d_small + 16;
+    BH_CUDA(c, cudaMemsetAsync(A.ncontact, 0, sizeof(unsigned long long), c->stream));
+    A.n = (uint32_t)c->n;
+    A.nn = c->n_nodes;
+    A.status = c->d_status;
+    A.fp = fp;
+    A.add_central = add_central;
+    const unsigned nb = blocks_for(A.ng, kW32);
+    const int smem = (int)(kW32 * sizeof(Smem32));
+    static bool attr = false;
+    if (!attr) {
+        BH_CUDA(c, cudaFuncSetAttribute(k_force32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        BH_CUDA(c, cudaFuncSetAttribute(k_force32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (c->prm.order >= 2)
+            k_force32<2><<<nb, 32 * kW32, smem, c->stream>>>(A);
+        else
+            k_force32<1><<<nb, 32 * kW32, smem, c->stream>>>(A);
+        BH_LAUNCH(c);
+        if (!(c->prm.r_coll > 0.0)) break;
+        // size the FP64 contact pass (one read-back per evaluation); on overflow
+        // grow the list and evaluate again
+        unsigned long long np = 0;
+        BH_CUDA(c, cudaMemcpyAsync(&np, A.ncontact, sizeof(np), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->n_contacts = (int64_t)np;
+        if ((int64_t)np > A.contact_cap) {
+            BH_TRY(grow(c, c->contacts, (size_t)(np + np / 4 + 1024), "contact pairs"));
+            A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
+            A.contact_cap = (int64_t)c->contacts.cap;
+            BH_CUDA(c, cudaMemsetAsync(A.ncontact, 0, sizeof(unsigned long long), c->stream));
+            continue;
+        }
+        if (np > 0) {
+            k_contacts64<<<blocks_for((int64_t)np, 128), 128, 0, c->stream>>>(
+                A.contacts, A.ncontact, A.contact_cap, fp, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->ax,
+                p->ay, p->az);
+            BH_LAUNCH(c);
+        }
+        break;
+    }
+    return BH_OK;
+}
+
+}  // namespace bh

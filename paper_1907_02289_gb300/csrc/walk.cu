@@ -35,10 +35,11 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                                               int64_t nn, int* status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < ng;
-    int64_t np = 0, nc = 0, nj = 0, ni = 0;
+    int64_t np = 0, nc = 0, nj = 0, ni = 0, nown = 0;
     if (active) {
         const int32_t g = groups[k];
         const WalkNode G = wn[g];
+        const uint32_t gb = begin[g], ge = end[g];
         const int glo0 = (int)G.a.x, glo1 = (int)G.a.y, glo2 = (int)G.a.z;
         const int ghi0 = (int)G.b.x, ghi1 = (int)G.b.y, ghi2 = (int)G.b.z;
         ni = (int64_t)(end[g] - begin[g]);
@@ -62,7 +63,11 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                 if (nch == 0) {
                     if (FILL) P[pbase + np] = node;
                     ++np;
-                    nj += (int64_t)(end[node] - begin[node]);
+                    const uint32_t lb = begin[node];
+                    if (lb >= gb && lb < ge)
+                        nown += (int64_t)(end[node] - lb);  // the group's own particles
+                    else
+                        nj += (int64_t)(end[node] - lb);
                 } else {
                     sn[sp] = (int)R.b.w;
                     se[sp] = (int)R.b.w + nch;
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
     }
     if (!FILL) {
         // interaction counts: n_i * (list particles) and n_i * (list cells)
-        unsigned long long ipp = (unsigned long long)(ni * nj), ipc = (unsigned long long)(ni * nc);
+        unsigned long long ipp = (unsigned long long)(ni * (nj + nown)), ipc = (unsigned long long)(ni * nc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
@@ -101,13 +106,18 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
     }
 }
 
-// One warp per group: particle entries -> particle indices.
-__global__ void k_expand(int64_t ng, const int64_t* __restrict__ pp_off, const int32_t* __restrict__ P,
-                         const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end,
-                         const int64_t* __restrict__ jj_off, uint32_t* __restrict__ JJ) {
+// One warp per group: particle entries -> particle indices, leaving out the
+// group's own particles (the force kernels evaluate those in a separate phase
+// that excludes i = j).
+__global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const int64_t* __restrict__ pp_off,
+                         const int32_t* __restrict__ P, const uint32_t* __restrict__ begin,
+                         const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
+                         uint32_t* __restrict__ JJ) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= ng) return;
+    const int32_t g = groups[k];
+    const uint32_t gb = begin[g], ge = end[g];
     const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
     int64_t jo = jj_off[k];
     for (int64_t e = e0; e < e1; e += 32) {
@@ -115,7 +125,7 @@ __global__ void k_expand(int64_t ng, const int64_t* __restrict__ pp_off, const i
         if (e + lane < e1) {
             const int32_t leaf = P[e + lane];
             b = begin[leaf];
-            cnt = end[leaf] - b;
+            cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
         }
         uint32_t x = cnt;
 #pragma unroll
@@ -197,8 +207,8 @@ int stage_lists(Ctx* c) {
                                             c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
                                             c->n_nodes, c->d_status);
     BH_LAUNCH(c);
-    k_expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->cnt_p.p, c->P.p, c->begin.p, c->end.p,
-                                                             c->cnt_j.p, c->JJ.p);
+    k_expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p,
+                                                             c->end.p, c->cnt_j.p, c->JJ.p);
     BH_LAUNCH(c);
     return BH_OK;
 }
