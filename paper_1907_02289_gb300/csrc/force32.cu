@@ -1,7 +1,7 @@
 // force32.cu -- the FP32 group-relative force kernel (Sec. 4.7: positions
-// and velocities shifted to an origin inside the group, then single
-// precision).  Origin: the centre of mass of the group node, taken from the
-// node's FP32 hi/lo record.
+// shifted to an origin inside the group, then single precision).  Origin:
+// the centre of mass of the group node, taken from the node's FP32 hi/lo
+// record.
 //
 // Shift: every FP64 coordinate is split once per evaluation into FP32 hi/lo
 // parts; the shifted coordinate (x_hi - o_hi) + (x_lo - o_lo) is within one
@@ -18,19 +18,20 @@
 // evaluates in FP64 in the oracle's operation order (contact term of Eq. (1)
 // and the r <= r_coll decision).
 //
-// Summation: each lane keeps FP32 partial sums per tile (even and odd list
-// entries apart) and folds them after every tile into a compensated
-// (TwoSum) hi/lo accumulator in shared memory.
+// Summation: FP32 partial sums per tile, folded after every tile into a
+// compensated (TwoSum) hi/lo accumulator in shared memory.
 //
-// Mapping: one warp per group.  A group of n_i = 32 R + t particles gives
-// every lane R full i-slots; the t remaining particles go to a "tail" slot
-// shared by J = 32 / T lanes (T = t rounded up to a power of two) that split
-// the list between them, so a 65-particle group costs 2 + 1/32 slots rather
-// than 3.  List entries are staged in pairs in shared memory and broadcast;
-// the pair (j, j+1) is evaluated with packed f32x2 instructions (FADD2,
-// FFMA2, FMUL2), which halves the issue slots per interaction.  The group's
-// own particles are evaluated first in a phase that excludes i = j; the
-// expanded list holds only the other particles.
+// Mapping: one warp per group.  Every lane holds its i-particles in pairs,
+// (x_i, x_i') in one f32x2 register, and each list entry is broadcast from
+// shared memory as (x_j, x_j); one packed FADD2/FFMA2/FMUL2 then serves two
+// interactions.  A group of n_i = 64 R + t particles gives every lane R full
+// pair-slots; the t remaining particles go to a "tail" pair-slot held by
+// T lanes (T = ceil(t/2) rounded up to a power of two) that split the list
+// J = 32/T ways, so a 65-particle group costs 1 + 1/32 slots rather than 2.
+// List tiles are gathered one tile ahead (indices two tiles ahead) so that
+// the gathers overlap the arithmetic.  The group's own particles are
+// evaluated first in a phase that excludes i = j; the expanded list holds
+// only the other particles.
 #include <cmath>
 
 #include "force_common.cuh"
@@ -39,35 +40,35 @@ namespace bh {
 namespace {
 
 #ifndef BH_F32_MINB
-#define BH_F32_MINB 3  // resident blocks per SM the register budget is sized for
+#define BH_F32_MINB 4  // resident blocks per SM the register budget is sized for
 #endif
-constexpr int kW32 = 4;      // warps per block
-constexpr int kTileJ = 128;  // list particles per tile (64 pairs)
-constexpr int kTileC = 64;   // list cells per tile (32 pairs)
-constexpr int kSlots = 4;    // i-slots per lane (full slots + tail)
-constexpr int kNearCap = 32 + 2 * kSlots * 32;
+constexpr int kW32 = 4;       // warps per block
+constexpr int kTileJ = 64;    // list particles per tile (2 per lane)
+constexpr int kTileC = 32;    // list cells per tile (1 per lane)
+constexpr int kPS = 2;        // pair-slots per lane (full + tail)
+constexpr int kNearCap = 32 + 2 * kPS * 32;
+constexpr int kPSlots = 64 * kPS;  // particle slots per warp
 
-struct JPair {  // two list particles, coordinates relative to the group origin
+struct JEnt {  // one list particle, each value duplicated for the packed ops
     float2 x, y, z, m;
 };
-struct CPair {  // two cells: centre relative to the origin, mass, negated quadrupole
+struct CEnt {  // one cell: centre, mass, negated traceless quadrupole (duplicated)
     float2 x, y, z, m, qxx, qxy, qxz, qyy, qyz, qzz;
 };
 
 struct Smem32 {
     union {
         struct {
-            JPair jp[kTileJ / 2];
-            uint32_t jid[kTileJ];
+            JEnt e[kTileJ];
+            uint32_t id[kTileJ];
         } p;
-        CPair cp[kTileC / 2];
+        CEnt c[kTileC];
     } t;
     uint32_t near_i[kNearCap];
     uint32_t near_j[kNearCap];
     uint8_t near_s[kNearCap];
-    float nacc[32 * kSlots][3];  // near-pair accelerations (G included)
-    float ahi[32 * kSlots][3];   // compensated fast-loop sums (G-free), hi part
-    float alo[32 * kSlots][3];   // ... low part
+    float ahi[kPSlots][3];  // compensated fast-loop sums (G-free), hi part
+    float alo[kPSlots][3];  // low part; G-free near-pair results are added here too
 };
 
 struct Args {
@@ -85,8 +86,8 @@ struct Args {
     const WalkNode* wnode;
     const double *x, *y, *z;
     double *ax, *ay, *az;
-    uint2* contacts;              // (i, j) pairs for the FP64 contact pass
-    unsigned long long* ncontact; // its counter
+    uint2* contacts;               // (i, j) pairs for the FP64 contact pass
+    unsigned long long* ncontact;  // its counter
     int64_t contact_cap;
     uint32_t n;
     int64_t nn;
@@ -113,8 +114,22 @@ __device__ __forceinline__ void central_newton(double G_Mc, double x, double y, 
     a[2] = fma(f, z, a[2]);
 }
 
-// One near pair (i, j): gravity from the exact hi/lo difference, or hand the
-// pair to the FP64 contact pass.  Returns the acceleration in out (G included).
+// ---- per-chunk state ------------------------------------------------------
+// Pair-slot r (r < R): lane holds particles p0 = i0 + 64 r + lane and
+// p1 = p0 + 32.  Tail pair-slot (r == R): lane holds i0 + 64 R + (lane % T)
+// and that + T, and sees only list entries q with q % J == lane / T.
+template <int R>
+struct Chunk {
+    static constexpr int NS = R + 1;
+    float2 nx[NS], ny[NS], nz[NS], gx[NS], gy[NS], gz[NS];
+    uint32_t i0v[NS], i1v[NS];
+    bool v0[NS], v1[NS];
+    int s0[NS], s1[NS];  // particle-slot indices (shared-memory accumulators)
+};
+
+// ---- near pairs ------------------------------------------------------------
+// Gravity from the exact hi/lo difference (G-free), or hand the pair to the
+// FP64 contact pass.
 __device__ __forceinline__ void near_pair(const Args& A, uint32_t i, uint32_t j, float* out, bool& contact) {
     const ForceParams& fp = A.fp;
     const float4 hi = A.phi[i], li = A.plo[i], hj = A.phi[j], lj = A.plo[j];
@@ -129,13 +144,13 @@ __device__ __forceinline__ void near_pair(const Args& A, uint32_t i, uint32_t j,
     }
     const float s2 = r2 + fp.eps2f;
     const float rs = rsqrtf(s2);
-    const float f = fp.Gf * hj.w * (rs * rs * rs);
+    const float f = hj.w * (rs * rs * rs);
     out[0] = f * dx;
     out[1] = f * dy;
     out[2] = f * dz;
 }
 
-__device__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
+__device__ __forceinline__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
     for (int base = 0; base < ncount; base += 32) {
         const int u = base + lane;
         bool contact = false;
@@ -147,9 +162,9 @@ __device__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
             float a[3];
             near_pair(A, i, j, a, contact);
             if (!contact) {
-                atomicAdd(&S.nacc[s][0], a[0]);
-                atomicAdd(&S.nacc[s][1], a[1]);
-                atomicAdd(&S.nacc[s][2], a[2]);
+                atomicAdd(&S.alo[s][0], a[0]);
+                atomicAdd(&S.alo[s][1], a[1]);
+                atomicAdd(&S.alo[s][2], a[2]);
             }
         }
         const unsigned msk = __ballot_sync(0xffffffffu, contact);
@@ -167,22 +182,20 @@ __device__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
     ncount = 0;
 }
 
-// Queue the near pairs of j-pair q (flags recomputed here; rare path).
-// Slots: full slot r holds particle i0 + 32 r + lane; the tail slot holds
-// i0 + 32 R + (lane % T) and sees the j-pairs q with q % J == lane / T.
-template <int NSLOT, bool SELF>
-__device__ __forceinline__ void queue_pair(const Args& A, Smem32& S, int& ncount, const JPair& P,
-                                           const uint32_t* jid, const float2* nx, const float2* ny,
-                                           const float2* nz, const uint32_t* iv, const bool* vl, const int* sidx,
-                                           float rnear2, int lane) {
-    const float2 eps2 = f2(A.fp.eps2f);
+// Queue the near pairs of list entry E (flags recomputed here; rare path)
+// for pair-slots [r0, r1).  Warp-uniform call.
+template <bool SELF, int R>
+__device__ __forceinline__ void queue_entry(Smem32& S, int& ncount, const JEnt& E, uint32_t jid, const Chunk<R>& K,
+                                            int r0, int r1, bool tail_ok, float2 eps2, float rnear2, int lane) {
     unsigned bits = 0;
 #pragma unroll
-    for (int r = 0; r < NSLOT; ++r) {
-        const float2 dx = __fadd2_rn(P.x, nx[r]), dy = __fadd2_rn(P.y, ny[r]), dz = __fadd2_rn(P.z, nz[r]);
+    for (int r = 0; r < R + 1; ++r) {
+        if (r < r0 || r >= r1) continue;
+        const bool ok = (r < R) || tail_ok;
+        const float2 dx = __fadd2_rn(E.x, K.nx[r]), dy = __fadd2_rn(E.y, K.ny[r]), dz = __fadd2_rn(E.z, K.nz[r]);
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
-        if (vl[r] && r2.x < rnear2 && (!SELF || jid[0] != iv[r])) bits |= 1u << (2 * r);
-        if (vl[r] && r2.y < rnear2 && (!SELF || jid[1] != iv[r])) bits |= 2u << (2 * r);
+        if (ok && K.v0[r] && r2.x < rnear2 && (!SELF || jid != K.i0v[r])) bits |= 1u << (2 * r);
+        if (ok && K.v1[r] && r2.y < rnear2 && (!SELF || jid != K.i1v[r])) bits |= 2u << (2 * r);
     }
     const int c = __popc(bits);
     int x = c;
@@ -194,179 +207,216 @@ __device__ __forceinline__ void queue_pair(const Args& A, Smem32& S, int& ncount
     const int total = __shfl_sync(0xffffffffu, x, 31);
     int pos = ncount + x - c;
 #pragma unroll
-    for (int r = 0; r < NSLOT; ++r)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (bits & (1u << (2 * r + h))) {
-                S.near_i[pos] = iv[r];
-                S.near_j[pos] = jid[h];
-                S.near_s[pos] = (uint8_t)sidx[r];
-                ++pos;
-            }
+    for (int r = 0; r < R + 1; ++r) {
+        if (bits & (1u << (2 * r))) {
+            S.near_i[pos] = K.i0v[r];
+            S.near_j[pos] = jid;
+            S.near_s[pos] = (uint8_t)K.s0[r];
+            ++pos;
+        }
+        if (bits & (2u << (2 * r))) {
+            S.near_i[pos] = K.i1v[r];
+            S.near_j[pos] = jid;
+            S.near_s[pos] = (uint8_t)K.s1[r];
+            ++pos;
+        }
+    }
     ncount += total;
     __syncwarp();
 }
 
-__device__ __forceinline__ void fold(Smem32& S, int s, float2& gx, float2& gy, float2& gz) {
-    const float t[3] = {__fadd_rn(gx.x, gx.y), __fadd_rn(gy.x, gy.y), __fadd_rn(gz.x, gz.y)};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float hi = S.ahi[s][c];
-        const float s1 = __fadd_rn(hi, t[c]);
-        const float bp = __fsub_rn(s1, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t[c], bp));
-        S.ahi[s][c] = s1;
-        S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
-    }
-    gx = gy = gz = make_float2(0.f, 0.f);
-}
-
-// Fast particle-particle term for one slot and one j-pair; returns whether a
-// near pair was masked out (self excluded when SELF).
+// ---- interaction bodies ------------------------------------------------------
+// Fast particle-particle term of one list entry for one pair-slot; returns
+// whether a near pair was masked out (self excluded when SELF).
 template <bool SELF>
-__device__ __forceinline__ bool pp_body(const JPair& P, const uint32_t* jid, uint32_t i, float2 nx, float2 ny,
-                                        float2 nz, float2& gx, float2& gy, float2& gz, float2 eps2,
+__device__ __forceinline__ bool pp_body(const JEnt& E, uint32_t jid, float2 nx, float2 ny, float2 nz, float2& gx,
+                                        float2& gy, float2& gz, uint32_t i0, uint32_t i1, float2 eps2,
                                         float rnear2) {
-    const float2 dx = __fadd2_rn(P.x, nx);
-    const float2 dy = __fadd2_rn(P.y, ny);
-    const float2 dz = __fadd2_rn(P.z, nz);
+    const float2 dx = __fadd2_rn(E.x, nx);
+    const float2 dy = __fadd2_rn(E.y, ny);
+    const float2 dz = __fadd2_rn(E.z, nz);
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
     const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
     const float2 ri2 = __fmul2_rn(ri, ri);
-    float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), ri2);
+    float2 f = __fmul2_rn(__fmul2_rn(E.m, ri), ri2);
     const bool n0 = r2.x < rnear2, n1 = r2.y < rnear2;
     f.x = n0 ? 0.f : f.x;
     f.y = n1 ? 0.f : f.y;
     gx = __ffma2_rn(f, dx, gx);
     gy = __ffma2_rn(f, dy, gy);
     gz = __ffma2_rn(f, dz, gz);
-    if (SELF) return (n0 && jid[0] != i) || (n1 && jid[1] != i);
+    if (SELF) return (n0 && jid != i0) || (n1 && jid != i1);
     return n0 || n1;
 }
 
 template <int ORDER>
-__device__ __forceinline__ void pc_body(const CPair& Cp, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
+__device__ __forceinline__ void pc_body(const CEnt& E, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
                                         float2& gz, float2 eps2) {
-    const float2 dx = __fadd2_rn(Cp.x, nx);
-    const float2 dy = __fadd2_rn(Cp.y, ny);
-    const float2 dz = __fadd2_rn(Cp.z, nz);
+    const float2 dx = __fadd2_rn(E.x, nx);
+    const float2 dy = __fadd2_rn(E.y, ny);
+    const float2 dz = __fadd2_rn(E.z, nz);
     const float2 R2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
     const float2 ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
     const float2 ri2 = __fmul2_rn(ri, ri);
     const float2 ri3 = __fmul2_rn(ri, ri2);
     if (ORDER >= 2) {
         // q = -Q d, dqd = d.(-Q d); a += (M/R^3 + 5/2 (dQd)/R^7) d - Q d / R^5
-        const float2 qx = __ffma2_rn(Cp.qxx, dx, __ffma2_rn(Cp.qxy, dy, __fmul2_rn(Cp.qxz, dz)));
-        const float2 qy = __ffma2_rn(Cp.qxy, dx, __ffma2_rn(Cp.qyy, dy, __fmul2_rn(Cp.qyz, dz)));
-        const float2 qz = __ffma2_rn(Cp.qxz, dx, __ffma2_rn(Cp.qyz, dy, __fmul2_rn(Cp.qzz, dz)));
+        const float2 qx = __ffma2_rn(E.qxx, dx, __ffma2_rn(E.qxy, dy, __fmul2_rn(E.qxz, dz)));
+        const float2 qy = __ffma2_rn(E.qxy, dx, __ffma2_rn(E.qyy, dy, __fmul2_rn(E.qyz, dz)));
+        const float2 qz = __ffma2_rn(E.qxz, dx, __ffma2_rn(E.qyz, dy, __fmul2_rn(E.qzz, dz)));
         const float2 dqd = __ffma2_rn(dx, qx, __ffma2_rn(dy, qy, __fmul2_rn(dz, qz)));
         const float2 ri5 = __fmul2_rn(ri3, ri2);
         const float2 ri7 = __fmul2_rn(ri5, ri2);
-        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(Cp.m, ri3));
+        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(E.m, ri3));
         gx = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, gx));
         gy = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, gy));
         gz = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, gz));
     } else {
-        const float2 s = __fmul2_rn(Cp.m, ri3);
+        const float2 s = __fmul2_rn(E.m, ri3);
         gx = __ffma2_rn(s, dx, gx);
         gy = __ffma2_rn(s, dy, gy);
         gz = __ffma2_rn(s, dz, gz);
     }
 }
 
-__device__ __forceinline__ void stage_particle(const Args& A, Smem32& S, int slot, uint32_t j, bool real,
-                                               const float (&oh)[3], const float (&ol)[3]) {
-    float px, py, pz, pm;
-    if (real) {
-        const float4 h = A.phi[j], l = A.plo[j];
-        px = rel(h.x, l.x, oh[0], ol[0]);
-        py = rel(h.y, l.y, oh[1], ol[1]);
-        pz = rel(h.z, l.z, oh[2], ol[2]);
-        pm = h.w;
-    } else {  // padding entry: far away, massless
-        px = py = pz = 1e15f;
-        pm = 0.f;
-        j = 0xffffffffu;
-    }
-    float* base = reinterpret_cast<float*>(&S.t.p.jp[slot >> 1]);
-    const int hh = slot & 1;
-    base[0 + hh] = px;
-    base[2 + hh] = py;
-    base[4 + hh] = pz;
-    base[6 + hh] = pm;
-    S.t.p.jid[slot] = j;
+__device__ __forceinline__ void fold1(Smem32& S, int s, float t, int c) {
+    const float hi = S.ahi[s][c];
+    const float s1 = __fadd_rn(hi, t);
+    const float bp = __fsub_rn(s1, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t, bp));
+    S.ahi[s][c] = s1;
+    S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
 }
 
-// Per-chunk state: R full slots (+1 tail slot when T > 0).
 template <int R>
-struct Chunk {
-    static constexpr int NS = R + 1;
-    float2 nx[NS], ny[NS], nz[NS], gx[NS], gy[NS], gz[NS];
-    uint32_t iv[NS];
-    bool vl[NS];
-    int sidx[NS];
+__device__ __forceinline__ void fold_all(Smem32& S, Chunk<R>& K, int T) {
+#pragma unroll
+    for (int r = 0; r < R + 1; ++r) {
+        if (r == R && T == 0) break;
+        fold1(S, K.s0[r], K.gx[r].x, 0);
+        fold1(S, K.s0[r], K.gy[r].x, 1);
+        fold1(S, K.s0[r], K.gz[r].x, 2);
+        fold1(S, K.s1[r], K.gx[r].y, 0);
+        fold1(S, K.s1[r], K.gy[r].y, 1);
+        fold1(S, K.s1[r], K.gz[r].y, 2);
+        K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
+    }
+}
+
+// ---- tiles -------------------------------------------------------------------
+// Gathered raw data of one particle entry (prefetched into registers).
+struct PRaw {
+    float4 h, l;
+    uint32_t j;
 };
 
+__device__ __forceinline__ void put_particle(Smem32& S, int u, const PRaw& P, bool real, const float (&oh)[3],
+                                             const float (&ol)[3]) {
+    JEnt E;
+    if (real) {
+        E.x = f2(rel(P.h.x, P.l.x, oh[0], ol[0]));
+        E.y = f2(rel(P.h.y, P.l.y, oh[1], ol[1]));
+        E.z = f2(rel(P.h.z, P.l.z, oh[2], ol[2]));
+        E.m = f2(P.h.w);
+    } else {  // padding entry: far away, massless
+        E.x = E.y = E.z = f2(1e15f);
+        E.m = f2(0.f);
+    }
+    S.t.p.e[u] = E;
+    S.t.p.id[u] = real ? P.j : 0xffffffffu;
+}
+
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t list_index(const Args& A, int64_t p, int64_t j1, uint32_t fallback) {
+    if (p >= j1) return kNone;
+    uint32_t j = A.JJ[p];
+    if (j >= A.n) {
+        atomicOr(A.status, kStatBounds);
+        j = fallback;
+    }
+    return j;
+}
+
+__device__ __forceinline__ int32_t cell_index(const Args& A, int64_t p, int64_t c1) {
+    if (p >= c1) return -1;
+    int32_t cc = A.C[p];
+    if (cc < 0 || cc >= A.nn) {
+        atomicOr(A.status, kStatBounds);
+        cc = 0;
+    }
+    return cc;
+}
+
+template <int ORDER>
+__device__ __forceinline__ void put_cell(Smem32& S, int u, const float4& r0, const float4& r1, const float4& r2v,
+                                         const float (&oh)[3], const float (&ol)[3]) {
+    CEnt E;
+    E.x = f2(rel(r0.x, r1.x, oh[0], ol[0]));
+    E.y = f2(rel(r0.y, r1.y, oh[1], ol[1]));
+    E.z = f2(rel(r0.z, r1.z, oh[2], ol[2]));
+    E.m = f2(r0.w);
+    if (ORDER >= 2) {  // stored negated; Qzz = -(Qxx + Qyy)
+        E.qxx = f2(-r1.w);
+        E.qxy = f2(-r2v.x);
+        E.qxz = f2(-r2v.y);
+        E.qyy = f2(-r2v.z);
+        E.qyz = f2(-r2v.w);
+        E.qzz = f2(r1.w + r2v.z);
+    } else {
+        E.qxx = E.qxy = E.qxz = E.qyy = E.qyz = E.qzz = f2(0.f);
+    }
+    S.t.c[u] = E;
+}
+
 template <int R, bool SELF>
-__device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R>& K, int npair, int T, int J, int tj,
+__device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R>& K, int nt, int T, int J, int tj,
                                         float rnear2, int& ncount, int lane) {
     const float2 eps2 = f2(A.fp.eps2f);
-    for (int q = 0; q < npair; ++q) {
-        const JPair P = S.t.p.jp[q];
-        const uint32_t* jid = &S.t.p.jid[2 * q];
-        bool any = false;
+    if (R > 0)
+        for (int q = 0; q < nt; ++q) {
+            const JEnt E = S.t.p.e[q];
+            const uint32_t jid = S.t.p.id[q];
+            bool any = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            any |= pp_body<SELF>(P, jid, K.iv[r], K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2,
-                                 rnear2);
-        if (__any_sync(0xffffffffu, any))
-            queue_pair<R, SELF>(A, S, ncount, P, jid, K.nx, K.ny, K.nz, K.iv, K.vl, K.sidx, rnear2, lane);
-        if (ncount >= 32) flush_near(A, S, ncount, lane);
-    }
+            for (int r = 0; r < R; ++r)
+                any |= pp_body<SELF>(E, jid, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], K.i0v[r], K.i1v[r],
+                                     eps2, rnear2);
+            if (__any_sync(0xffffffffu, any))
+                queue_entry<SELF, R>(S, ncount, E, jid, K, 0, R, false, eps2, rnear2, lane);
+            if (ncount >= 32) flush_near(A, S, ncount, lane);
+        }
     if (T > 0) {
-        const int trips = (npair + J - 1) / J;
+        const int trips = (nt + J - 1) / J;
         for (int u = 0; u < trips; ++u) {
             const int q = u * J + tj;
+            const bool ok = q < nt;
+            const JEnt E = S.t.p.e[ok ? q : 0];
+            const uint32_t jid = S.t.p.id[ok ? q : 0];
             bool any = false;
-            JPair P;
-            const uint32_t* jid = &S.t.p.jid[0];
-            if (q < npair) {
-                P = S.t.p.jp[q];
-                jid = &S.t.p.jid[2 * q];
-                any = pp_body<SELF>(P, jid, K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2,
-                                    rnear2);
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                if (q >= npair) P = S.t.p.jp[0];
-                const float2 tnx[1] = {K.nx[R]}, tny[1] = {K.ny[R]}, tnz[1] = {K.nz[R]};
-                const uint32_t tiv[1] = {K.iv[R]};
-                const bool tvl[1] = {K.vl[R] && q < npair};
-                const int tsi[1] = {K.sidx[R]};
-                queue_pair<1, SELF>(A, S, ncount, P, jid, tnx, tny, tnz, tiv, tvl, tsi, rnear2, lane);
-            }
+            if (ok)
+                any = pp_body<SELF>(E, jid, K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], K.i0v[R], K.i1v[R],
+                                    eps2, rnear2);
+            if (__any_sync(0xffffffffu, any))
+                queue_entry<SELF, R>(S, ncount, E, jid, K, R, R + 1, ok, eps2, rnear2, lane);
             if (ncount >= 32) flush_near(A, S, ncount, lane);
         }
     }
 }
 
 template <int R, int ORDER>
-__device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R>& K, int npair, int T, int J, int tj) {
+__device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R>& K, int nt, int T, int J, int tj) {
     const float2 eps2 = f2(A.fp.eps2f);
-    for (int q = 0; q < npair; ++q) {
-        const CPair& Cp = S.t.cp[q];
+    if (R > 0)
+        for (int q = 0; q < nt; ++q) {
+            const CEnt& E = S.t.c[q];
 #pragma unroll
-        for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
-    }
+            for (int r = 0; r < R; ++r) pc_body<ORDER>(E, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
+        }
     if (T > 0)
-        for (int q = tj; q < npair; q += J)
-            pc_body<ORDER>(S.t.cp[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
-}
-
-template <int R>
-__device__ __forceinline__ void fold_all(Smem32& S, Chunk<R>& K, int T) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) fold(S, K.sidx[r], K.gx[r], K.gy[r], K.gz[r]);
-    if (T > 0) fold(S, K.sidx[R], K.gx[R], K.gy[R], K.gz[R]);
+        for (int q = tj; q < nt; q += J)
+            pc_body<ORDER>(S.t.c[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
 }
 
 template <int R, int ORDER>
@@ -378,108 +428,107 @@ __device__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uin
 #pragma unroll
     for (int r = 0; r < R + 1; ++r) {
         const bool tail = (r == R);
-        const uint32_t i = tail ? i0 + 32 * R + ti : i0 + 32 * r + lane;
-        K.vl[r] = tail ? (T > 0 && i < e) : (i < e);
-        K.iv[r] = K.vl[r] ? i : b;
-        K.sidx[r] = 32 * r + lane;
-        const float4 h = A.phi[K.iv[r]], l = A.plo[K.iv[r]];
-        K.nx[r] = f2(-rel(h.x, l.x, oh[0], ol[0]));
-        K.ny[r] = f2(-rel(h.y, l.y, oh[1], ol[1]));
-        K.nz[r] = f2(-rel(h.z, l.z, oh[2], ol[2]));
+        uint32_t p0, p1;
+        if (tail) {
+            p0 = i0 + 64 * R + ti;
+            p1 = p0 + T;
+        } else {
+            p0 = i0 + 64 * r + lane;
+            p1 = p0 + 32;
+        }
+        K.v0[r] = (!tail || T > 0) && p0 < e;
+        K.v1[r] = (!tail || T > 0) && p1 < e;
+        K.i0v[r] = K.v0[r] ? p0 : b;
+        K.i1v[r] = K.v1[r] ? p1 : b;
+        K.s0[r] = 64 * r + lane;
+        K.s1[r] = 64 * r + 32 + lane;
+        const float4 h0 = A.phi[K.i0v[r]], l0 = A.plo[K.i0v[r]], h1 = A.phi[K.i1v[r]], l1 = A.plo[K.i1v[r]];
+        K.nx[r] = make_float2(-rel(h0.x, l0.x, oh[0], ol[0]), -rel(h1.x, l1.x, oh[0], ol[0]));
+        K.ny[r] = make_float2(-rel(h0.y, l0.y, oh[1], ol[1]), -rel(h1.y, l1.y, oh[1], ol[1]));
+        K.nz[r] = make_float2(-rel(h0.z, l0.z, oh[2], ol[2]), -rel(h1.z, l1.z, oh[2], ol[2]));
         K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
         if (!tail || T > 0)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) S.nacc[K.sidx[r]][c] = S.ahi[K.sidx[r]][c] = S.alo[K.sidx[r]][c] = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                S.ahi[K.s0[r]][c] = S.alo[K.s0[r]][c] = 0.f;
+                S.ahi[K.s1[r]][c] = S.alo[K.s1[r]][c] = 0.f;
+            }
     }
     int ncount = 0;
     __syncwarp();
 
-    // (1) the group's own particles, i = j excluded
-    for (uint32_t t0 = b; t0 < e; t0 += kTileJ) {
-        const int nt = (int)min((uint32_t)kTileJ, e - t0);
-        const int npair = (nt + 1) >> 1;
-#pragma unroll
-        for (int s = 0; s < kTileJ / 32; ++s) {
-            const int u = lane + 32 * s;
-            if (u < 2 * npair) stage_particle(A, S, u, t0 + u, u < nt, oh, ol);
+    // (1) the group's own particles (contiguous), i = j excluded
+    {
+        PRaw d0, d1;  // next tile, entries lane and lane + 32
+        d0.j = b + lane;
+        d1.j = b + lane + 32;
+        if (d0.j < e) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
+        if (d1.j < e) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+        for (uint32_t t0 = b; t0 < e; t0 += kTileJ) {
+            const int nt = (int)min((uint32_t)kTileJ, e - t0);
+            put_particle(S, lane, d0, lane < nt, oh, ol);
+            put_particle(S, lane + 32, d1, lane + 32 < nt, oh, ol);
+            __syncwarp();
+            d0.j = t0 + kTileJ + lane;
+            d1.j = t0 + kTileJ + lane + 32;
+            if (d0.j < e) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
+            if (d1.j < e) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+            pp_tile<R, true>(A, S, K, nt, T, J, tj, rnear2, ncount, lane);
+            fold_all<R>(S, K, T);
+            __syncwarp();
         }
-        __syncwarp();
-        pp_tile<R, true>(A, S, K, npair, T, J, tj, rnear2, ncount, lane);
-        fold_all<R>(S, K, T);
-        __syncwarp();
     }
-    // (2) the other list particles
-    const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
-    for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
-        const int nt = (int)min((int64_t)kTileJ, j1 - t0);
-        const int npair = (nt + 1) >> 1;
-#pragma unroll
-        for (int s = 0; s < kTileJ / 32; ++s) {
-            const int u = lane + 32 * s;
-            if (u < 2 * npair) {
-                uint32_t j = 0;
-                if (u < nt) {
-                    j = A.JJ[t0 + u];
-                    if (j >= A.n) {
-                        atomicOr(A.status, kStatBounds);
-                        j = b;
-                    }
-                }
-                stage_particle(A, S, u, j, u < nt, oh, ol);
-            }
+    // (2) the other list particles: indices two tiles ahead, data one tile ahead
+    {
+        const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
+        PRaw d0, d1;
+        d0.j = list_index(A, j0 + lane, j1, b);
+        d1.j = list_index(A, j0 + lane + 32, j1, b);
+        uint32_t ib0 = list_index(A, j0 + kTileJ + lane, j1, b), ib1 = list_index(A, j0 + kTileJ + lane + 32, j1, b);
+        if (d0.j != kNone) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
+        if (d1.j != kNone) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+        for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
+            const int nt = (int)min((int64_t)kTileJ, j1 - t0);
+            put_particle(S, lane, d0, lane < nt, oh, ol);
+            put_particle(S, lane + 32, d1, lane + 32 < nt, oh, ol);
+            __syncwarp();
+            d0.j = ib0;
+            d1.j = ib1;
+            if (d0.j != kNone) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
+            if (d1.j != kNone) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+            ib0 = list_index(A, t0 + 2 * kTileJ + lane, j1, b);
+            ib1 = list_index(A, t0 + 2 * kTileJ + lane + 32, j1, b);
+            pp_tile<R, false>(A, S, K, nt, T, J, tj, rnear2, ncount, lane);
+            fold_all<R>(S, K, T);
+            __syncwarp();
         }
-        __syncwarp();
-        pp_tile<R, false>(A, S, K, npair, T, J, tj, rnear2, ncount, lane);
-        fold_all<R>(S, K, T);
-        __syncwarp();
     }
     if (ncount > 0) flush_near(A, S, ncount, lane);
-    // (3) list cells
-    const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
-    for (int64_t t0 = c0; t0 < c1; t0 += kTileC) {
-        const int nt = (int)min((int64_t)kTileC, c1 - t0);
-        const int npair = (nt + 1) >> 1;
-#pragma unroll
-        for (int s = 0; s < kTileC / 32; ++s) {
-            const int u = lane + 32 * s;
-            if (u < 2 * npair) {
-                float v[10];
-                if (u < nt) {
-                    int32_t cc = A.C[t0 + u];
-                    if (cc < 0 || cc >= A.nn) {
-                        atomicOr(A.status, kStatBounds);
-                        cc = 0;
-                    }
-                    const float4 r0 = A.cell32[3 * (int64_t)cc], r1 = A.cell32[3 * (int64_t)cc + 1];
-                    v[0] = rel(r0.x, r1.x, oh[0], ol[0]);
-                    v[1] = rel(r0.y, r1.y, oh[1], ol[1]);
-                    v[2] = rel(r0.z, r1.z, oh[2], ol[2]);
-                    v[3] = r0.w;
-                    if (ORDER >= 2) {
-                        const float4 r2v = A.cell32[3 * (int64_t)cc + 2];  // Qxy, Qxz, Qyy, Qyz
-                        v[4] = -r1.w;
-                        v[5] = -r2v.x;
-                        v[6] = -r2v.y;
-                        v[7] = -r2v.z;
-                        v[8] = -r2v.w;
-                        v[9] = r1.w + r2v.z;  // -Qzz = Qxx + Qyy (traceless)
-                    }
-                } else {
-                    v[0] = v[1] = v[2] = 1e15f;
-                    v[3] = 0.f;
-#pragma unroll
-                    for (int a = 4; a < 10; ++a) v[a] = 0.f;
-                }
-                float* base = reinterpret_cast<float*>(&S.t.cp[u >> 1]);
-                const int hh = u & 1;
-#pragma unroll
-                for (int a = 0; a < (ORDER >= 2 ? 10 : 4); ++a) base[2 * a + hh] = v[a];
-            }
+    // (3) list cells: indices two tiles ahead, data one tile ahead
+    {
+        const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2v = r0;
+        int32_t ca = cell_index(A, c0 + lane, c1);
+        int32_t cb = cell_index(A, c0 + kTileC + lane, c1);
+        if (ca >= 0) {
+            r0 = A.cell32[3 * (int64_t)ca];
+            r1 = A.cell32[3 * (int64_t)ca + 1];
+            if (ORDER >= 2) r2v = A.cell32[3 * (int64_t)ca + 2];
         }
-        __syncwarp();
-        pc_tile<R, ORDER>(A, S, K, npair, T, J, tj);
-        fold_all<R>(S, K, T);
-        __syncwarp();
+        for (int64_t t0 = c0; t0 < c1; t0 += kTileC) {
+            const int nt = (int)min((int64_t)kTileC, c1 - t0);
+            if (lane < nt) put_cell<ORDER>(S, lane, r0, r1, r2v, oh, ol);
+            __syncwarp();
+            if (cb >= 0) {
+                r0 = A.cell32[3 * (int64_t)cb];
+                r1 = A.cell32[3 * (int64_t)cb + 1];
+                if (ORDER >= 2) r2v = A.cell32[3 * (int64_t)cb + 2];
+            }
+            cb = cell_index(A, t0 + 2 * kTileC + lane, c1);
+            pc_tile<R, ORDER>(A, S, K, nt, T, J, tj);
+            fold_all<R>(S, K, T);
+            __syncwarp();
+        }
     }
     __syncwarp();
     // (4) outputs: full slots directly, the tail slot after a reduction over its J lanes
@@ -487,21 +536,24 @@ __device__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uin
     for (int r = 0; r < R + 1; ++r) {
         const bool tail = (r == R);
         if (tail && T == 0) break;
-        const int s = K.sidx[r];
-        double a[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]) + (double)S.nacc[s][c];
-        if (tail)
-            for (int o = T; o < 32; o <<= 1)
+        for (int h = 0; h < 2; ++h) {
+            const int s = h ? K.s1[r] : K.s0[r];
+            double a[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
-        if (K.vl[r] && (!tail || tj == 0)) {
-            const uint32_t i = K.iv[r];
-            if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
-            A.ax[i] = a[0];
-            A.ay[i] = a[1];
-            A.az[i] = a[2];
+            for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
+            if (tail)
+                for (int o = T; o < 32; o <<= 1)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+            const bool valid = h ? K.v1[r] : K.v0[r];
+            if (valid && (!tail || tj == 0)) {
+                const uint32_t i = h ? K.i1v[r] : K.i0v[r];
+                if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
+                A.ax[i] = a[0];
+                A.ay[i] = a[1];
+                A.az[i] = a[2];
+            }
         }
     }
     __syncwarp();
@@ -525,22 +577,32 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     const uint32_t ext = max(G.b.x - G.a.x, max(G.b.y - G.a.y, G.b.z - G.a.z)) + 1u;
     const float rn = A.fp.near_frac * (float)ext * A.fp.h;
     const float rnear2 = fmaxf(A.fp.rnear_min2, rn * rn) + A.fp.eps2f;
-    for (uint32_t i0 = b; i0 < e; i0 += 32 * kSlots) {
-        const uint32_t cnt = min((uint32_t)(32 * kSlots), e - i0);
-        int R = (int)(cnt >> 5), t = (int)(cnt & 31), T = 0;
-        if (t > 16) {
-            ++R;  // more than half a slot left: a full slot
-        } else if (t > 0) {
+    // chunks: 64 particles (one full pair-slot) while more than 96 remain; the
+    // last chunk is a full pair-slot plus a tail of at most 32, a partly
+    // filled pair-slot (33..64 left), or a tail alone (at most 32 left)
+    for (uint32_t i0 = b; i0 < e;) {
+        const uint32_t rem = e - i0;
+        int T = 0;
+        uint32_t cnt;
+        bool full;
+        if (rem > 96) {
+            full = true;
+            cnt = 64;
+        } else if (rem > 64 || rem <= 32) {
+            full = rem > 64;
+            const int t = (int)(full ? rem - 64 : rem), need = (t + 1) >> 1;
             T = 1;
-            while (T < t) T <<= 1;
+            while (T < need) T <<= 1;
+            cnt = rem;
+        } else {
+            full = true;
+            cnt = rem;
         }
-        switch (R) {
-            case 0: group_chunk<0, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
-            case 1: group_chunk<1, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
-            case 2: group_chunk<2, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
-            case 3: group_chunk<3, ORDER>(A, S, k, b, e, i0, T, oh, ol, rnear2, lane); break;
-            default: group_chunk<4, ORDER>(A, S, k, b, e, i0, 0, oh, ol, rnear2, lane); break;
-        }
+        if (full)
+            group_chunk<1, ORDER>(A, S, k, b, i0 + cnt, i0, T, oh, ol, rnear2, lane);
+        else
+            group_chunk<0, ORDER>(A, S, k, b, i0 + cnt, i0, T, oh, ol, rnear2, lane);
+        i0 += cnt;
     }
 }
 
