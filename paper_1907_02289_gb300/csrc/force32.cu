@@ -18,20 +18,21 @@
 // evaluates in FP64 in the oracle's operation order (contact term of Eq. (1)
 // and the r <= r_coll decision).
 //
-// Summation: FP32 partial sums per tile, folded after every tile into a
-// compensated (TwoSum) hi/lo accumulator in shared memory.
+// Summation: FP32 partial sums per tile (even and odd list entries apart),
+// folded after every tile into a compensated (TwoSum) hi/lo accumulator in
+// shared memory.
 //
-// Mapping: one warp per group.  Every lane holds its i-particles in pairs,
-// (x_i, x_i') in one f32x2 register, and each list entry is broadcast from
-// shared memory as (x_j, x_j); one packed FADD2/FFMA2/FMUL2 then serves two
-// interactions.  A group of n_i = 64 R + t particles gives every lane R full
-// pair-slots; the t remaining particles go to a "tail" pair-slot held by
-// T lanes (T = ceil(t/2) rounded up to a power of two) that split the list
-// J = 32/T ways, so a 65-particle group costs 1 + 1/32 slots rather than 2.
-// List tiles are gathered one tile ahead (indices two tiles ahead) so that
-// the gathers overlap the arithmetic.  The group's own particles are
-// evaluated first in a phase that excludes i = j; the expanded list holds
-// only the other particles.
+// Mapping: one warp per group.  A group of n_i = 32 R + t particles gives
+// every lane R i-slots; the t remaining particles go to a "tail" slot shared
+// by J = 32 / T lanes (T = t rounded up to a power of two) that split the
+// list between them, so a 65-particle group costs 2 + 1/32 slots rather
+// than 3.  List entries are staged in pairs in shared memory and broadcast,
+// and the pair (j, j+1) is evaluated with packed f32x2 instructions (FADD2,
+// FFMA2, FMUL2) against the i-particle held as (x_i, x_i), which halves the
+// issue slots per interaction.  List tiles are gathered one tile ahead
+// (indices two tiles ahead) so that the gathers overlap the arithmetic.  The
+// group's own particles are evaluated first in a phase that excludes i = j;
+// the expanded list holds only the other particles.
 #include <cmath>
 
 #include "force_common.cuh"
@@ -42,33 +43,40 @@ namespace {
 #ifndef BH_F32_MINB
 #define BH_F32_MINB 4  // resident blocks per SM the register budget is sized for
 #endif
-constexpr int kW32 = 4;       // warps per block
-constexpr int kTileJ = 64;    // list particles per tile (2 per lane)
-constexpr int kTileC = 32;    // list cells per tile (1 per lane)
-constexpr int kPS = 2;        // pair-slots per lane (full + tail)
-constexpr int kNearCap = 32 + 2 * kPS * 32;
-constexpr int kPSlots = 64 * kPS;  // particle slots per warp
+constexpr int kW32 = 4;     // warps per block
+constexpr int kTileJ = 64;  // list particles per tile (32 pairs, 2 per lane)
+constexpr int kTileC = 32;  // list cells per tile (16 pairs, 1 per lane)
+constexpr int kSlots = 3;   // i-slots per lane (full slots + tail)
+constexpr int kNearCap = 32 + 2 * kSlots * 32;
+constexpr uint32_t kNone = 0xffffffffu;
 
-struct JEnt {  // one list particle, each value duplicated for the packed ops
+struct JPair {  // two list particles, coordinates relative to the group origin
     float2 x, y, z, m;
 };
-struct CEnt {  // one cell: centre, mass, negated traceless quadrupole (duplicated)
+struct CPair {  // two cells: centre relative to the origin, mass, negated quadrupole
     float2 x, y, z, m, qxx, qxy, qxz, qyy, qyz, qzz;
 };
 
 struct Smem32 {
     union {
         struct {
-            JEnt e[kTileJ];
-            uint32_t id[kTileJ];
+            JPair jp[kTileJ / 2];
+            uint32_t jid[kTileJ];
         } p;
-        CEnt c[kTileC];
+        CPair cp[kTileC / 2];
     } t;
+    union {  // raw gathered data of the next tile (filled by cp.async)
+        struct {
+            float4 h[kTileJ], l[kTileJ];
+        } p;
+        float4 c[kTileC][3];
+    } raw;
+    uint32_t raw_id[kTileJ];
     uint32_t near_i[kNearCap];
     uint32_t near_j[kNearCap];
     uint8_t near_s[kNearCap];
-    float ahi[kPSlots][3];  // compensated fast-loop sums (G-free), hi part
-    float alo[kPSlots][3];  // low part; G-free near-pair results are added here too
+    float ahi[32 * kSlots][3];  // compensated fast-loop sums (G-free), hi part
+    float alo[32 * kSlots][3];  // low part; G-free near-pair results are added here too
 };
 
 struct Args {
@@ -115,16 +123,15 @@ __device__ __forceinline__ void central_newton(double G_Mc, double x, double y, 
 }
 
 // ---- per-chunk state ------------------------------------------------------
-// Pair-slot r (r < R): lane holds particles p0 = i0 + 64 r + lane and
-// p1 = p0 + 32.  Tail pair-slot (r == R): lane holds i0 + 64 R + (lane % T)
-// and that + T, and sees only list entries q with q % J == lane / T.
-template <int R>
+// Slot r (r < R): lane holds particle i0 + 32 r + lane.  Tail slot (r == R):
+// lane holds i0 + 32 R + (lane % T) and sees only the list pairs q with
+// q % J == lane / T.
+template <int R, bool TAIL>
 struct Chunk {
-    static constexpr int NS = R + 1;
+    static constexpr int NS = R + (TAIL ? 1 : 0);
     float2 nx[NS], ny[NS], nz[NS], gx[NS], gy[NS], gz[NS];
-    uint32_t i0v[NS], i1v[NS];
-    bool v0[NS], v1[NS];
-    int s0[NS], s1[NS];  // particle-slot indices (shared-memory accumulators)
+    uint32_t iv[NS];
+    bool vl[NS];
 };
 
 // ---- near pairs ------------------------------------------------------------
@@ -182,20 +189,22 @@ __device__ __forceinline__ void flush_near(const Args& A, Smem32& S, int& ncount
     ncount = 0;
 }
 
-// Queue the near pairs of list entry E (flags recomputed here; rare path)
-// for pair-slots [r0, r1).  Warp-uniform call.
-template <bool SELF, int R>
-__device__ __forceinline__ void queue_entry(Smem32& S, int& ncount, const JEnt& E, uint32_t jid, const Chunk<R>& K,
-                                            int r0, int r1, bool tail_ok, float2 eps2, float rnear2, int lane) {
+// Queue the near pairs of list pair P (flags recomputed here; rare path)
+// for slots [r0, r1).  Warp-uniform call.
+template <bool SELF, int R, bool TAIL>
+__device__ __forceinline__ void queue_pair(Smem32& S, int& ncount, const JPair& P, const uint32_t* jid,
+                                           const Chunk<R, TAIL>& K, int r0, int r1, bool tail_ok, float2 eps2,
+                                           float rnear2, int lane) {
+    constexpr int NS = Chunk<R, TAIL>::NS;
     unsigned bits = 0;
 #pragma unroll
-    for (int r = 0; r < R + 1; ++r) {
+    for (int r = 0; r < NS; ++r) {
         if (r < r0 || r >= r1) continue;
-        const bool ok = (r < R) || tail_ok;
-        const float2 dx = __fadd2_rn(E.x, K.nx[r]), dy = __fadd2_rn(E.y, K.ny[r]), dz = __fadd2_rn(E.z, K.nz[r]);
+        const bool ok = K.vl[r] && ((r < R) || tail_ok);
+        const float2 dx = __fadd2_rn(P.x, K.nx[r]), dy = __fadd2_rn(P.y, K.ny[r]), dz = __fadd2_rn(P.z, K.nz[r]);
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
-        if (ok && K.v0[r] && r2.x < rnear2 && (!SELF || jid != K.i0v[r])) bits |= 1u << (2 * r);
-        if (ok && K.v1[r] && r2.y < rnear2 && (!SELF || jid != K.i1v[r])) bits |= 2u << (2 * r);
+        if (ok && r2.x < rnear2 && (!SELF || jid[0] != K.iv[r])) bits |= 1u << (2 * r);
+        if (ok && r2.y < rnear2 && (!SELF || jid[1] != K.iv[r])) bits |= 2u << (2 * r);
     }
     const int c = __popc(bits);
     int x = c;
@@ -207,127 +216,140 @@ __device__ __forceinline__ void queue_entry(Smem32& S, int& ncount, const JEnt& 
     const int total = __shfl_sync(0xffffffffu, x, 31);
     int pos = ncount + x - c;
 #pragma unroll
-    for (int r = 0; r < R + 1; ++r) {
-        if (bits & (1u << (2 * r))) {
-            S.near_i[pos] = K.i0v[r];
-            S.near_j[pos] = jid;
-            S.near_s[pos] = (uint8_t)K.s0[r];
-            ++pos;
-        }
-        if (bits & (2u << (2 * r))) {
-            S.near_i[pos] = K.i1v[r];
-            S.near_j[pos] = jid;
-            S.near_s[pos] = (uint8_t)K.s1[r];
-            ++pos;
-        }
-    }
+    for (int r = 0; r < NS; ++r)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (bits & (1u << (2 * r + h))) {
+                S.near_i[pos] = K.iv[r];
+                S.near_j[pos] = jid[h];
+                S.near_s[pos] = (uint8_t)(32 * r + lane);
+                ++pos;
+            }
     ncount += total;
     __syncwarp();
 }
 
 // ---- interaction bodies ------------------------------------------------------
-// Fast particle-particle term of one list entry for one pair-slot; returns
-// whether a near pair was masked out (self excluded when SELF).
+// Fast particle-particle term of one list pair for one slot; returns whether
+// a near pair was masked out (self excluded when SELF).
 template <bool SELF>
-__device__ __forceinline__ bool pp_body(const JEnt& E, uint32_t jid, float2 nx, float2 ny, float2 nz, float2& gx,
-                                        float2& gy, float2& gz, uint32_t i0, uint32_t i1, float2 eps2,
+__device__ __forceinline__ bool pp_body(const JPair& P, const uint32_t* jid, uint32_t i, float2 nx, float2 ny,
+                                        float2 nz, float2& gx, float2& gy, float2& gz, float2 eps2,
                                         float rnear2) {
-    const float2 dx = __fadd2_rn(E.x, nx);
-    const float2 dy = __fadd2_rn(E.y, ny);
-    const float2 dz = __fadd2_rn(E.z, nz);
+    const float2 dx = __fadd2_rn(P.x, nx);
+    const float2 dy = __fadd2_rn(P.y, ny);
+    const float2 dz = __fadd2_rn(P.z, nz);
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
     const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
     const float2 ri2 = __fmul2_rn(ri, ri);
-    float2 f = __fmul2_rn(__fmul2_rn(E.m, ri), ri2);
+    float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), ri2);
     const bool n0 = r2.x < rnear2, n1 = r2.y < rnear2;
     f.x = n0 ? 0.f : f.x;
     f.y = n1 ? 0.f : f.y;
     gx = __ffma2_rn(f, dx, gx);
     gy = __ffma2_rn(f, dy, gy);
     gz = __ffma2_rn(f, dz, gz);
-    if (SELF) return (n0 && jid != i0) || (n1 && jid != i1);
+    if (SELF) return (n0 && jid[0] != i) || (n1 && jid[1] != i);
     return n0 || n1;
 }
 
 template <int ORDER>
-__device__ __forceinline__ void pc_body(const CEnt& E, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
+__device__ __forceinline__ void pc_body(const CPair& Cp, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
                                         float2& gz, float2 eps2) {
-    const float2 dx = __fadd2_rn(E.x, nx);
-    const float2 dy = __fadd2_rn(E.y, ny);
-    const float2 dz = __fadd2_rn(E.z, nz);
+    const float2 dx = __fadd2_rn(Cp.x, nx);
+    const float2 dy = __fadd2_rn(Cp.y, ny);
+    const float2 dz = __fadd2_rn(Cp.z, nz);
     const float2 R2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
     const float2 ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
     const float2 ri2 = __fmul2_rn(ri, ri);
     const float2 ri3 = __fmul2_rn(ri, ri2);
     if (ORDER >= 2) {
         // q = -Q d, dqd = d.(-Q d); a += (M/R^3 + 5/2 (dQd)/R^7) d - Q d / R^5
-        const float2 qx = __ffma2_rn(E.qxx, dx, __ffma2_rn(E.qxy, dy, __fmul2_rn(E.qxz, dz)));
-        const float2 qy = __ffma2_rn(E.qxy, dx, __ffma2_rn(E.qyy, dy, __fmul2_rn(E.qyz, dz)));
-        const float2 qz = __ffma2_rn(E.qxz, dx, __ffma2_rn(E.qyz, dy, __fmul2_rn(E.qzz, dz)));
+        const float2 qx = __ffma2_rn(Cp.qxx, dx, __ffma2_rn(Cp.qxy, dy, __fmul2_rn(Cp.qxz, dz)));
+        const float2 qy = __ffma2_rn(Cp.qxy, dx, __ffma2_rn(Cp.qyy, dy, __fmul2_rn(Cp.qyz, dz)));
+        const float2 qz = __ffma2_rn(Cp.qxz, dx, __ffma2_rn(Cp.qyz, dy, __fmul2_rn(Cp.qzz, dz)));
         const float2 dqd = __ffma2_rn(dx, qx, __ffma2_rn(dy, qy, __fmul2_rn(dz, qz)));
         const float2 ri5 = __fmul2_rn(ri3, ri2);
         const float2 ri7 = __fmul2_rn(ri5, ri2);
-        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(E.m, ri3));
+        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(Cp.m, ri3));
         gx = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, gx));
         gy = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, gy));
         gz = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, gz));
     } else {
-        const float2 s = __fmul2_rn(E.m, ri3);
+        const float2 s = __fmul2_rn(Cp.m, ri3);
         gx = __ffma2_rn(s, dx, gx);
         gy = __ffma2_rn(s, dy, gy);
         gz = __ffma2_rn(s, dz, gz);
     }
 }
 
-__device__ __forceinline__ void fold1(Smem32& S, int s, float t, int c) {
-    const float hi = S.ahi[s][c];
-    const float s1 = __fadd_rn(hi, t);
-    const float bp = __fsub_rn(s1, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t, bp));
-    S.ahi[s][c] = s1;
-    S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
-}
-
-template <int R>
-__device__ __forceinline__ void fold_all(Smem32& S, Chunk<R>& K, int T) {
+__device__ __forceinline__ void fold(Smem32& S, int s, float2& gx, float2& gy, float2& gz) {
+    const float t[3] = {__fadd_rn(gx.x, gx.y), __fadd_rn(gy.x, gy.y), __fadd_rn(gz.x, gz.y)};
 #pragma unroll
-    for (int r = 0; r < R + 1; ++r) {
-        if (r == R && T == 0) break;
-        fold1(S, K.s0[r], K.gx[r].x, 0);
-        fold1(S, K.s0[r], K.gy[r].x, 1);
-        fold1(S, K.s0[r], K.gz[r].x, 2);
-        fold1(S, K.s1[r], K.gx[r].y, 0);
-        fold1(S, K.s1[r], K.gy[r].y, 1);
-        fold1(S, K.s1[r], K.gz[r].y, 2);
-        K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
+    for (int c = 0; c < 3; ++c) {
+        const float hi = S.ahi[s][c];
+        const float s1 = __fadd_rn(hi, t[c]);
+        const float bp = __fsub_rn(s1, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t[c], bp));
+        S.ahi[s][c] = s1;
+        S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
+    }
+    gx = gy = gz = make_float2(0.f, 0.f);
+}
+
+template <int R, bool TAIL>
+__device__ __forceinline__ void fold_all(Smem32& S, Chunk<R, TAIL>& K, int lane) {
+#pragma unroll
+    for (int r = 0; r < Chunk<R, TAIL>::NS; ++r) fold(S, 32 * r + lane, K.gx[r], K.gy[r], K.gz[r]);
+}
+
+// ---- staging -------------------------------------------------------------------
+// Asynchronous 16-byte global -> shared copies (no registers held while the
+// gather is in flight); one commit group per tile, waited for at the top of
+// the next tile.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start the gather of list particle j into raw slot u (kNone: nothing).
+__device__ __forceinline__ void gather_particle(const Args& A, Smem32& S, int u, uint32_t j) {
+    S.raw_id[u] = j;
+    if (j != kNone) {
+        cp_async16(&S.raw.p.h[u], &A.phi[j]);
+        cp_async16(&S.raw.p.l[u], &A.plo[j]);
     }
 }
 
-// ---- tiles -------------------------------------------------------------------
-// Gathered raw data of one particle entry (prefetched into registers).
-struct PRaw {
-    float4 h, l;
-    uint32_t j;
-};
-
-__device__ __forceinline__ void put_particle(Smem32& S, int u, const PRaw& P, bool real, const float (&oh)[3],
+// Raw slot u -> shifted entry u of the particle tile (padding when !real).
+__device__ __forceinline__ void put_particle(Smem32& S, int u, bool real, const float (&oh)[3],
                                              const float (&ol)[3]) {
-    JEnt E;
+    float px, py, pz, pm;
     if (real) {
-        E.x = f2(rel(P.h.x, P.l.x, oh[0], ol[0]));
-        E.y = f2(rel(P.h.y, P.l.y, oh[1], ol[1]));
-        E.z = f2(rel(P.h.z, P.l.z, oh[2], ol[2]));
-        E.m = f2(P.h.w);
+        const float4 h = S.raw.p.h[u], l = S.raw.p.l[u];
+        px = rel(h.x, l.x, oh[0], ol[0]);
+        py = rel(h.y, l.y, oh[1], ol[1]);
+        pz = rel(h.z, l.z, oh[2], ol[2]);
+        pm = h.w;
     } else {  // padding entry: far away, massless
-        E.x = E.y = E.z = f2(1e15f);
-        E.m = f2(0.f);
+        px = py = pz = 1e15f;
+        pm = 0.f;
     }
-    S.t.p.e[u] = E;
-    S.t.p.id[u] = real ? P.j : 0xffffffffu;
+    float* base = reinterpret_cast<float*>(&S.t.p.jp[u >> 1]);
+    const int hh = u & 1;
+    base[0 + hh] = px;
+    base[2 + hh] = py;
+    base[4 + hh] = pz;
+    base[6 + hh] = pm;
+    S.t.p.jid[u] = real ? S.raw_id[u] : kNone;
 }
 
-
-constexpr uint32_t kNone = 0xffffffffu;
+__device__ __forceinline__ void gather_cell(const Args& A, Smem32& S, int u, int32_t cc, int nrec) {
+    if (cc >= 0)
+        for (int a = 0; a < nrec; ++a) cp_async16(&S.raw.c[u][a], &A.cell32[3 * (int64_t)cc + a]);
+}
 
 __device__ __forceinline__ uint32_t list_index(const Args& A, int64_t p, int64_t j1, uint32_t fallback) {
     if (p >= j1) return kNone;
@@ -350,210 +372,203 @@ __device__ __forceinline__ int32_t cell_index(const Args& A, int64_t p, int64_t 
 }
 
 template <int ORDER>
-__device__ __forceinline__ void put_cell(Smem32& S, int u, const float4& r0, const float4& r1, const float4& r2v,
-                                         const float (&oh)[3], const float (&ol)[3]) {
-    CEnt E;
-    E.x = f2(rel(r0.x, r1.x, oh[0], ol[0]));
-    E.y = f2(rel(r0.y, r1.y, oh[1], ol[1]));
-    E.z = f2(rel(r0.z, r1.z, oh[2], ol[2]));
-    E.m = f2(r0.w);
-    if (ORDER >= 2) {  // stored negated; Qzz = -(Qxx + Qyy)
-        E.qxx = f2(-r1.w);
-        E.qxy = f2(-r2v.x);
-        E.qxz = f2(-r2v.y);
-        E.qyy = f2(-r2v.z);
-        E.qyz = f2(-r2v.w);
-        E.qzz = f2(r1.w + r2v.z);
-    } else {
-        E.qxx = E.qxy = E.qxz = E.qyy = E.qyz = E.qzz = f2(0.f);
+__device__ __forceinline__ void put_cell(Smem32& S, int u, bool real, const float (&oh)[3], const float (&ol)[3]) {
+    float v[10];
+    if (real) {
+        const float4 r0 = S.raw.c[u][0], r1 = S.raw.c[u][1], r2v = S.raw.c[u][2];
+        v[0] = rel(r0.x, r1.x, oh[0], ol[0]);
+        v[1] = rel(r0.y, r1.y, oh[1], ol[1]);
+        v[2] = rel(r0.z, r1.z, oh[2], ol[2]);
+        v[3] = r0.w;
+        if (ORDER >= 2) {  // stored negated; Qzz = -(Qxx + Qyy)
+            v[4] = -r1.w;
+            v[5] = -r2v.x;
+            v[6] = -r2v.y;
+            v[7] = -r2v.z;
+            v[8] = -r2v.w;
+            v[9] = r1.w + r2v.z;
+        }
+    } else {  // padding entry: far away, massless
+        v[0] = v[1] = v[2] = 1e15f;
+        v[3] = 0.f;
+#pragma unroll
+        for (int a = 4; a < 10; ++a) v[a] = 0.f;
     }
-    S.t.c[u] = E;
+    float* base = reinterpret_cast<float*>(&S.t.cp[u >> 1]);
+    const int hh = u & 1;
+#pragma unroll
+    for (int a = 0; a < (ORDER >= 2 ? 10 : 4); ++a) base[2 * a + hh] = v[a];
 }
 
-template <int R, bool SELF>
-__device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R>& K, int nt, int T, int J, int tj,
+// ---- tile loops --------------------------------------------------------------
+template <int R, bool TAIL, bool SELF>
+__device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj,
                                         float rnear2, int& ncount, int lane) {
     const float2 eps2 = f2(A.fp.eps2f);
-    if (R > 0)
-        for (int q = 0; q < nt; ++q) {
-            const JEnt E = S.t.p.e[q];
-            const uint32_t jid = S.t.p.id[q];
+    if constexpr (R > 0)
+        for (int q = 0; q < npair; ++q) {
+            const JPair P = S.t.p.jp[q];
+            const uint32_t* jid = &S.t.p.jid[2 * q];
             bool any = false;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                any |= pp_body<SELF>(E, jid, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], K.i0v[r], K.i1v[r],
-                                     eps2, rnear2);
+                any |= pp_body<SELF>(P, jid, K.iv[r], K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2,
+                                     rnear2);
             if (__any_sync(0xffffffffu, any))
-                queue_entry<SELF, R>(S, ncount, E, jid, K, 0, R, false, eps2, rnear2, lane);
+                queue_pair<SELF, R, TAIL>(S, ncount, P, jid, K, 0, R, false, eps2, rnear2, lane);
             if (ncount >= 32) flush_near(A, S, ncount, lane);
         }
-    if (T > 0) {
-        const int trips = (nt + J - 1) / J;
+    if constexpr (TAIL) {
+        const int trips = (npair + J - 1) / J;
         for (int u = 0; u < trips; ++u) {
             const int q = u * J + tj;
-            const bool ok = q < nt;
-            const JEnt E = S.t.p.e[ok ? q : 0];
-            const uint32_t jid = S.t.p.id[ok ? q : 0];
+            const bool ok = q < npair;
+            const JPair P = S.t.p.jp[ok ? q : 0];
+            const uint32_t* jid = &S.t.p.jid[ok ? 2 * q : 0];
             bool any = false;
             if (ok)
-                any = pp_body<SELF>(E, jid, K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], K.i0v[R], K.i1v[R],
-                                    eps2, rnear2);
+                any = pp_body<SELF>(P, jid, K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2,
+                                    rnear2);
             if (__any_sync(0xffffffffu, any))
-                queue_entry<SELF, R>(S, ncount, E, jid, K, R, R + 1, ok, eps2, rnear2, lane);
+                queue_pair<SELF, R, TAIL>(S, ncount, P, jid, K, R, R + 1, ok, eps2, rnear2, lane);
             if (ncount >= 32) flush_near(A, S, ncount, lane);
         }
     }
 }
 
-template <int R, int ORDER>
-__device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R>& K, int nt, int T, int J, int tj) {
+template <int R, bool TAIL, int ORDER>
+__device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj) {
     const float2 eps2 = f2(A.fp.eps2f);
-    if (R > 0)
-        for (int q = 0; q < nt; ++q) {
-            const CEnt& E = S.t.c[q];
+    if constexpr (R > 0)
+        for (int q = 0; q < npair; ++q) {
+            const CPair& Cp = S.t.cp[q];
 #pragma unroll
-            for (int r = 0; r < R; ++r) pc_body<ORDER>(E, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
+            for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
         }
-    if (T > 0)
-        for (int q = tj; q < nt; q += J)
-            pc_body<ORDER>(S.t.c[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
+    if constexpr (TAIL)
+        for (int q = tj; q < npair; q += J)
+            pc_body<ORDER>(S.t.cp[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
 }
 
-template <int R, int ORDER>
-__device__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e, uint32_t i0, int T,
+template <int R, bool TAIL, int ORDER>
+__device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e, uint32_t i0, int T,
                             const float (&oh)[3], const float (&ol)[3], float rnear2, int lane) {
-    Chunk<R> K;
-    const int J = T > 0 ? 32 / T : 1;
-    const int ti = T > 0 ? lane % T : 0, tj = T > 0 ? lane / T : 0;
+    constexpr int NS = Chunk<R, TAIL>::NS;
+    Chunk<R, TAIL> K;
+    const int J = TAIL ? 32 / T : 1;
+    const int ti = TAIL ? lane % T : 0, tj = TAIL ? lane / T : 0;
 #pragma unroll
-    for (int r = 0; r < R + 1; ++r) {
+    for (int r = 0; r < NS; ++r) {
         const bool tail = (r == R);
-        uint32_t p0, p1;
-        if (tail) {
-            p0 = i0 + 64 * R + ti;
-            p1 = p0 + T;
-        } else {
-            p0 = i0 + 64 * r + lane;
-            p1 = p0 + 32;
-        }
-        K.v0[r] = (!tail || T > 0) && p0 < e;
-        K.v1[r] = (!tail || T > 0) && p1 < e;
-        K.i0v[r] = K.v0[r] ? p0 : b;
-        K.i1v[r] = K.v1[r] ? p1 : b;
-        K.s0[r] = 64 * r + lane;
-        K.s1[r] = 64 * r + 32 + lane;
-        const float4 h0 = A.phi[K.i0v[r]], l0 = A.plo[K.i0v[r]], h1 = A.phi[K.i1v[r]], l1 = A.plo[K.i1v[r]];
-        K.nx[r] = make_float2(-rel(h0.x, l0.x, oh[0], ol[0]), -rel(h1.x, l1.x, oh[0], ol[0]));
-        K.ny[r] = make_float2(-rel(h0.y, l0.y, oh[1], ol[1]), -rel(h1.y, l1.y, oh[1], ol[1]));
-        K.nz[r] = make_float2(-rel(h0.z, l0.z, oh[2], ol[2]), -rel(h1.z, l1.z, oh[2], ol[2]));
+        const uint32_t i = tail ? i0 + 32 * R + ti : i0 + 32 * r + lane;
+        K.vl[r] = i < e;
+        K.iv[r] = K.vl[r] ? i : b;
+        const float4 h = A.phi[K.iv[r]], l = A.plo[K.iv[r]];
+        K.nx[r] = f2(-rel(h.x, l.x, oh[0], ol[0]));
+        K.ny[r] = f2(-rel(h.y, l.y, oh[1], ol[1]));
+        K.nz[r] = f2(-rel(h.z, l.z, oh[2], ol[2]));
         K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
-        if (!tail || T > 0)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                S.ahi[K.s0[r]][c] = S.alo[K.s0[r]][c] = 0.f;
-                S.ahi[K.s1[r]][c] = S.alo[K.s1[r]][c] = 0.f;
-            }
+        for (int c = 0; c < 3; ++c) S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
     }
     int ncount = 0;
     __syncwarp();
 
     // (1) the group's own particles (contiguous), i = j excluded
     {
-        PRaw d0, d1;  // next tile, entries lane and lane + 32
-        d0.j = b + lane;
-        d1.j = b + lane + 32;
-        if (d0.j < e) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
-        if (d1.j < e) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+        gather_particle(A, S, lane, b + lane < e ? b + lane : kNone);
+        gather_particle(A, S, lane + 32, b + lane + 32 < e ? b + lane + 32 : kNone);
+        cp_async_commit();
         for (uint32_t t0 = b; t0 < e; t0 += kTileJ) {
             const int nt = (int)min((uint32_t)kTileJ, e - t0);
-            put_particle(S, lane, d0, lane < nt, oh, ol);
-            put_particle(S, lane + 32, d1, lane + 32 < nt, oh, ol);
+            const int npair = (nt + 1) >> 1;
+            cp_async_wait_all();
             __syncwarp();
-            d0.j = t0 + kTileJ + lane;
-            d1.j = t0 + kTileJ + lane + 32;
-            if (d0.j < e) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
-            if (d1.j < e) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
-            pp_tile<R, true>(A, S, K, nt, T, J, tj, rnear2, ncount, lane);
-            fold_all<R>(S, K, T);
+            if (lane < 2 * npair) put_particle(S, lane, lane < nt, oh, ol);
+            if (lane + 32 < 2 * npair) put_particle(S, lane + 32, lane + 32 < nt, oh, ol);
+            __syncwarp();
+            const uint32_t n0 = t0 + kTileJ + lane, n1 = n0 + 32;
+            gather_particle(A, S, lane, n0 < e ? n0 : kNone);
+            gather_particle(A, S, lane + 32, n1 < e ? n1 : kNone);
+            cp_async_commit();
+            pp_tile<R, TAIL, true>(A, S, K, npair, J, tj, rnear2, ncount, lane);
+            fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
+        cp_async_wait_all();
+        __syncwarp();
     }
-    // (2) the other list particles: indices two tiles ahead, data one tile ahead
+    // (2) the other list particles: data gathered one tile ahead, indices two
     {
         const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
-        PRaw d0, d1;
-        d0.j = list_index(A, j0 + lane, j1, b);
-        d1.j = list_index(A, j0 + lane + 32, j1, b);
-        uint32_t ib0 = list_index(A, j0 + kTileJ + lane, j1, b), ib1 = list_index(A, j0 + kTileJ + lane + 32, j1, b);
-        if (d0.j != kNone) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
-        if (d1.j != kNone) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+        gather_particle(A, S, lane, list_index(A, j0 + lane, j1, b));
+        gather_particle(A, S, lane + 32, list_index(A, j0 + lane + 32, j1, b));
+        cp_async_commit();
+        uint32_t ib0 = list_index(A, j0 + kTileJ + lane, j1, b);
+        uint32_t ib1 = list_index(A, j0 + kTileJ + lane + 32, j1, b);
         for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
             const int nt = (int)min((int64_t)kTileJ, j1 - t0);
-            put_particle(S, lane, d0, lane < nt, oh, ol);
-            put_particle(S, lane + 32, d1, lane + 32 < nt, oh, ol);
+            const int npair = (nt + 1) >> 1;
+            cp_async_wait_all();
             __syncwarp();
-            d0.j = ib0;
-            d1.j = ib1;
-            if (d0.j != kNone) { d0.h = A.phi[d0.j]; d0.l = A.plo[d0.j]; }
-            if (d1.j != kNone) { d1.h = A.phi[d1.j]; d1.l = A.plo[d1.j]; }
+            if (lane < 2 * npair) put_particle(S, lane, lane < nt, oh, ol);
+            if (lane + 32 < 2 * npair) put_particle(S, lane + 32, lane + 32 < nt, oh, ol);
+            __syncwarp();
+            gather_particle(A, S, lane, ib0);
+            gather_particle(A, S, lane + 32, ib1);
+            cp_async_commit();
             ib0 = list_index(A, t0 + 2 * kTileJ + lane, j1, b);
             ib1 = list_index(A, t0 + 2 * kTileJ + lane + 32, j1, b);
-            pp_tile<R, false>(A, S, K, nt, T, J, tj, rnear2, ncount, lane);
-            fold_all<R>(S, K, T);
+            pp_tile<R, TAIL, false>(A, S, K, npair, J, tj, rnear2, ncount, lane);
+            fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
+        cp_async_wait_all();
+        __syncwarp();
     }
     if (ncount > 0) flush_near(A, S, ncount, lane);
-    // (3) list cells: indices two tiles ahead, data one tile ahead
+    // (3) list cells: data gathered one tile ahead, indices two
     {
         const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2v = r0;
-        int32_t ca = cell_index(A, c0 + lane, c1);
+        gather_cell(A, S, lane, cell_index(A, c0 + lane, c1), ORDER >= 2 ? 3 : 2);
+        cp_async_commit();
         int32_t cb = cell_index(A, c0 + kTileC + lane, c1);
-        if (ca >= 0) {
-            r0 = A.cell32[3 * (int64_t)ca];
-            r1 = A.cell32[3 * (int64_t)ca + 1];
-            if (ORDER >= 2) r2v = A.cell32[3 * (int64_t)ca + 2];
-        }
         for (int64_t t0 = c0; t0 < c1; t0 += kTileC) {
             const int nt = (int)min((int64_t)kTileC, c1 - t0);
-            if (lane < nt) put_cell<ORDER>(S, lane, r0, r1, r2v, oh, ol);
+            const int npair = (nt + 1) >> 1;
+            cp_async_wait_all();
             __syncwarp();
-            if (cb >= 0) {
-                r0 = A.cell32[3 * (int64_t)cb];
-                r1 = A.cell32[3 * (int64_t)cb + 1];
-                if (ORDER >= 2) r2v = A.cell32[3 * (int64_t)cb + 2];
-            }
+            if (lane < 2 * npair) put_cell<ORDER>(S, lane, lane < nt, oh, ol);
+            __syncwarp();
+            gather_cell(A, S, lane, cb, ORDER >= 2 ? 3 : 2);
+            cp_async_commit();
             cb = cell_index(A, t0 + 2 * kTileC + lane, c1);
-            pc_tile<R, ORDER>(A, S, K, nt, T, J, tj);
-            fold_all<R>(S, K, T);
+            pc_tile<R, TAIL, ORDER>(A, S, K, npair, J, tj);
+            fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
+        cp_async_wait_all();
+        __syncwarp();
     }
     __syncwarp();
     // (4) outputs: full slots directly, the tail slot after a reduction over its J lanes
 #pragma unroll
-    for (int r = 0; r < R + 1; ++r) {
+    for (int r = 0; r < NS; ++r) {
         const bool tail = (r == R);
-        if (tail && T == 0) break;
+        const int s = 32 * r + lane;
+        double a[3];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int s = h ? K.s1[r] : K.s0[r];
-            double a[3];
+        for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
+        if (tail)
+            for (int o = T; o < 32; o <<= 1)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
-            if (tail)
-                for (int o = T; o < 32; o <<= 1)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
-            const bool valid = h ? K.v1[r] : K.v0[r];
-            if (valid && (!tail || tj == 0)) {
-                const uint32_t i = h ? K.i1v[r] : K.i0v[r];
-                if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
-                A.ax[i] = a[0];
-                A.ay[i] = a[1];
-                A.az[i] = a[2];
-            }
+                for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+        if (K.vl[r] && (!tail || tj == 0)) {
+            const uint32_t i = K.iv[r];
+            if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
+            A.ax[i] = a[0];
+            A.ay[i] = a[1];
+            A.az[i] = a[2];
         }
     }
     __syncwarp();
@@ -577,31 +592,30 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     const uint32_t ext = max(G.b.x - G.a.x, max(G.b.y - G.a.y, G.b.z - G.a.z)) + 1u;
     const float rn = A.fp.near_frac * (float)ext * A.fp.h;
     const float rnear2 = fmaxf(A.fp.rnear_min2, rn * rn) + A.fp.eps2f;
-    // chunks: 64 particles (one full pair-slot) while more than 96 remain; the
-    // last chunk is a full pair-slot plus a tail of at most 32, a partly
-    // filled pair-slot (33..64 left), or a tail alone (at most 32 left)
+    // chunks of at most 96 particles: R full slots plus a tail of at most 16
     for (uint32_t i0 = b; i0 < e;) {
-        const uint32_t rem = e - i0;
-        int T = 0;
-        uint32_t cnt;
-        bool full;
-        if (rem > 96) {
-            full = true;
-            cnt = 64;
-        } else if (rem > 64 || rem <= 32) {
-            full = rem > 64;
-            const int t = (int)(full ? rem - 64 : rem), need = (t + 1) >> 1;
+        const uint32_t rem = e - i0, cnt = min(rem, 96u);
+        int R = (int)(cnt >> 5), t = (int)(cnt & 31), T = 0;
+        if (t > 16) {
+            ++R;  // more than half a slot left: a full one
+        } else if (t > 0) {
             T = 1;
-            while (T < need) T <<= 1;
-            cnt = rem;
-        } else {
-            full = true;
-            cnt = rem;
+            while (T < t) T <<= 1;
         }
-        if (full)
-            group_chunk<1, ORDER>(A, S, k, b, i0 + cnt, i0, T, oh, ol, rnear2, lane);
-        else
-            group_chunk<0, ORDER>(A, S, k, b, i0 + cnt, i0, T, oh, ol, rnear2, lane);
+        const uint32_t ce = i0 + cnt;
+        if (T > 0) {
+            switch (R) {
+                case 0: group_chunk<0, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
+                case 1: group_chunk<1, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
+                default: group_chunk<2, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
+            }
+        } else {
+            switch (R) {
+                case 1: group_chunk<1, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
+                case 2: group_chunk<2, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
+                default: group_chunk<3, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
+            }
+        }
         i0 += cnt;
     }
 }
