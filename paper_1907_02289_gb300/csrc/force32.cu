@@ -43,9 +43,12 @@ namespace {
 #ifndef BH_F32_MINB
 #define BH_F32_MINB 4  // resident blocks per SM the register budget is sized for
 #endif
-constexpr int kW32 = 4;     // warps per block
-constexpr int kTileJ = 64;  // list particles per tile (32 pairs, 2 per lane)
-constexpr int kTileC = 32;  // list cells per tile (16 pairs, 1 per lane)
+#ifndef BH_F32_TILE
+#define BH_F32_TILE 1  // list particles per tile = 64 x this, list cells = 32 x this
+#endif
+constexpr int kW32 = 4;                   // warps per block
+constexpr int kTileJ = 64 * BH_F32_TILE;  // list particles per tile (2 per lane per 64)
+constexpr int kTileC = 32 * BH_F32_TILE;  // list cells per tile (1 per lane per 32)
 constexpr int kSlots = 3;   // i-slots per lane (full slots + tail)
 constexpr int kNearCap = 32 + 2 * kSlots * 32;
 constexpr uint32_t kNone = 0xffffffffu;
@@ -475,21 +478,31 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     __syncwarp();
 
     // (1) the group's own particles (contiguous), i = j excluded
+    constexpr int PJ = kTileJ / 32, PC = kTileC / 32;  // staged entries per lane
+    // (1) the group's own particles (contiguous), i = j excluded
     {
-        gather_particle(A, S, lane, b + lane < e ? b + lane : kNone);
-        gather_particle(A, S, lane + 32, b + lane + 32 < e ? b + lane + 32 : kNone);
+#pragma unroll
+        for (int s = 0; s < PJ; ++s) {
+            const uint32_t jj = b + lane + 32 * s;
+            gather_particle(A, S, lane + 32 * s, jj < e ? jj : kNone);
+        }
         cp_async_commit();
         for (uint32_t t0 = b; t0 < e; t0 += kTileJ) {
             const int nt = (int)min((uint32_t)kTileJ, e - t0);
             const int npair = (nt + 1) >> 1;
             cp_async_wait_all();
             __syncwarp();
-            if (lane < 2 * npair) put_particle(S, lane, lane < nt, oh, ol);
-            if (lane + 32 < 2 * npair) put_particle(S, lane + 32, lane + 32 < nt, oh, ol);
+#pragma unroll
+            for (int s = 0; s < PJ; ++s) {
+                const int u = lane + 32 * s;
+                if (u < 2 * npair) put_particle(S, u, u < nt, oh, ol);
+            }
             __syncwarp();
-            const uint32_t n0 = t0 + kTileJ + lane, n1 = n0 + 32;
-            gather_particle(A, S, lane, n0 < e ? n0 : kNone);
-            gather_particle(A, S, lane + 32, n1 < e ? n1 : kNone);
+#pragma unroll
+            for (int s = 0; s < PJ; ++s) {
+                const uint32_t jj = t0 + kTileJ + lane + 32 * s;
+                gather_particle(A, S, lane + 32 * s, jj < e ? jj : kNone);
+            }
             cp_async_commit();
             pp_tile<R, TAIL, true>(A, S, K, npair, J, tj, rnear2, ncount, lane);
             fold_all<R, TAIL>(S, K, lane);
@@ -501,24 +514,30 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     // (2) the other list particles: data gathered one tile ahead, indices two
     {
         const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
-        gather_particle(A, S, lane, list_index(A, j0 + lane, j1, b));
-        gather_particle(A, S, lane + 32, list_index(A, j0 + lane + 32, j1, b));
+        uint32_t ib[PJ];
+#pragma unroll
+        for (int s = 0; s < PJ; ++s) {
+            gather_particle(A, S, lane + 32 * s, list_index(A, j0 + lane + 32 * s, j1, b));
+            ib[s] = list_index(A, j0 + kTileJ + lane + 32 * s, j1, b);
+        }
         cp_async_commit();
-        uint32_t ib0 = list_index(A, j0 + kTileJ + lane, j1, b);
-        uint32_t ib1 = list_index(A, j0 + kTileJ + lane + 32, j1, b);
         for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
             const int nt = (int)min((int64_t)kTileJ, j1 - t0);
             const int npair = (nt + 1) >> 1;
             cp_async_wait_all();
             __syncwarp();
-            if (lane < 2 * npair) put_particle(S, lane, lane < nt, oh, ol);
-            if (lane + 32 < 2 * npair) put_particle(S, lane + 32, lane + 32 < nt, oh, ol);
+#pragma unroll
+            for (int s = 0; s < PJ; ++s) {
+                const int u = lane + 32 * s;
+                if (u < 2 * npair) put_particle(S, u, u < nt, oh, ol);
+            }
             __syncwarp();
-            gather_particle(A, S, lane, ib0);
-            gather_particle(A, S, lane + 32, ib1);
+#pragma unroll
+            for (int s = 0; s < PJ; ++s) {
+                gather_particle(A, S, lane + 32 * s, ib[s]);
+                ib[s] = list_index(A, t0 + 2 * kTileJ + lane + 32 * s, j1, b);
+            }
             cp_async_commit();
-            ib0 = list_index(A, t0 + 2 * kTileJ + lane, j1, b);
-            ib1 = list_index(A, t0 + 2 * kTileJ + lane + 32, j1, b);
             pp_tile<R, TAIL, false>(A, S, K, npair, J, tj, rnear2, ncount, lane);
             fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
@@ -530,19 +549,30 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     // (3) list cells: data gathered one tile ahead, indices two
     {
         const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
-        gather_cell(A, S, lane, cell_index(A, c0 + lane, c1), ORDER >= 2 ? 3 : 2);
+        int32_t cb[PC];
+#pragma unroll
+        for (int s = 0; s < PC; ++s) {
+            gather_cell(A, S, lane + 32 * s, cell_index(A, c0 + lane + 32 * s, c1), ORDER >= 2 ? 3 : 2);
+            cb[s] = cell_index(A, c0 + kTileC + lane + 32 * s, c1);
+        }
         cp_async_commit();
-        int32_t cb = cell_index(A, c0 + kTileC + lane, c1);
         for (int64_t t0 = c0; t0 < c1; t0 += kTileC) {
             const int nt = (int)min((int64_t)kTileC, c1 - t0);
             const int npair = (nt + 1) >> 1;
             cp_async_wait_all();
             __syncwarp();
-            if (lane < 2 * npair) put_cell<ORDER>(S, lane, lane < nt, oh, ol);
+#pragma unroll
+            for (int s = 0; s < PC; ++s) {
+                const int u = lane + 32 * s;
+                if (u < 2 * npair) put_cell<ORDER>(S, u, u < nt, oh, ol);
+            }
             __syncwarp();
-            gather_cell(A, S, lane, cb, ORDER >= 2 ? 3 : 2);
+#pragma unroll
+            for (int s = 0; s < PC; ++s) {
+                gather_cell(A, S, lane + 32 * s, cb[s], ORDER >= 2 ? 3 : 2);
+                cb[s] = cell_index(A, t0 + 2 * kTileC + lane + 32 * s, c1);
+            }
             cp_async_commit();
-            cb = cell_index(A, t0 + 2 * kTileC + lane, c1);
             pc_tile<R, TAIL, ORDER>(A, S, K, npair, J, tj);
             fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
