@@ -75,6 +75,7 @@ struct Smem32 {
         float4 c[kTileC][3];
     } raw;
     uint32_t raw_id[kTileJ];
+    uint8_t trig[kTileJ / 2];  // list pairs of the current tile that had a near pair
     uint32_t near_i[kNearCap];
     uint32_t near_j[kNearCap];
     uint8_t near_s[kNearCap];
@@ -160,7 +161,8 @@ __device__ __forceinline__ void near_pair(const Args& A, uint32_t i, uint32_t j,
     out[2] = f * dz;
 }
 
-__device__ __forceinline__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
+// Rare path, kept out of line so that the hot loops stay compact.
+__device__ __noinline__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
     for (int base = 0; base < ncount; base += 32) {
         const int u = base + lane;
         bool contact = false;
@@ -407,8 +409,12 @@ __device__ __forceinline__ void put_cell(Smem32& S, int u, bool real, const floa
 template <int R, bool TAIL, bool SELF>
 __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj,
                                         float rnear2, int& ncount, int lane) {
+    // The hot loops only mask near pairs and note (warp-uniformly) which list
+    // pairs had one; the near pairs are queued after the loop.
     const float2 eps2 = f2(A.fp.eps2f);
-    if constexpr (R > 0)
+    if constexpr (R > 0) {
+        int ntrig = 0;
+#pragma unroll 1
         for (int q = 0; q < npair; ++q) {
             const JPair P = S.t.p.jp[q];
             const uint32_t* jid = &S.t.p.jid[2 * q];
@@ -417,23 +423,41 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             for (int r = 0; r < R; ++r)
                 any |= pp_body<SELF>(P, jid, K.iv[r], K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2,
                                      rnear2);
-            if (__any_sync(0xffffffffu, any))
-                queue_pair<SELF, R, TAIL>(S, ncount, P, jid, K, 0, R, false, eps2, rnear2, lane);
+            if (__any_sync(0xffffffffu, any)) {
+                if (lane == 0) S.trig[ntrig] = (uint8_t)q;
+                ++ntrig;
+            }
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int t = 0; t < ntrig; ++t) {
+            const int q = S.trig[t];
+            queue_pair<SELF, R, TAIL>(S, ncount, S.t.p.jp[q], &S.t.p.jid[2 * q], K, 0, R, false, eps2, rnear2, lane);
             if (ncount >= 32) flush_near(A, S, ncount, lane);
         }
+    }
     if constexpr (TAIL) {
         const int trips = (npair + J - 1) / J;
+        int ntrig = 0;
+#pragma unroll 1
         for (int u = 0; u < trips; ++u) {
             const int q = u * J + tj;
-            const bool ok = q < npair;
-            const JPair P = S.t.p.jp[ok ? q : 0];
-            const uint32_t* jid = &S.t.p.jid[ok ? 2 * q : 0];
             bool any = false;
-            if (ok)
-                any = pp_body<SELF>(P, jid, K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2,
-                                    rnear2);
-            if (__any_sync(0xffffffffu, any))
-                queue_pair<SELF, R, TAIL>(S, ncount, P, jid, K, R, R + 1, ok, eps2, rnear2, lane);
+            if (q < npair)
+                any = pp_body<SELF>(S.t.p.jp[q], &S.t.p.jid[2 * q], K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R],
+                                    K.gz[R], eps2, rnear2);
+            if (__any_sync(0xffffffffu, any)) {
+                if (lane == 0) S.trig[ntrig] = (uint8_t)u;
+                ++ntrig;
+            }
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int t = 0; t < ntrig; ++t) {
+            const int q = S.trig[t] * J + tj;
+            const bool ok = q < npair;
+            queue_pair<SELF, R, TAIL>(S, ncount, S.t.p.jp[ok ? q : 0], &S.t.p.jid[ok ? 2 * q : 0], K, R, R + 1, ok,
+                                      eps2, rnear2, lane);
             if (ncount >= 32) flush_near(A, S, ncount, lane);
         }
     }
@@ -443,12 +467,14 @@ template <int R, bool TAIL, int ORDER>
 __device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj) {
     const float2 eps2 = f2(A.fp.eps2f);
     if constexpr (R > 0)
+#pragma unroll 1
         for (int q = 0; q < npair; ++q) {
             const CPair& Cp = S.t.cp[q];
 #pragma unroll
             for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
         }
     if constexpr (TAIL)
+#pragma unroll 1
         for (int q = tj; q < npair; q += J)
             pc_body<ORDER>(S.t.cp[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
 }
