@@ -339,6 +339,27 @@ int bh_get_moments(bh_ctx* ctx, double* M, double* c3, double* Q6) {
     if (!c) return BH_E_INVAL;
     if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
     const size_t nn = (size_t)c->n_nodes;
+    if (c->prm.precision == BH_PREC_FP32) {
+        // the FP32 path keeps FP32 records: centre as hi + lo, M, Q (traceless)
+        std::vector<float4> rec(nn * 3);
+        BH_CUDA(c, cudaMemcpyAsync(rec.data(), c->cell32.p, nn * 3 * sizeof(float4), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        BH_TRY(bh::read_status(c));
+        for (size_t k = 0; k < nn; ++k) {
+            const float4 h = rec[3 * k], l = rec[3 * k + 1], u = rec[3 * k + 2];
+            if (M) M[k] = h.w;
+            if (c3) {
+                c3[k] = (double)h.x + (double)l.x;
+                c3[nn + k] = (double)h.y + (double)l.y;
+                c3[2 * nn + k] = (double)h.z + (double)l.z;
+            }
+            if (Q6) {
+                const double q[6] = {l.w, u.z, -((double)l.w + (double)u.z), u.x, u.y, u.w};
+                for (int a = 0; a < 6; ++a) Q6[6 * k + a] = q[a];
+            }
+        }
+        return BH_OK;
+    }
     BH_D2H(c, M, c->M.p, nn * 8);
     if (c3) {
         double* cys = c3 + nn;

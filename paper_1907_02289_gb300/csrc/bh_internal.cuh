@@ -161,6 +161,7 @@ int stage_lists(Ctx* c);                           // walk (count, fill) + parti
 
 // force.cu
 int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of particles
+int build_order32(Ctx* c);                         // FP32 kernel's group order (per list build)
 int stage_force(Ctx* c, bh_particles* p, bool add_central);
 
 // update.cu

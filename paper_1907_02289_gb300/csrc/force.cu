@@ -210,7 +210,7 @@ int stage_force(Ctx* c, bh_particles* p, bool add_central) {
         BH_LAUNCH(c);
         return BH_OK;
     }
-    BH_TRY(stage_split(c, p));
+    // the hi/lo split and the FP32 records were made by stage_moments
     return launch_force32(c, p, fp, add_central);
 }
 

@@ -85,6 +85,7 @@ struct Smem32 {
 
 struct Args {
     int64_t ng;
+    const int32_t* order;  // processing order of the groups (NULL: list order)
     const int32_t* groups;
     const uint32_t* begin;
     const uint32_t* end;
@@ -635,8 +636,9 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem32* sm = reinterpret_cast<Smem32*>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t k = (int64_t)blockIdx.x * kW32 + w;
-    if (k >= A.ng) return;
+    const int64_t slot = (int64_t)blockIdx.x * kW32 + w;
+    if (slot >= A.ng) return;
+    const int64_t k = A.order ? A.order[slot] : slot;  // groups of one size class run side by side
     Smem32& S = sm[w];
     const int32_t g = A.groups[k];
     const uint32_t b = A.begin[g], e = A.end[g];
@@ -676,6 +678,41 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     }
 }
 
+// Size class of a group = the (R, tail) variant of its last chunk; classes
+// are numbered so that larger work comes first.
+__device__ __forceinline__ int size_class(uint32_t n_i) {
+    const uint32_t rem = n_i - 96u * ((n_i - 1u) / 96u);
+    int R = (int)(rem >> 5);
+    const int t = (int)(rem & 31);
+    bool tail = false;
+    if (t > 16)
+        ++R;
+    else if (t > 0)
+        tail = true;
+    const int cls = 2 * R + (tail ? 1 : 0) - 1;  // (0,T)=0 (1,F)=1 (1,T)=2 (2,F)=3 (2,T)=4 (3,F)=5
+    return 5 - cls;
+}
+
+__global__ void k_order_hist(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+                             const uint32_t* __restrict__ end, unsigned long long* cnt) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    const int32_t g = groups[k];
+    atomicAdd(&cnt[size_class(end[g] - begin[g])], 1ull);
+}
+
+__global__ void k_order_scatter(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+                                const uint32_t* __restrict__ end, const unsigned long long* __restrict__ cnt,
+                                unsigned long long* cursor, int32_t* __restrict__ order) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    const int32_t g = groups[k];
+    const int cls = size_class(end[g] - begin[g]);
+    unsigned long long off = 0;
+    for (int c = 0; c < cls; ++c) off += cnt[c];
+    order[off + atomicAdd(&cursor[cls], 1ull)] = (int32_t)k;
+}
+
 // FP64 pass over the contact candidates: Eq. (1) in the oracle's operation
 // order (gravity at r_coll + spring + dashpot, or plain gravity if the FP64
 // decision says r > r_coll), added to the acceleration of i.
@@ -700,9 +737,25 @@ __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned lon
 
 }  // namespace
 
+// Processing order of the groups for the FP32 kernel (once per list build):
+// by size class, so that warps running side by side execute the same code.
+int build_order32(Ctx* c) {
+    const int64_t ng = c->n_groups;
+    BH_TRY(grow(c, c->order, (size_t)ng + 1, "group order"));
+    unsigned long long* cnt = c->d_small + 24;  // 6 counters + 6 cursors
+    BH_CUDA(c, cudaMemsetAsync(cnt, 0, 12 * sizeof(unsigned long long), c->stream));
+    k_order_hist<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, cnt);
+    BH_LAUNCH(c);
+    k_order_scatter<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, cnt, cnt + 6,
+                                                                c->order.p);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+
 int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_central) {
     Args A;
     A.ng = c->n_groups;
+    A.order = c->order.p;
     A.groups = c->groups.p;
     A.begin = c->begin.p;
     A.end = c->end.p;

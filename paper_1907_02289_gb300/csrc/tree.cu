@@ -237,6 +237,101 @@ __global__ void k_moments(int64_t ls, int64_t cnt, const uint32_t* __restrict__ 
     }
 }
 
+// Moments for the FP32 force path, all in FP32: offsets from a reference
+// point inside the node (its first particle, or its first child's centre)
+// are exact hi/lo differences; the centre of mass is kept as an FP32 hi/lo
+// pair (reference + offset), mass and traceless quadrupole in FP32.
+// Record layout: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz).
+__device__ __forceinline__ float dsub(float ah, float al, float bh, float bl) {
+    return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
+}
+
+template <int ORDER>
+__global__ void k_moments32(int64_t ls, int64_t cnt, const uint32_t* __restrict__ begin,
+                            const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
+                            const uint8_t* __restrict__ nchild, const float4* __restrict__ phi,
+                            const float4* __restrict__ plo, float4* cell32) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t k = ls + t;
+    const int nc = nchild[k];
+    float rh[3], rl[3];  // reference point (hi/lo)
+    float Mk = 0.f, s[3] = {0.f, 0.f, 0.f}, q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (nc == 0) {
+        const uint32_t b = begin[k], e = end[k];
+        const float4 h0 = phi[b], l0 = plo[b];
+        rh[0] = h0.x; rh[1] = h0.y; rh[2] = h0.z;
+        rl[0] = l0.x; rl[1] = l0.y; rl[2] = l0.z;
+        for (uint32_t i = b; i < e; ++i) {
+            const float4 h = phi[i], l = plo[i];
+            const float d[3] = {dsub(h.x, l.x, rh[0], rl[0]), dsub(h.y, l.y, rh[1], rl[1]), dsub(h.z, l.z, rh[2], rl[2])};
+            Mk += h.w;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s[a] = fmaf(h.w, d[a], s[a]);
+        }
+        const float inv = Mk > 0.f ? 1.f / Mk : 0.f;
+        const float dc[3] = {s[0] * inv, s[1] * inv, s[2] * inv};
+        if (ORDER >= 2)
+            for (uint32_t i = b; i < e; ++i) {
+                const float4 h = phi[i], l = plo[i];
+                const float d[3] = {dsub(h.x, l.x, rh[0], rl[0]) - dc[0], dsub(h.y, l.y, rh[1], rl[1]) - dc[1],
+                                    dsub(h.z, l.z, rh[2], rl[2]) - dc[2]};
+                const float d2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+                const float m3 = 3.f * h.w;
+                q[0] = fmaf(h.w, fmaf(3.f * d[0], d[0], -d2), q[0]);
+                q[1] = fmaf(h.w, fmaf(3.f * d[1], d[1], -d2), q[1]);
+                q[2] = fmaf(h.w, fmaf(3.f * d[2], d[2], -d2), q[2]);
+                q[3] = fmaf(m3 * d[0], d[1], q[3]);
+                q[4] = fmaf(m3 * d[0], d[2], q[4]);
+                q[5] = fmaf(m3 * d[1], d[2], q[5]);
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[a] = dc[a];
+    } else {
+        const int64_t f = first_child[k];
+        const float4 c0h = cell32[3 * f], c0l = cell32[3 * f + 1];
+        rh[0] = c0h.x; rh[1] = c0h.y; rh[2] = c0h.z;
+        rl[0] = c0l.x; rl[1] = c0l.y; rl[2] = c0l.z;
+        for (int cc = 0; cc < nc; ++cc) {
+            const float4 h = cell32[3 * (f + cc)], l = cell32[3 * (f + cc) + 1];
+            const float d[3] = {dsub(h.x, l.x, rh[0], rl[0]), dsub(h.y, l.y, rh[1], rl[1]), dsub(h.z, l.z, rh[2], rl[2])};
+            Mk += h.w;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s[a] = fmaf(h.w, d[a], s[a]);
+        }
+        const float inv = Mk > 0.f ? 1.f / Mk : 0.f;
+        const float dc[3] = {s[0] * inv, s[1] * inv, s[2] * inv};
+        if (ORDER >= 2)
+            for (int cc = 0; cc < nc; ++cc) {
+                const float4 h = cell32[3 * (f + cc)], l = cell32[3 * (f + cc) + 1], u = cell32[3 * (f + cc) + 2];
+                const float D[3] = {dsub(h.x, l.x, rh[0], rl[0]) - dc[0], dsub(h.y, l.y, rh[1], rl[1]) - dc[1],
+                                    dsub(h.z, l.z, rh[2], rl[2]) - dc[2]};
+                const float D2 = fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2]));
+                const float Mc = h.w, m3 = 3.f * Mc;
+                q[0] += l.w + Mc * fmaf(3.f * D[0], D[0], -D2);
+                q[1] += u.z + Mc * fmaf(3.f * D[1], D[1], -D2);
+                q[2] += -(l.w + u.z) + Mc * fmaf(3.f * D[2], D[2], -D2);
+                q[3] += u.x + m3 * D[0] * D[1];
+                q[4] += u.y + m3 * D[0] * D[2];
+                q[5] += u.w + m3 * D[1] * D[2];
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[a] = dc[a];
+    }
+    // centre = reference + offset, renormalised into a hi/lo pair
+    float ch[3], cl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = __fadd_rn(rl[a], s[a]);
+        const float hi = __fadd_rn(rh[a], lo);
+        ch[a] = hi;
+        cl[a] = __fsub_rn(lo, __fsub_rn(hi, rh[a]));
+    }
+    cell32[3 * k + 0] = make_float4(ch[0], ch[1], ch[2], Mk);
+    cell32[3 * k + 1] = make_float4(cl[0], cl[1], cl[2], q[0]);
+    cell32[3 * k + 2] = make_float4(q[3], q[4], q[1], q[5]);
+}
+
 __global__ void k_group_mark(int64_t nn, const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end,
                              const int32_t* __restrict__ parent, const uint8_t* __restrict__ nchild,
                              int n_g, int32_t* __restrict__ gmark) {
@@ -326,14 +421,32 @@ int stage_boxes(Ctx* c) {
 
 int stage_moments(Ctx* c, const bh_particles* p) {
     const int64_t nn = c->n_nodes;
+    const bool f32 = c->prm.precision == BH_PREC_FP32;
+    const int depth = (int)c->lvl_start.size() - 1;
+    if (f32) {
+        // FP32 path: hi/lo split of the particles, then FP32 moments with a
+        // hi/lo centre (no FP64 arithmetic per node)
+        BH_TRY(grow(c, c->cell32, (size_t)nn * 3, "FP32 cell records"));
+        BH_TRY(stage_split(c, p));
+        for (int lev = depth - 1; lev >= 0; --lev) {
+            const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
+            if (c->prm.order >= 2)
+                k_moments32<2><<<blocks_for(cnt, 128), 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p,
+                                                                            c->first_child.p, c->nchild.p,
+                                                                            c->phi.p, c->plo.p, c->cell32.p);
+            else
+                k_moments32<1><<<blocks_for(cnt, 128), 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p,
+                                                                            c->first_child.p, c->nchild.p,
+                                                                            c->phi.p, c->plo.p, c->cell32.p);
+            BH_LAUNCH(c);
+        }
+        return BH_OK;
+    }
     BH_TRY(grow(c, c->M, (size_t)nn, "moments M"));
     BH_TRY(grow(c, c->cx, (size_t)nn, "moments cx"));
     BH_TRY(grow(c, c->cy, (size_t)nn, "moments cy"));
     BH_TRY(grow(c, c->cz, (size_t)nn, "moments cz"));
     BH_TRY(grow(c, c->Q, (size_t)nn * 6, "moments Q"));
-    const bool f32 = c->prm.precision == BH_PREC_FP32;
-    if (f32) BH_TRY(grow(c, c->cell32, (size_t)nn * 3, "FP32 cell records"));
-    const int depth = (int)c->lvl_start.size() - 1;
     for (int lev = depth - 1; lev >= 0; --lev) {
         const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
         const unsigned nb = blocks_for(cnt, 128);

@@ -210,6 +210,7 @@ int stage_lists(Ctx* c) {
     k_expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p,
                                                              c->end.p, c->cnt_j.p, c->JJ.p);
     BH_LAUNCH(c);
+    if (c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
     return BH_OK;
 }
 

@@ -262,3 +262,20 @@ def test_step_host_buffers_equal_device_path():
     out = D.numpy()
     for f in ("x", "y", "z", "vx", "vy", "vz", "id", "ax"):
         assert np.array_equal(out[f], H.a[f]), f
+
+
+@pytest.mark.parametrize("name", ["ring20k", "ring_ragged_65537", "cube4096"])
+def test_fp32_moments_close(built, name):
+    """The FP32 path's node records (FP32 mass and quadrupole, hi/lo centre)
+    against the oracle's FP64 moments of the same tree."""
+    P, prm, ref = built[name]
+    ctx, D = gpu_build(P, prm, precision=1, forces=False)
+    mo = ctx.bh_get_moments()
+    t = ref.tree
+    s = ref.L * 2.0 ** -t["level"].astype(float)  # node side
+    M = ref.mom["M"]
+    assert np.allclose(mo["M"], M, rtol=2e-6, atol=0)
+    for f in ("cx", "cy", "cz"):
+        assert np.all(np.abs(mo[f] - ref.mom[f]) <= 2e-6 * s + 1e-15)
+    scale = (M * s * s)[:, None]
+    assert np.all(np.abs(mo["Q"] - ref.mom["Q"]) <= 1e-5 * scale)
