@@ -180,9 +180,6 @@ ForceParams force_params(const Ctx* c) {
     fp.etaf = (float)p.eta;
     fp.rcollf = (float)p.r_coll;
     fp.Gf = (float)p.G;
-    fp.rnear_min2 = (float)(4.0 * fp.rc2);
-    fp.near_frac = 0.05f;
-    fp.h = (float)(c->h_L / 2097152.0);
     fp.order = p.order;
     return fp;
 }

@@ -4,19 +4,20 @@
 // record.
 //
 // Shift: every FP64 coordinate is split once per evaluation into FP32 hi/lo
-// parts; the shifted coordinate (x_hi - o_hi) + (x_lo - o_lo) is within one
-// FP32 rounding of the FP64-shifted value, so no FP64 arithmetic (1/64 of the
-// FP32 rate on this GPU) runs per list entry.
+// parts, so no FP64 arithmetic (1/64 of the FP32 rate on this GPU) runs per
+// list entry.  List particles and the group's particles are held relative to
+// the origin as FP32 hi/lo pairs, and the separation of a pair is formed as
+// (x_hi,j - x_hi,i) + (x_lo,j - x_lo,i): exact to an FP32 rounding of the
+// separation itself, however wide the group is.  List cells, which the
+// opening test keeps at least a cell size away, use the hi part alone.
 //
-// Near pairs: the FP32 separation of two particles carries an absolute error
-// of ~2^-23 x (group extent), which matters only when they are much closer
-// than the group is wide.  Pairs closer than max(2 r_coll, 0.05 x group
-// extent) are masked out of the fast loop and queued per warp.  Queued pairs
-// are evaluated in batches (one pair per lane) from the hi/lo parts
-// directly, whose difference is exact to ~2^-48 (gravity), or -- when they
-// may be in contact -- appended to a global list that a separate kernel
-// evaluates in FP64 in the oracle's operation order (contact term of Eq. (1)
-// and the r <= r_coll decision).
+// Gravity inside r_coll (Eq. 1) is G m_j r / (r_coll^2 + eps^2)^(3/2), so
+// max(r^2, r_coll^2) + eps^2 in the fast loop gives it for every pair (and
+// 0 for i = j).  Pairs that may be in contact are queued per warp and
+// appended to a global list; a separate FP64 kernel adds their contact term
+// of Eq. (1) in the oracle's operation order (the r <= r_coll decision
+// included), with every lane busy -- FP64 inside the warp loop would leave
+// 31 lanes idle at 1/64 of the FP32 rate.
 //
 // Summation: FP32 partial sums per tile (even and odd list entries apart),
 // folded after every tile into a compensated (TwoSum) hi/lo accumulator in
@@ -29,8 +30,9 @@
 // than 3.  List entries are staged in pairs in shared memory and broadcast,
 // and the pair (j, j+1) is evaluated with packed f32x2 instructions (FADD2,
 // FFMA2, FMUL2) against the i-particle held as (x_i, x_i), which halves the
-// issue slots per interaction.  List tiles are gathered one tile ahead
-// (indices two tiles ahead) so that the gathers overlap the arithmetic.  The
+// issue slots per interaction.  The next tile is gathered with cp.async
+// while the current one is evaluated.  Groups are processed in order of
+// size class so that warps running side by side execute the same code.  The
 // group's own particles are evaluated first in a phase that excludes i = j;
 // the expanded list holds only the other particles.
 #include <cmath>
@@ -49,12 +51,17 @@ namespace {
 constexpr int kW32 = 4;                   // warps per block
 constexpr int kTileJ = 64 * BH_F32_TILE;  // list particles per tile (2 per lane per 64)
 constexpr int kTileC = 32 * BH_F32_TILE;  // list cells per tile (1 per lane per 32)
-constexpr int kSlots = 3;   // i-slots per lane (full slots + tail)
-constexpr int kNearCap = 32 + 2 * kSlots * 32;
+constexpr int kSlots = 3;                 // i-slots per lane (full slots + tail)
+constexpr int kQueueCap = 32 + 2 * kSlots * 32;
 constexpr uint32_t kNone = 0xffffffffu;
 
-struct JPair {  // two list particles, coordinates relative to the group origin
-    float2 x, y, z, m;
+// Pair-term modes: contact candidates detected (r_coll > 0); plain (no
+// contact, r_coll^2 + eps^2 > 0); mask (r_coll = eps = 0: coincident pairs
+// masked out explicitly).
+constexpr int kContact = 0, kPlain = 1, kMask = 2;
+
+struct __align__(16) JPair {  // two list particles relative to the origin (hi/lo)
+    float2 x, y, z, m, xl, yl, zl, pad;
 };
 struct CPair {  // two cells: centre relative to the origin, mass, negated quadrupole
     float2 x, y, z, m, qxx, qxy, qxz, qyy, qyz, qzz;
@@ -75,12 +82,11 @@ struct Smem32 {
         float4 c[kTileC][3];
     } raw;
     uint32_t raw_id[kTileJ];
-    uint8_t trig[kTileJ / 2];  // list pairs of the current tile that had a near pair
-    uint32_t near_i[kNearCap];
-    uint32_t near_j[kNearCap];
-    uint8_t near_s[kNearCap];
-    float ahi[32 * kSlots][3];  // compensated fast-loop sums (G-free), hi part
-    float alo[32 * kSlots][3];  // low part; G-free near-pair results are added here too
+    uint8_t trig[kTileJ / 2];  // list pairs of the current tile with a contact candidate
+    uint32_t q_i[kQueueCap];   // contact candidates (i, j) waiting for the global list
+    uint32_t q_j[kQueueCap];
+    float ahi[32 * kSlots][3];  // compensated sums (G-free), hi part
+    float alo[32 * kSlots][3];  // low part
 };
 
 struct Args {
@@ -96,7 +102,6 @@ struct Args {
     const float4* phi;
     const float4* plo;
     const float4* cell32;
-    const WalkNode* wnode;
     const double *x, *y, *z;
     double *ax, *ay, *az;
     uint2* contacts;               // (i, j) pairs for the FP64 contact pass
@@ -106,6 +111,8 @@ struct Args {
     int64_t nn;
     int* status;
     ForceParams fp;
+    float floor2;   // r_coll^2 + eps^2 (or eps^2)
+    float rc2chk;   // r^2 below this (FP32) may be a contact: r_coll^2 (1 + 1e-5)
     bool add_central;
 };
 
@@ -113,6 +120,16 @@ __device__ __forceinline__ float rel(float hi, float lo, float ohi, float olo) {
     return __fadd_rn(__fsub_rn(hi, ohi), __fsub_rn(lo, olo));
 }
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// (x_hi + x_lo) - (o_hi + o_lo) as an FP32 hi/lo pair.
+__device__ __forceinline__ void rel2(float xh, float xl, float oh, float ol, float& rh, float& rl) {
+    const float s = __fsub_rn(xh, oh);
+    const float v = __fsub_rn(s, xh);
+    const float e = __fsub_rn(__fsub_rn(xh, __fsub_rn(s, v)), __fadd_rn(oh, v));  // s + e == xh - oh exactly
+    const float t = __fadd_rn(e, __fsub_rn(xl, ol));
+    rh = __fadd_rn(s, t);
+    rl = __fsub_rn(t, __fsub_rn(rh, s));
+}
 
 // Central mass, FP64: r^-1 from the FP32 estimate refined by two Newton
 // steps y <- y (3 - r2 y^2) / 2 (each roughly doubles the correct bits).
@@ -130,87 +147,52 @@ __device__ __forceinline__ void central_newton(double G_Mc, double x, double y, 
 // ---- per-chunk state ------------------------------------------------------
 // Slot r (r < R): lane holds particle i0 + 32 r + lane.  Tail slot (r == R):
 // lane holds i0 + 32 R + (lane % T) and sees only the list pairs q with
-// q % J == lane / T.
+// q % J == lane / T.  Coordinates are stored negated, (-x, -x).
 template <int R, bool TAIL>
 struct Chunk {
     static constexpr int NS = R + (TAIL ? 1 : 0);
-    float2 nx[NS], ny[NS], nz[NS], gx[NS], gy[NS], gz[NS];
+    float2 nh[NS][3], nl[NS][3], g[NS][3];
     uint32_t iv[NS];
     bool vl[NS];
 };
 
-// ---- near pairs ------------------------------------------------------------
-// Gravity from the exact hi/lo difference (G-free), or hand the pair to the
-// FP64 contact pass.
-__device__ __forceinline__ void near_pair(const Args& A, uint32_t i, uint32_t j, float* out, bool& contact) {
-    const ForceParams& fp = A.fp;
-    const float4 hi = A.phi[i], li = A.plo[i], hj = A.phi[j], lj = A.plo[j];
-    const float dx = __fadd_rn(__fsub_rn(hj.x, hi.x), __fsub_rn(lj.x, li.x));
-    const float dy = __fadd_rn(__fsub_rn(hj.y, hi.y), __fsub_rn(lj.y, li.y));
-    const float dz = __fadd_rn(__fsub_rn(hj.z, hi.z), __fsub_rn(lj.z, li.z));
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    contact = fp.rc2f > 0.f && !(r2 > fp.rc2f * 1.00001f);
-    if (contact || r2 == 0.f) {  // contact candidate (FP64 pass) or coincident (no force)
-        out[0] = out[1] = out[2] = 0.f;
-        return;
-    }
-    const float s2 = r2 + fp.eps2f;
-    const float rs = rsqrtf(s2);
-    const float f = hj.w * (rs * rs * rs);
-    out[0] = f * dx;
-    out[1] = f * dy;
-    out[2] = f * dz;
-}
-
-// Rare path, kept out of line so that the hot loops stay compact.
-__device__ __noinline__ void flush_near(const Args& A, Smem32& S, int& ncount, int lane) {
-    for (int base = 0; base < ncount; base += 32) {
+// ---- contact candidates ---------------------------------------------------
+// Queued pairs go to the global list for the FP64 contact pass.
+__device__ __noinline__ void flush_queue(const Args& A, Smem32& S, int& qn, int lane) {
+    for (int base = 0; base < qn; base += 32) {
         const int u = base + lane;
-        bool contact = false;
-        uint32_t i = 0, j = 0;
-        if (u < ncount) {
-            const int s = S.near_s[u];
-            i = S.near_i[u];
-            j = S.near_j[u];
-            float a[3];
-            near_pair(A, i, j, a, contact);
-            if (!contact) {
-                atomicAdd(&S.alo[s][0], a[0]);
-                atomicAdd(&S.alo[s][1], a[1]);
-                atomicAdd(&S.alo[s][2], a[2]);
-            }
-        }
-        const unsigned msk = __ballot_sync(0xffffffffu, contact);
-        if (msk) {
-            unsigned long long base_pos = 0;
-            if (lane == 0) base_pos = atomicAdd(A.ncontact, (unsigned long long)__popc(msk));
-            base_pos = __shfl_sync(0xffffffffu, base_pos, 0);
-            if (contact) {
-                const unsigned long long pos = base_pos + __popc(msk & ((1u << lane) - 1u));
-                if ((int64_t)pos < A.contact_cap) A.contacts[pos] = make_uint2(i, j);
-            }
+        const bool has = u < qn;
+        const unsigned msk = __ballot_sync(0xffffffffu, has);
+        unsigned long long pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(A.ncontact, (unsigned long long)__popc(msk));
+        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+        if (has) {
+            const unsigned long long pos = pos0 + lane;
+            if ((int64_t)pos < A.contact_cap) A.contacts[pos] = make_uint2(S.q_i[u], S.q_j[u]);
         }
     }
     __syncwarp();
-    ncount = 0;
+    qn = 0;
 }
 
-// Queue the near pairs of list pair P (flags recomputed here; rare path)
-// for slots [r0, r1).  Warp-uniform call.
+// Queue the contact candidates of list pair P for slots [r0, r1) (flags
+// recomputed here; rare path).  Warp-uniform call.
 template <bool SELF, int R, bool TAIL>
-__device__ __forceinline__ void queue_pair(Smem32& S, int& ncount, const JPair& P, const uint32_t* jid,
-                                           const Chunk<R, TAIL>& K, int r0, int r1, bool tail_ok, float2 eps2,
-                                           float rnear2, int lane) {
+__device__ __forceinline__ void queue_pair(const Args& A, Smem32& S, int& qn, const JPair& P, const uint32_t* jid,
+                                           const Chunk<R, TAIL>& K, int r0, int r1, bool tail_ok, int lane) {
     constexpr int NS = Chunk<R, TAIL>::NS;
     unsigned bits = 0;
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
         if (r < r0 || r >= r1) continue;
         const bool ok = K.vl[r] && ((r < R) || tail_ok);
-        const float2 dx = __fadd2_rn(P.x, K.nx[r]), dy = __fadd2_rn(P.y, K.ny[r]), dz = __fadd2_rn(P.z, K.nz[r]);
-        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
-        if (ok && r2.x < rnear2 && (!SELF || jid[0] != K.iv[r])) bits |= 1u << (2 * r);
-        if (ok && r2.y < rnear2 && (!SELF || jid[1] != K.iv[r])) bits |= 2u << (2 * r);
+        float2 d[3];
+        d[0] = __fadd2_rn(__fadd2_rn(P.x, K.nh[r][0]), __fadd2_rn(P.xl, K.nl[r][0]));
+        d[1] = __fadd2_rn(__fadd2_rn(P.y, K.nh[r][1]), __fadd2_rn(P.yl, K.nl[r][1]));
+        d[2] = __fadd2_rn(__fadd2_rn(P.z, K.nh[r][2]), __fadd2_rn(P.zl, K.nl[r][2]));
+        const float2 r2 = __ffma2_rn(d[0], d[0], __ffma2_rn(d[1], d[1], __fmul2_rn(d[2], d[2])));
+        if (ok && r2.x < A.rc2chk && jid[0] != K.iv[r] && jid[0] != kNone) bits |= 1u << (2 * r);
+        if (ok && r2.y < A.rc2chk && jid[1] != K.iv[r] && jid[1] != kNone) bits |= 2u << (2 * r);
     }
     const int c = __popc(bits);
     int x = c;
@@ -220,51 +202,56 @@ __device__ __forceinline__ void queue_pair(Smem32& S, int& ncount, const JPair& 
         if (lane >= o) x += y;
     }
     const int total = __shfl_sync(0xffffffffu, x, 31);
-    int pos = ncount + x - c;
+    int pos = qn + x - c;
 #pragma unroll
     for (int r = 0; r < NS; ++r)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             if (bits & (1u << (2 * r + h))) {
-                S.near_i[pos] = K.iv[r];
-                S.near_j[pos] = jid[h];
-                S.near_s[pos] = (uint8_t)(32 * r + lane);
+                S.q_i[pos] = K.iv[r];
+                S.q_j[pos] = jid[h];
                 ++pos;
             }
-    ncount += total;
+    qn += total;
     __syncwarp();
 }
 
 // ---- interaction bodies ------------------------------------------------------
-// Fast particle-particle term of one list pair for one slot; returns whether
-// a near pair was masked out (self excluded when SELF).
-template <bool SELF>
-__device__ __forceinline__ bool pp_body(const JPair& P, const uint32_t* jid, uint32_t i, float2 nx, float2 ny,
-                                        float2 nz, float2& gx, float2& gy, float2& gz, float2 eps2,
-                                        float rnear2) {
-    const float2 dx = __fadd2_rn(P.x, nx);
-    const float2 dy = __fadd2_rn(P.y, ny);
-    const float2 dz = __fadd2_rn(P.z, nz);
-    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
-    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-    const float2 ri2 = __fmul2_rn(ri, ri);
-    float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), ri2);
-    const bool n0 = r2.x < rnear2, n1 = r2.y < rnear2;
-    f.x = n0 ? 0.f : f.x;
-    f.y = n1 ? 0.f : f.y;
-    gx = __ffma2_rn(f, dx, gx);
-    gy = __ffma2_rn(f, dy, gy);
-    gz = __ffma2_rn(f, dz, gz);
-    if (SELF) return (n0 && jid[0] != i) || (n1 && jid[1] != i);
-    return n0 || n1;
+// Particle-particle term of one list pair for one slot (G-free).  Returns
+// whether a contact candidate was seen (self excluded when SELF).
+template <int MODE, bool SELF>
+__device__ __forceinline__ bool pp_body(const Args& A, const JPair& P, const uint32_t* jid, uint32_t i,
+                                        const float2 (&nh)[3], const float2 (&nl)[3], float2 (&g)[3]) {
+    const float2 dx = __fadd2_rn(__fadd2_rn(P.x, nh[0]), __fadd2_rn(P.xl, nl[0]));
+    const float2 dy = __fadd2_rn(__fadd2_rn(P.y, nh[1]), __fadd2_rn(P.yl, nl[1]));
+    const float2 dz = __fadd2_rn(__fadd2_rn(P.z, nh[2]), __fadd2_rn(P.zl, nl[2]));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 s2;
+    if (MODE == kMask) {
+        s2 = r2;
+    } else {
+        s2.x = fmaxf(r2.x + A.fp.eps2f, A.floor2);
+        s2.y = fmaxf(r2.y + A.fp.eps2f, A.floor2);
+    }
+    const float2 ri = make_float2(rsqrt_approx(s2.x), rsqrt_approx(s2.y));
+    float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), __fmul2_rn(ri, ri));
+    if (MODE == kMask) {
+        f.x = r2.x > 0.f ? f.x : 0.f;
+        f.y = r2.y > 0.f ? f.y : 0.f;
+    }
+    g[0] = __ffma2_rn(f, dx, g[0]);
+    g[1] = __ffma2_rn(f, dy, g[1]);
+    g[2] = __ffma2_rn(f, dz, g[2]);
+    if (MODE != kContact) return false;
+    if (SELF) return (r2.x < A.rc2chk && jid[0] != i) || (r2.y < A.rc2chk && jid[1] != i);
+    return r2.x < A.rc2chk || r2.y < A.rc2chk;
 }
 
 template <int ORDER>
-__device__ __forceinline__ void pc_body(const CPair& Cp, float2 nx, float2 ny, float2 nz, float2& gx, float2& gy,
-                                        float2& gz, float2 eps2) {
-    const float2 dx = __fadd2_rn(Cp.x, nx);
-    const float2 dy = __fadd2_rn(Cp.y, ny);
-    const float2 dz = __fadd2_rn(Cp.z, nz);
+__device__ __forceinline__ void pc_body(const CPair& Cp, const float2 (&nh)[3], float2 (&g)[3], float2 eps2) {
+    const float2 dx = __fadd2_rn(Cp.x, nh[0]);
+    const float2 dy = __fadd2_rn(Cp.y, nh[1]);
+    const float2 dz = __fadd2_rn(Cp.z, nh[2]);
     const float2 R2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
     const float2 ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
     const float2 ri2 = __fmul2_rn(ri, ri);
@@ -278,35 +265,35 @@ __device__ __forceinline__ void pc_body(const CPair& Cp, float2 nx, float2 ny, f
         const float2 ri5 = __fmul2_rn(ri3, ri2);
         const float2 ri7 = __fmul2_rn(ri5, ri2);
         const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(Cp.m, ri3));
-        gx = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, gx));
-        gy = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, gy));
-        gz = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, gz));
+        g[0] = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, g[0]));
+        g[1] = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, g[1]));
+        g[2] = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, g[2]));
     } else {
         const float2 s = __fmul2_rn(Cp.m, ri3);
-        gx = __ffma2_rn(s, dx, gx);
-        gy = __ffma2_rn(s, dy, gy);
-        gz = __ffma2_rn(s, dz, gz);
+        g[0] = __ffma2_rn(s, dx, g[0]);
+        g[1] = __ffma2_rn(s, dy, g[1]);
+        g[2] = __ffma2_rn(s, dz, g[2]);
     }
 }
 
-__device__ __forceinline__ void fold(Smem32& S, int s, float2& gx, float2& gy, float2& gz) {
-    const float t[3] = {__fadd_rn(gx.x, gx.y), __fadd_rn(gy.x, gy.y), __fadd_rn(gz.x, gz.y)};
+__device__ __forceinline__ void fold(Smem32& S, int s, float2 (&g)[3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        const float t = __fadd_rn(g[c].x, g[c].y);
         const float hi = S.ahi[s][c];
-        const float s1 = __fadd_rn(hi, t[c]);
+        const float s1 = __fadd_rn(hi, t);
         const float bp = __fsub_rn(s1, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t[c], bp));
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t, bp));
         S.ahi[s][c] = s1;
         S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
+        g[c] = make_float2(0.f, 0.f);
     }
-    gx = gy = gz = make_float2(0.f, 0.f);
 }
 
 template <int R, bool TAIL>
 __device__ __forceinline__ void fold_all(Smem32& S, Chunk<R, TAIL>& K, int lane) {
 #pragma unroll
-    for (int r = 0; r < Chunk<R, TAIL>::NS; ++r) fold(S, 32 * r + lane, K.gx[r], K.gy[r], K.gz[r]);
+    for (int r = 0; r < Chunk<R, TAIL>::NS; ++r) fold(S, 32 * r + lane, K.g[r]);
 }
 
 // ---- staging -------------------------------------------------------------------
@@ -329,26 +316,31 @@ __device__ __forceinline__ void gather_particle(const Args& A, Smem32& S, int u,
     }
 }
 
-// Raw slot u -> shifted entry u of the particle tile (padding when !real).
+// Raw slot u -> entry u of the particle tile, relative to the origin as
+// hi/lo pairs (padding when !real).
 __device__ __forceinline__ void put_particle(Smem32& S, int u, bool real, const float (&oh)[3],
                                              const float (&ol)[3]) {
-    float px, py, pz, pm;
+    float ph[3], pl[3], pm;
     if (real) {
         const float4 h = S.raw.p.h[u], l = S.raw.p.l[u];
-        px = rel(h.x, l.x, oh[0], ol[0]);
-        py = rel(h.y, l.y, oh[1], ol[1]);
-        pz = rel(h.z, l.z, oh[2], ol[2]);
+        rel2(h.x, l.x, oh[0], ol[0], ph[0], pl[0]);
+        rel2(h.y, l.y, oh[1], ol[1], ph[1], pl[1]);
+        rel2(h.z, l.z, oh[2], ol[2], ph[2], pl[2]);
         pm = h.w;
     } else {  // padding entry: far away, massless
-        px = py = pz = 1e15f;
+        ph[0] = ph[1] = ph[2] = 1e15f;
+        pl[0] = pl[1] = pl[2] = 0.f;
         pm = 0.f;
     }
     float* base = reinterpret_cast<float*>(&S.t.p.jp[u >> 1]);
     const int hh = u & 1;
-    base[0 + hh] = px;
-    base[2 + hh] = py;
-    base[4 + hh] = pz;
+    base[0 + hh] = ph[0];
+    base[2 + hh] = ph[1];
+    base[4 + hh] = ph[2];
     base[6 + hh] = pm;
+    base[8 + hh] = pl[0];
+    base[10 + hh] = pl[1];
+    base[12 + hh] = pl[2];
     S.t.p.jid[u] = real ? S.raw_id[u] : kNone;
 }
 
@@ -407,12 +399,11 @@ __device__ __forceinline__ void put_cell(Smem32& S, int u, bool real, const floa
 }
 
 // ---- tile loops --------------------------------------------------------------
-template <int R, bool TAIL, bool SELF>
+// The hot loops note (warp-uniformly) which list pairs had a contact
+// candidate; the candidates are queued after the loop.
+template <int MODE, int R, bool TAIL, bool SELF>
 __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj,
-                                        float rnear2, int& ncount, int lane) {
-    // The hot loops only mask near pairs and note (warp-uniformly) which list
-    // pairs had one; the near pairs are queued after the loop.
-    const float2 eps2 = f2(A.fp.eps2f);
+                                        int& qn, int lane) {
     if constexpr (R > 0) {
         int ntrig = 0;
 #pragma unroll 1
@@ -421,20 +412,20 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             const uint32_t* jid = &S.t.p.jid[2 * q];
             bool any = false;
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                any |= pp_body<SELF>(P, jid, K.iv[r], K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2,
-                                     rnear2);
-            if (__any_sync(0xffffffffu, any)) {
+            for (int r = 0; r < R; ++r) any |= pp_body<MODE, SELF>(A, P, jid, K.iv[r], K.nh[r], K.nl[r], K.g[r]);
+            if (MODE == kContact && __any_sync(0xffffffffu, any)) {
                 if (lane == 0) S.trig[ntrig] = (uint8_t)q;
                 ++ntrig;
             }
         }
-        __syncwarp();
+        if (MODE == kContact) {
+            __syncwarp();
 #pragma unroll 1
-        for (int t = 0; t < ntrig; ++t) {
-            const int q = S.trig[t];
-            queue_pair<SELF, R, TAIL>(S, ncount, S.t.p.jp[q], &S.t.p.jid[2 * q], K, 0, R, false, eps2, rnear2, lane);
-            if (ncount >= 32) flush_near(A, S, ncount, lane);
+            for (int t = 0; t < ntrig; ++t) {
+                const int q = S.trig[t];
+                queue_pair<SELF, R, TAIL>(A, S, qn, S.t.p.jp[q], &S.t.p.jid[2 * q], K, 0, R, false, lane);
+                if (qn >= 32) flush_queue(A, S, qn, lane);
+            }
         }
     }
     if constexpr (TAIL) {
@@ -445,21 +436,22 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             const int q = u * J + tj;
             bool any = false;
             if (q < npair)
-                any = pp_body<SELF>(S.t.p.jp[q], &S.t.p.jid[2 * q], K.iv[R], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R],
-                                    K.gz[R], eps2, rnear2);
-            if (__any_sync(0xffffffffu, any)) {
+                any = pp_body<MODE, SELF>(A, S.t.p.jp[q], &S.t.p.jid[2 * q], K.iv[R], K.nh[R], K.nl[R], K.g[R]);
+            if (MODE == kContact && __any_sync(0xffffffffu, any)) {
                 if (lane == 0) S.trig[ntrig] = (uint8_t)u;
                 ++ntrig;
             }
         }
-        __syncwarp();
+        if (MODE == kContact) {
+            __syncwarp();
 #pragma unroll 1
-        for (int t = 0; t < ntrig; ++t) {
-            const int q = S.trig[t] * J + tj;
-            const bool ok = q < npair;
-            queue_pair<SELF, R, TAIL>(S, ncount, S.t.p.jp[ok ? q : 0], &S.t.p.jid[ok ? 2 * q : 0], K, R, R + 1, ok,
-                                      eps2, rnear2, lane);
-            if (ncount >= 32) flush_near(A, S, ncount, lane);
+            for (int t = 0; t < ntrig; ++t) {
+                const int q = S.trig[t] * J + tj;
+                const bool ok = q < npair;
+                queue_pair<SELF, R, TAIL>(A, S, qn, S.t.p.jp[ok ? q : 0], &S.t.p.jid[ok ? 2 * q : 0], K, R, R + 1, ok,
+                                          lane);
+                if (qn >= 32) flush_queue(A, S, qn, lane);
+            }
         }
     }
 }
@@ -472,17 +464,17 @@ __device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
         for (int q = 0; q < npair; ++q) {
             const CPair& Cp = S.t.cp[q];
 #pragma unroll
-            for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nx[r], K.ny[r], K.nz[r], K.gx[r], K.gy[r], K.gz[r], eps2);
+            for (int r = 0; r < R; ++r) pc_body<ORDER>(Cp, K.nh[r], K.g[r], eps2);
         }
     if constexpr (TAIL)
 #pragma unroll 1
-        for (int q = tj; q < npair; q += J)
-            pc_body<ORDER>(S.t.cp[q], K.nx[R], K.ny[R], K.nz[R], K.gx[R], K.gy[R], K.gz[R], eps2);
+        for (int q = tj; q < npair; q += J) pc_body<ORDER>(S.t.cp[q], K.nh[R], K.g[R], eps2);
 }
 
-template <int R, bool TAIL, int ORDER>
-__device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e, uint32_t i0, int T,
-                            const float (&oh)[3], const float (&ol)[3], float rnear2, int lane) {
+template <int MODE, int R, bool TAIL, int ORDER>
+__device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e,
+                                            uint32_t i0, int T, const float (&oh)[3], const float (&ol)[3],
+                                            int lane) {
     constexpr int NS = Chunk<R, TAIL>::NS;
     Chunk<R, TAIL> K;
     const int J = TAIL ? 32 / T : 1;
@@ -494,17 +486,20 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
         K.vl[r] = i < e;
         K.iv[r] = K.vl[r] ? i : b;
         const float4 h = A.phi[K.iv[r]], l = A.plo[K.iv[r]];
-        K.nx[r] = f2(-rel(h.x, l.x, oh[0], ol[0]));
-        K.ny[r] = f2(-rel(h.y, l.y, oh[1], ol[1]));
-        K.nz[r] = f2(-rel(h.z, l.z, oh[2], ol[2]));
-        K.gx[r] = K.gy[r] = K.gz[r] = make_float2(0.f, 0.f);
+        const float hv[3] = {h.x, h.y, h.z}, lv[3] = {l.x, l.y, l.z};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            float rh, rl;
+            rel2(hv[c], lv[c], oh[c], ol[c], rh, rl);
+            K.nh[r][c] = f2(-rh);
+            K.nl[r][c] = f2(-rl);
+            K.g[r][c] = make_float2(0.f, 0.f);
+            S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
+        }
     }
-    int ncount = 0;
+    int qn = 0;
     __syncwarp();
 
-    // (1) the group's own particles (contiguous), i = j excluded
     constexpr int PJ = kTileJ / 32, PC = kTileC / 32;  // staged entries per lane
     // (1) the group's own particles (contiguous), i = j excluded
     {
@@ -531,7 +526,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
                 gather_particle(A, S, lane + 32 * s, jj < e ? jj : kNone);
             }
             cp_async_commit();
-            pp_tile<R, TAIL, true>(A, S, K, npair, J, tj, rnear2, ncount, lane);
+            pp_tile<MODE, R, TAIL, true>(A, S, K, npair, J, tj, qn, lane);
             fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
@@ -565,14 +560,14 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
                 ib[s] = list_index(A, t0 + 2 * kTileJ + lane + 32 * s, j1, b);
             }
             cp_async_commit();
-            pp_tile<R, TAIL, false>(A, S, K, npair, J, tj, rnear2, ncount, lane);
+            pp_tile<MODE, R, TAIL, false>(A, S, K, npair, J, tj, qn, lane);
             fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
         cp_async_wait_all();
         __syncwarp();
     }
-    if (ncount > 0) flush_near(A, S, ncount, lane);
+    if (MODE == kContact && qn > 0) flush_queue(A, S, qn, lane);
     // (3) list cells: data gathered one tile ahead, indices two
     {
         const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
@@ -631,7 +626,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     __syncwarp();
 }
 
-template <int ORDER>
+template <int ORDER, int MODE>
 __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem32* sm = reinterpret_cast<Smem32*>(smem_raw);
@@ -645,11 +640,6 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     // origin: the group node's centre of mass as an FP32 hi/lo pair
     const float4 o0 = A.cell32[3 * (int64_t)g], o1 = A.cell32[3 * (int64_t)g + 1];
     const float oh[3] = {o0.x, o0.y, o0.z}, ol[3] = {o1.x, o1.y, o1.z};
-    // group extent from its integer box -> near-pair radius
-    const WalkNode G = A.wnode[g];
-    const uint32_t ext = max(G.b.x - G.a.x, max(G.b.y - G.a.y, G.b.z - G.a.z)) + 1u;
-    const float rn = A.fp.near_frac * (float)ext * A.fp.h;
-    const float rnear2 = fmaxf(A.fp.rnear_min2, rn * rn) + A.fp.eps2f;
     // chunks of at most 96 particles: R full slots plus a tail of at most 16
     for (uint32_t i0 = b; i0 < e;) {
         const uint32_t rem = e - i0, cnt = min(rem, 96u);
@@ -663,15 +653,15 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
         const uint32_t ce = i0 + cnt;
         if (T > 0) {
             switch (R) {
-                case 0: group_chunk<0, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
-                case 1: group_chunk<1, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
-                default: group_chunk<2, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, rnear2, lane); break;
+                case 0: group_chunk<MODE, 0, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
+                case 1: group_chunk<MODE, 1, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
+                default: group_chunk<MODE, 2, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
             }
         } else {
             switch (R) {
-                case 1: group_chunk<1, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
-                case 2: group_chunk<2, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
-                default: group_chunk<3, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, rnear2, lane); break;
+                case 1: group_chunk<MODE, 1, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
+                case 2: group_chunk<MODE, 2, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
+                default: group_chunk<MODE, 3, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
             }
         }
         i0 += cnt;
@@ -714,8 +704,8 @@ __global__ void k_order_scatter(int64_t ng, const int32_t* __restrict__ groups, 
 }
 
 // FP64 pass over the contact candidates: Eq. (1) in the oracle's operation
-// order (gravity at r_coll + spring + dashpot, or plain gravity if the FP64
-// decision says r > r_coll), added to the acceleration of i.
+// order less the gravity the FP32 kernel already added for the pair (r_coll
+// or r clamp), i.e. the spring and dashpot term when r <= r_coll.
 __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
                              int64_t cap, ForceParams fp, const double* __restrict__ x,
                              const double* __restrict__ y, const double* __restrict__ z,
@@ -728,11 +718,16 @@ __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned lon
         const uint2 pr = pairs[u];
         const uint32_t i = pr.x, j = pr.y;
         double a[3] = {0.0, 0.0, 0.0};
-        exact_pair64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j], vz[j], m[j], a);
+        contact_term64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j], vz[j], m[j], a);
         atomicAdd(&ax[i], a[0]);
         atomicAdd(&ay[i], a[1]);
         atomicAdd(&az[i], a[2]);
     }
+}
+
+template <int ORDER, int MODE>
+void set_smem_attr(int smem) {
+    cudaFuncSetAttribute(k_force32<ORDER, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 }  // namespace
@@ -766,15 +761,15 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.phi = c->phi.p;
     A.plo = c->plo.p;
     A.cell32 = c->cell32.p;
-    A.wnode = c->wnode.p;
     A.x = p->x;
     A.y = p->y;
     A.z = p->z;
     A.ax = p->ax;
     A.ay = p->ay;
     A.az = p->az;
+    const bool contact = c->prm.r_coll > 0.0;
     const int64_t cap = c->n > 65536 ? c->n : 65536;
-    if (c->contacts.cap < (size_t)cap) BH_TRY(grow(c, c->contacts, (size_t)cap, "contact pairs"));
+    if (contact && c->contacts.cap < (size_t)cap) BH_TRY(grow(c, c->contacts, (size_t)cap, "contact pairs"));
     A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
     A.contact_cap = (int64_t)c->contacts.cap;
     A.ncontact = c->d_small + 16;
@@ -783,22 +778,32 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.nn = c->n_nodes;
     A.status = c->d_status;
     A.fp = fp;
+    A.floor2 = (float)(fp.rc2 + fp.eps2);
+    A.rc2chk = (float)(fp.rc2 * (1.0 + 1e-5));
     A.add_central = add_central;
+    const int mode = contact ? kContact : (A.floor2 > 0.f ? kPlain : kMask);
     const unsigned nb = blocks_for(A.ng, kW32);
     const int smem = (int)(kW32 * sizeof(Smem32));
     static bool attr = false;
     if (!attr) {
-        BH_CUDA(c, cudaFuncSetAttribute(k_force32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        BH_CUDA(c, cudaFuncSetAttribute(k_force32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        set_smem_attr<1, kContact>(smem);
+        set_smem_attr<1, kPlain>(smem);
+        set_smem_attr<1, kMask>(smem);
+        set_smem_attr<2, kContact>(smem);
+        set_smem_attr<2, kPlain>(smem);
+        set_smem_attr<2, kMask>(smem);
         attr = true;
     }
     for (int attempt = 0; attempt < 2; ++attempt) {
-        if (c->prm.order >= 2)
-            k_force32<2><<<nb, 32 * kW32, smem, c->stream>>>(A);
-        else
-            k_force32<1><<<nb, 32 * kW32, smem, c->stream>>>(A);
+#define BH_K32(O, M) k_force32<O, M><<<nb, 32 * kW32, smem, c->stream>>>(A)
+        if (c->prm.order >= 2) {
+            if (mode == kContact) BH_K32(2, kContact); else if (mode == kPlain) BH_K32(2, kPlain); else BH_K32(2, kMask);
+        } else {
+            if (mode == kContact) BH_K32(1, kContact); else if (mode == kPlain) BH_K32(1, kPlain); else BH_K32(1, kMask);
+        }
+#undef BH_K32
         BH_LAUNCH(c);
-        if (!(c->prm.r_coll > 0.0)) break;
+        if (!contact) break;
         // size the FP64 contact pass (one read-back per evaluation); on overflow
         // grow the list and evaluate again
         unsigned long long np = 0;

@@ -8,9 +8,6 @@ namespace bh {
 struct ForceParams {
     double G, eps2, rc2, rc2_hi, kappa, eta, r_coll, GMc;
     float eps2f, rc2f, kappaf, etaf, rcollf, Gf;
-    float rnear_min2;  // (2 r_coll)^2: pairs closer than this take the near-pair path
-    float near_frac;   // ... and pairs closer than near_frac x the group extent
-    float h;           // key-grid cell side (group extents from integer boxes)
     int order;
 };
 
@@ -41,6 +38,26 @@ __device__ __forceinline__ void exact_pair64(const ForceParams& fp, double xi, d
                                 __dadd_rn(__ddiv_rn(__dmul_rn(fp.kappa, __dsub_rn(r, fp.r_coll)), r),
                                           __ddiv_rn(__dmul_rn(fp.eta, rv), r2))));
     }
+    a[0] += f * dx;
+    a[1] += f * dy;
+    a[2] += f * dz;
+}
+
+// The spring and dashpot part of Eq. (1) alone (the gravity at r_coll is
+// added elsewhere): nonzero iff 0 < r <= r_coll, decided in FP64 in the
+// oracle's operation order.
+__device__ __forceinline__ void contact_term64(const ForceParams& fp, double xi, double yi, double zi, double vxi,
+                                               double vyi, double vzi, double mi, double xj, double yj, double zj,
+                                               double vxj, double vyj, double vzj, double mj, double* a) {
+    const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (r2 == 0.0 || r2 > fp.rc2) return;
+    const double r = __dsqrt_rn(r2);
+    const double dvx = __dsub_rn(vxj, vxi), dvy = __dsub_rn(vyj, vyi), dvz = __dsub_rn(vzj, vzi);
+    const double rv = __dadd_rn(__dadd_rn(__dmul_rn(dx, dvx), __dmul_rn(dy, dvy)), __dmul_rn(dz, dvz));
+    const double f = __dmul_rn(__ddiv_rn(mj, __dadd_rn(mi, mj)),
+                               __dadd_rn(__ddiv_rn(__dmul_rn(fp.kappa, __dsub_rn(r, fp.r_coll)), r),
+                                         __ddiv_rn(__dmul_rn(fp.eta, rv), r2)));
     a[0] += f * dx;
     a[1] += f * dy;
     a[2] += f * dz;
