@@ -473,8 +473,9 @@ __device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
 
 template <int MODE, int R, bool TAIL, int ORDER>
 __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k, uint32_t b, uint32_t e,
-                                            uint32_t i0, int T, const float (&oh)[3], const float (&ol)[3],
-                                            int lane) {
+                                            uint32_t i0, uint32_t ce, int T, const float (&oh)[3],
+                                            const float (&ol)[3], int lane) {
+    // group particles [b, e); this chunk's i-particles [i0, ce)
     constexpr int NS = Chunk<R, TAIL>::NS;
     Chunk<R, TAIL> K;
     const int J = TAIL ? 32 / T : 1;
@@ -483,7 +484,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     for (int r = 0; r < NS; ++r) {
         const bool tail = (r == R);
         const uint32_t i = tail ? i0 + 32 * R + ti : i0 + 32 * r + lane;
-        K.vl[r] = i < e;
+        K.vl[r] = i < ce;
         K.iv[r] = K.vl[r] ? i : b;
         const float4 h = A.phi[K.iv[r]], l = A.plo[K.iv[r]];
         const float hv[3] = {h.x, h.y, h.z}, lv[3] = {l.x, l.y, l.z};
@@ -653,15 +654,15 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
         const uint32_t ce = i0 + cnt;
         if (T > 0) {
             switch (R) {
-                case 0: group_chunk<MODE, 0, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
-                case 1: group_chunk<MODE, 1, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
-                default: group_chunk<MODE, 2, true, ORDER>(A, S, k, b, ce, i0, T, oh, ol, lane); break;
+                case 0: group_chunk<MODE, 0, true, ORDER>(A, S, k, b, e, i0, ce, T, oh, ol, lane); break;
+                case 1: group_chunk<MODE, 1, true, ORDER>(A, S, k, b, e, i0, ce, T, oh, ol, lane); break;
+                default: group_chunk<MODE, 2, true, ORDER>(A, S, k, b, e, i0, ce, T, oh, ol, lane); break;
             }
         } else {
             switch (R) {
-                case 1: group_chunk<MODE, 1, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
-                case 2: group_chunk<MODE, 2, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
-                default: group_chunk<MODE, 3, false, ORDER>(A, S, k, b, ce, i0, 0, oh, ol, lane); break;
+                case 1: group_chunk<MODE, 1, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
+                case 2: group_chunk<MODE, 2, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
+                default: group_chunk<MODE, 3, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
             }
         }
         i0 += cnt;

@@ -279,3 +279,17 @@ def test_fp32_moments_close(built, name):
         assert np.all(np.abs(mo[f] - ref.mom[f]) <= 2e-6 * s + 1e-15)
     scale = (M * s * s)[:, None]
     assert np.all(np.abs(mo["Q"] - ref.mom["Q"]) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("n_g", [16, 40, 100, 200, 300])
+def test_fp32_every_group_size_class(n_g):
+    """Groups from a few particles to several i-chunks (every slot/tail
+    variant of the FP32 kernel and multi-chunk groups)."""
+    P = synth.ring(30000, 21, r_in=0.999, r_out=1.001, phi_max=0.05)
+    prm = ring_prm(n_g=n_g, n_leaf=min(8, n_g))
+    ref = orc.rebuild(P, orc_params(prm))
+    sizes = ref.tree["end"][ref.groups].astype(int) - ref.tree["begin"][ref.groups]
+    assert sizes.max() > min(n_g, 96) // 2
+    aref = orc.tree_forces(ref, orc_params(prm))
+    ctx, D = gpu_build(P, prm, precision=1)
+    assert_force_close(accel_of(D), aref, TOL32, f"n_g={n_g}")
