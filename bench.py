@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: group-shared Barnes-Hut force evaluation with persistent lists
+(Sec. 4.2) on a synthetic planetary ring, one JSON line on stdout.
+
+A step is one kick-drift-kick leapfrog step of the whole path: keys, sort,
+octree, moments, groups and the tree walk on list-constructing steps (every
+4th force evaluation), the moment refresh otherwise, the force kernel, the
+FP64 contact pass and the update.  Default workload: the large ring, 2^26
+particles, theta 0.4, quadrupole, FP32 group-relative forces, FP64 positions
+and updates.
+
+  value    interactions/s over the timed steps (all ranks), device-timed with
+           CUDA events; particle-steps/s beside it
+  e2e      the same through bh_step_host with pinned host buffers, the
+           host<->device copies of every step inside the timed region
+  roofline the force kernel against the FP32 peak (152 SMs x 128 lanes x 2
+           flops x 2070 MHz), achieved = counted interactions x FP32 flops
+           per interaction of the kernel source / event-timed kernel time
+  cpu_baseline  the CPU FP64 oracle (host cores) on a ring sector of the same
+           surface density
+
+--impl reference runs the oracle as the reference arm.  Under torchrun each
+rank runs an independent replica (weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 flops per interaction of the force kernel (FFMA/FFMA2 lane = 2,
+# FADD/FMUL = 1; rsqrt not counted): particle-particle with the two-float
+# separation 24, particle-cell with quadrupole 49, monopole only 18.
+FLOPS_PP, FLOPS_PC2, FLOPS_PC1 = 24, 49, 18
+# The paper's convention (Sec. 5.1): 49 per particle-particle, 31 per particle-cell.
+PAPER_PP, PAPER_PC = 49, 31
+NUM_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return NUM_SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ring64m_fp32")
+    ap.add_argument("--n", type=int, default=None, help="override the particle count")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true")
+    return ap.parse_args()
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sector(n_sector: int, full_n: int, prm: dict, seed: int = 77):
+    """A ring sector with the surface density of the full ring (same
+    workload, bounded sample) for the CPU oracle."""
+    from paper_1907_02289_gb300 import synth
+    return synth.ring(n_sector, seed, phi_max=2 * math.pi * n_sector / full_n)
+
+
+def cpu_oracle_rate(P: dict, prm: dict):
+    """One oracle force evaluation with list construction; interactions/s."""
+    import numpy as np
+
+    import oracle as orc
+    op = orc.Params(**{k: v for k, v in prm.items() if k in orc.Params.__dataclass_fields__})
+    t0 = time.perf_counter()
+    S = orc.rebuild(P, op)
+    orc.accel(S, op)
+    dt = time.perf_counter() - t0
+    t = S.tree
+    ni = t["end"][S.groups].astype(np.int64) - t["begin"][S.groups]
+    leafn = t["end"].astype(np.int64) - t["begin"]
+    nj = np.add.reduceat(leafn[S.lists["P"]], S.lists["pp_off"][:-1]) if len(S.lists["P"]) else np.zeros(len(ni))
+    inter = int((ni * nj).sum() + (ni * np.diff(S.lists["pc_off"])).sum())
+    return inter / dt, inter, dt, orc.num_threads()
+
+
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    from paper_1907_02289_gb300 import synth
+
+    import numpy as np
+
+    import oracle as orc
+    pr = synth.PRESETS[args.workload]
+    full_n = args.n or pr["n"]
+    prm = dict(pr["params"])
+    n_s = min(full_n, 1 << 18)
+    P = oracle_sector(n_s, full_n, prm)
+    op = orc.Params(**{k: v for k, v in prm.items() if k in orc.Params.__dataclass_fields__})
+    # KDK steps of the oracle on the sector, lists rebuilt every rebuild_every
+    S = orc.rebuild(P, op)
+    a = orc.accel(S, op)
+    k = 1
+    inter_tot, t_tot = 0, 0.0
+
+    def count(S):
+        t = S.tree
+        ni = t["end"][S.groups].astype(np.int64) - t["begin"][S.groups]
+        leafn = t["end"].astype(np.int64) - t["begin"]
+        nj = np.add.reduceat(leafn[S.lists["P"]], S.lists["pp_off"][:-1])
+        return int((ni * nj).sum() + (ni * np.diff(S.lists["pc_off"])).sum())
+
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        Q = S.P
+        for ci, c in enumerate("xyz"):
+            Q["v" + c] = Q["v" + c] + 0.5 * op.dt * a[:, ci]
+        for c in "xyz":
+            Q[c] = Q[c] + op.dt * Q["v" + c]
+        if k % op.rebuild_every == 0:
+            S = orc.rebuild(Q, op)
+        else:
+            orc.refresh(S, op)
+        a = orc.accel(S, op)
+        for ci, c in enumerate("xyz"):
+            S.P["v" + c] = S.P["v" + c] + 0.5 * op.dt * a[:, ci]
+        k += 1
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            inter_tot += count(S)
+            t_tot += dt
+    value = inter_tot / t_tot
+    sample = f"ring sector of {n_s} particles at the surface density of the {full_n}-particle ring"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "N": n_s, "sample_of_N": full_n},
+            "particle_steps_per_s": n_s * args.steps / t_tot,
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": orc.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "interactions/s and particle-steps/s per GB300 at stated force error; % FP32 peak"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1907_02289_gb300 import _build, bh, synth
+    rank, local, world = rank_info()
+    _build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pr = synth.PRESETS[args.workload]
+    n = args.n or pr["n"]
+    prm = dict(pr["params"])
+    P = synth.ring(n, pr["seed"] + 1000 * rank) if pr["kind"] == "ring" else synth.make(args.workload, n)[0]
+    stream = torch.cuda.current_stream()
+
+    ctx = bh.Context(**prm)
+    D = bh.Particles(P)
+    # initial evaluation + warm-up steps (evaluations 0..W); timed steps then
+    # start on a list-constructing evaluation when W = 3 and rebuild_every = 4
+    ctx.bh_step(D, args.warmup)
+    ctx.bh_sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    ctx.bh_set_timing(True)
+    ctx.bh_get_timing(reset=True)
+    c0 = ctx.bh_get_counters()
+    inter = pp = pc = 0
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.bh_step(D, 1)
+        c = ctx.bh_get_counters()
+        pp += c["n_pp"]
+        pc += c["n_pc"]
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    force_ms, force_launches = ctx.bh_get_timing(reset=True)
+    ctx.bh_set_timing(False)
+    c1 = ctx.bh_get_counters()
+    launches = c1["n_launches"] - c0["n_launches"]
+    inter = pp + pc
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * inter / elapsed
+    flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
+    flops = pp * FLOPS_PP + pc * flops_pc
+    achieved = flops / (force_ms / 1e3) / 1e12 if force_ms > 0 else None
+    peak = fp32_peak_tflops(SM_MAX_MHZ)
+    roofline = {"kernel": "k_force32" if prm["precision"] == 1 else "k_force64", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                "traffic": None, "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
+                "flops_per_interaction": {"pp": FLOPS_PP, "pc": flops_pc},
+                "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}
+    if clk.get("sm_mhz"):
+        roofline["peak_at_median_clock"] = fp32_peak_tflops(clk["sm_mhz"])
+        roofline["frac_at_median_clock"] = achieved / roofline["peak_at_median_clock"] if achieved else None
+
+    # force error of this path against the plain FP64 GPU path on the same lists
+    err = None
+    if not args.no_error and prm["precision"] == 1:
+        Pnow = D.numpy()
+        ctxe = bh.Context(**dict(prm, precision=0))
+        De = bh.Particles(Pnow)
+        ctxe.bh_build_tree(De)
+        ctxe.bh_make_lists()
+        ctxe.bh_compute_forces(De, bh.BH_FORCE_TREE_ONLY)
+        ctx32 = bh.Context(**prm)
+        D32 = bh.Particles(De.numpy())
+        ctx32.bh_build_tree(D32)
+        ctx32.bh_make_lists()
+        ctx32.bh_compute_forces(D32, bh.BH_FORCE_TREE_ONLY)
+        ctxe.bh_sync()
+        ctx32.bh_sync()
+        a64 = torch.stack([De.t["ax"], De.t["ay"], De.t["az"]], 1)
+        a32 = torch.stack([D32.t["ax"], D32.t["ay"], D32.t["az"]], 1)
+        r = torch.linalg.norm(a64, dim=1)
+        rel = (torch.linalg.norm(a32 - a64, dim=1) / r).cpu().numpy()
+        rn = r.cpu().numpy()
+        ok = rn >= 1e-2 * np.median(rn)
+        err = {"reference": "plain FP64 GPU path on the same lists (itself within 1e-12 of the CPU oracle)",
+               "max_rel": float(rel.max()), "max_rel_excl_near_cancelling": float(rel[ok].max()),
+               "p99_9_rel": float(np.percentile(rel, 99.9)), "median_rel": float(np.median(rel)),
+               "gate": 1e-5}
+        for x in (ctxe, ctx32):
+            x.close()
+        del De, D32
+
+    e2e = None
+    if not args.no_e2e:
+        ctxh = bh.Context(**prm)
+        H = bh.HostParticles(P, pinned=True)
+        ctxh.bh_step_host(H, args.warmup)
+        ctxh.bh_set_timing(False)
+        ppe = pce = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctxh.bh_step_host(H, 1)
+            c = ctxh.bh_get_counters()
+            ppe += c["n_pp"]
+            pce += c["n_pc"]
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * (ppe + pce) / te, "unit": "interactions/s",
+               "h2d_bytes_per_step": n * (10 * 8 + 8), "d2h_bytes_per_step": n * (10 * 8 + 8),
+               "particle_steps_per_s": world * n * args.steps / te, "api": "bh_step_host (pinned host buffers)"}
+        ctxh.close()
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        n_s = min(n, 1 << 21)
+        rate, inter_s, dt_s, cores = cpu_oracle_rate(oracle_sector(n_s, n, prm), prm)
+        cpu = {"value": rate, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+               "sample": f"one list-constructing force evaluation of a {n_s}-particle ring sector at the surface "
+                         f"density of the {n}-particle ring ({inter_s} interactions, {dt_s:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prm["precision"] == 1 else "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "N": n, "theta": prm["theta"], "n_g": prm["n_g"],
+                           "order": prm["order"], "rebuild_every": prm["rebuild_every"],
+                           "precision": "FP32 group-relative forces, FP64 positions/velocities/updates"
+                           if prm["precision"] == 1 else "FP64",
+                           "l2": "inputs larger than L2 (particle arrays %.1f GB)" % (n * 88 / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "particle_steps_per_s": world * n * args.steps / elapsed,
+                "interactions_per_step": inter / args.steps,
+                "pct_fp32_peak": 100 * roofline["frac"] if roofline["frac"] else None,
+                "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
+                "force_error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

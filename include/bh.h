@@ -97,6 +97,8 @@ typedef struct {
     int64_t n_pc; /* particle-cell interactions                                   */
     int64_t n_evals;    /* force evaluations since the last list build            */
     int64_t n_rebuilds; /* list-constructing evaluations so far                   */
+    int64_t n_launches; /* CUDA kernels launched by this context                  */
+    int64_t n_contacts; /* contact candidates of the last FP32 force evaluation   */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
@@ -158,6 +160,13 @@ int bh_get_moments(bh_ctx* ctx, double* M, double* c3, double* Q6);
 int bh_get_groups(bh_ctx* ctx, int32_t* group_nodes);
 int bh_get_lists(bh_ctx* ctx, int64_t* pp_off, int32_t* pp_ids, int64_t* pc_off, int32_t* pc_ids);
 int bh_get_counters(bh_ctx* ctx, bh_counters* out);
+
+/* Measurement hooks.  bh_set_timing(ctx, 1) makes every force-kernel launch
+ * record a pair of CUDA events on the context's stream; bh_get_timing
+ * synchronises the stream and returns the summed kernel time (ms) and the
+ * number of timed launches, clearing them when reset != 0. */
+int bh_set_timing(bh_ctx* ctx, int enable);
+int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset);
 
 #ifdef __cplusplus
 }

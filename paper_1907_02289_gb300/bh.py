@@ -21,7 +21,7 @@ BH_FORCE_TREE_ONLY = 1
 SYMBOLS = ("bh_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
-           "bh_get_counters")
+           "bh_get_counters", "bh_set_timing", "bh_get_timing")
 
 
 class bh_params(ctypes.Structure):
@@ -39,7 +39,8 @@ class bh_particles(ctypes.Structure):
 
 
 class bh_counters(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds")]
+    _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
+                                               "n_contacts")]
 
 
 _lib = None
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.bh_get_groups.argtypes = [P, P]
     lib.bh_get_lists.argtypes = [P, P, P, P, P]
     lib.bh_get_counters.argtypes = [P, ctypes.POINTER(bh_counters)]
+    lib.bh_set_timing.argtypes = [P, ctypes.c_int]
+    lib.bh_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     _lib = lib
     return lib
 
@@ -119,15 +122,24 @@ class Particles:
 
 
 class HostParticles:
-    """Caller-owned HOST arrays (numpy, optionally page-locked) for bh_step_host."""
+    """Caller-owned HOST arrays for bh_step_host (page-locked when pinned)."""
 
-    def __init__(self, arrays: dict):
+    def __init__(self, arrays: dict, pinned: bool = False):
         n = len(arrays["x"])
         self.n = n
         self.a = {}
+        self._keep = []
         for f in Particles.FIELDS:
             dt = np.int64 if f == "id" else np.float64
-            self.a[f] = np.ascontiguousarray(arrays[f], dtype=dt).copy() if f in arrays else np.zeros(n, dt)
+            if pinned:
+                import torch
+                t = torch.empty(n, dtype=torch.int64 if f == "id" else torch.float64, pin_memory=True)
+                self._keep.append(t)
+                v = t.numpy()
+                v[:] = arrays[f] if f in arrays else 0
+                self.a[f] = v
+            else:
+                self.a[f] = np.ascontiguousarray(arrays[f], dtype=dt).copy() if f in arrays else np.zeros(n, dt)
         self.struct = bh_particles(*(self.a[f].ctypes.data for f in Particles.FIELDS), n)
 
 
@@ -236,3 +248,12 @@ class Context:
         c = bh_counters()
         self._chk(self.lib.bh_get_counters(self.h, ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in bh_counters._fields_}
+
+    def bh_set_timing(self, enable: bool = True):
+        return self._chk(self.lib.bh_set_timing(self.h, 1 if enable else 0))
+
+    def bh_get_timing(self, reset: bool = True):
+        ms = ctypes.c_double()
+        nl = ctypes.c_int64()
+        self._chk(self.lib.bh_get_timing(self.h, ctypes.byref(ms), ctypes.byref(nl), 1 if reset else 0))
+        return ms.value, nl.value

@@ -44,6 +44,35 @@ int grow_raw(Ctx* c, void** p, size_t* cap, size_t need, const char* what, bool 
     return BH_OK;
 }
 
+static cudaEvent_t take_event(Ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+int timing_begin(Ctx* c) {
+    if (!c->timing) return BH_OK;
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    if (!a || !b) return fail(c, BH_E_CUDA, "cudaEventCreate failed");
+    BH_CUDA(c, cudaEventRecord(a, c->stream));
+    c->ev_force.push_back({a, b});
+    return BH_OK;
+}
+
+int timing_end(Ctx* c) {
+    if (!c->timing || c->ev_force.empty()) return BH_OK;
+    BH_CUDA(c, cudaEventRecord(c->ev_force.back().second, c->stream));
+    return BH_OK;
+}
+
 namespace {
 
 template <typename T>
@@ -193,6 +222,11 @@ int bh_destroy(bh_ctx* ctx) {
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
     release(c->cnt_c); release(c->cnt_j); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
     release(c->hbuf); release(c->hid);
+    for (auto& pr : c->ev_force) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return BH_OK;
 }
@@ -400,6 +434,37 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_pc = c->n_int_pc;
     out->n_evals = c->evals_since_build;
     out->n_rebuilds = c->n_rebuilds;
+    out->n_launches = c->n_launches;
+    out->n_contacts = c->n_contacts;
+    return BH_OK;
+}
+
+int bh_set_timing(bh_ctx* ctx, int enable) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    c->timing = enable != 0;
+    return BH_OK;
+}
+
+int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (auto& pr : c->ev_force) {
+        float ms = 0.f;
+        BH_CUDA(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        total += ms;
+    }
+    if (force_ms) *force_ms = total;
+    if (force_launches) *force_launches = (int64_t)c->ev_force.size();
+    if (reset) {
+        for (auto& pr : c->ev_force) {
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        c->ev_force.clear();
+    }
     return BH_OK;
 }
 

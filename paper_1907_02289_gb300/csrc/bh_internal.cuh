@@ -59,6 +59,12 @@ struct Ctx {
     bool have_tree = false, have_lists = false, have_acc = false;
     int64_t k_eval = 0;        // force evaluations done (drives the rebuild schedule)
     int64_t evals_since_build = 0, n_rebuilds = 0;
+    int64_t n_launches = 0;    // kernels launched by this context
+
+    // optional CUDA-event timing of the force kernel (one event pair per launch)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_force;
 
     // status and small device scalars
     int* d_status = nullptr;
@@ -133,6 +139,7 @@ struct Ctx {
         if (e_ != cudaSuccess)                                                        \
             return ::bh::fail((c), BH_E_CUDA, "kernel launch failed: %s (%s:%d)",      \
                               cudaGetErrorString(e_), __FILE__, __LINE__);            \
+        (c)->n_launches++;                                                            \
     } while (0)
 
 inline unsigned blocks_for(int64_t n, int threads) {
@@ -163,6 +170,10 @@ int stage_lists(Ctx* c);                           // walk (count, fill) + parti
 int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of particles
 int build_order32(Ctx* c);                         // FP32 kernel's group order (per list build)
 int stage_force(Ctx* c, bh_particles* p, bool add_central);
+
+// bh_api.cu: force-kernel timing (no-ops unless enabled)
+int timing_begin(Ctx* c);
+int timing_end(Ctx* c);
 
 // update.cu
 int stage_kick(Ctx* c, bh_particles* p, double h);

@@ -796,6 +796,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         attr = true;
     }
     for (int attempt = 0; attempt < 2; ++attempt) {
+        BH_TRY(timing_begin(c));
 #define BH_K32(O, M) k_force32<O, M><<<nb, 32 * kW32, smem, c->stream>>>(A)
         if (c->prm.order >= 2) {
             if (mode == kContact) BH_K32(2, kContact); else if (mode == kPlain) BH_K32(2, kPlain); else BH_K32(2, kMask);
@@ -804,6 +805,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         }
 #undef BH_K32
         BH_LAUNCH(c);
+        BH_TRY(timing_end(c));
         if (!contact) break;
         // size the FP64 contact pass (one read-back per evaluation); on overflow
         // grow the list and evaluate again
