@@ -168,6 +168,40 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out);
 int bh_set_timing(bh_ctx* ctx, int enable);
 int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset);
 
+/* Stable radix sort that allocates nothing.  The paper has no counterpart:
+ * this is the sort of bh_build_tree (Sec. 4.2 step 3a, same kernels, same
+ * result) offered on its own to callers that must not allocate device
+ * memory here, e.g. code whose device memory is all handed to its own pool
+ * allocator (so a cudaMalloc would fail or fragment that pool), or a
+ * real-time loop that cannot take the device-wide synchronisation cudaFree
+ * implies.  It makes no cudaMalloc/cudaFree call and calls no allocating
+ * library routine; its scratch is one fixed array of
+ * 4 * (256 * BH_SORT_STATIC_MAX_N / 4096 + 128) bytes (about 1 MiB) in the
+ * library's device global memory, one copy per device.
+ *
+ *  keys      [n] uint64 device, in: keys; out: keys in ascending order.
+ *  idx       [n] uint32 device, out: idx[i] = input position of the key now
+ *            at i; equal keys keep their input order (stable).
+ *  keys_tmp, idx_tmp  [n] caller-owned device scratch, contents clobbered;
+ *            must not alias keys or idx.
+ *  n         0 <= n <= BH_SORT_STATIC_MAX_N; larger n is rejected with
+ *            BH_E_INVAL before anything runs.
+ *  stream    cudaStream_t for all work (NULL = legacy default stream).  The
+ *            call only enqueues work and returns; it does not synchronise.
+ *  err, err_len  optional caller buffer for a message on failure (NULL ok).
+ * All eight 8-bit passes run, so all 64 key bits are sorted.
+ * The first call on each device does set-up with that device current: it
+ * looks up the scratch array's address (cudaGetSymbolAddress) and sets the
+ * sort kernel's shared-memory limit; make that first call before capturing
+ * any stream on that device.  Every call on one device uses the same scratch
+ * array, so calls that can overlap in time (different streams or host
+ * threads) race and give wrong results: order them, e.g. on one stream.
+ * Errors: BH_E_INVAL (n out of range, NULL or aliased buffers, device
+ * ordinal >= 64), BH_E_CUDA (set-up or launch failure). */
+#define BH_SORT_STATIC_MAX_N 4194304
+int bh_sort_keys_static(uint64_t* keys, uint32_t* idx, uint64_t* keys_tmp, uint32_t* idx_tmp, int64_t n,
+                        void* stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ BH_FORCE_TREE_ONLY = 1
 SYMBOLS = ("bh_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
-           "bh_get_counters", "bh_set_timing", "bh_get_timing")
+           "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_sort_keys_static")
+BH_SORT_STATIC_MAX_N = 4194304
 
 
 class bh_params(ctypes.Structure):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.bh_get_counters.argtypes = [P, ctypes.POINTER(bh_counters)]
     lib.bh_set_timing.argtypes = [P, ctypes.c_int]
     lib.bh_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.bh_sort_keys_static.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_char_p, ctypes.c_size_t]
     _lib = lib
     return lib
 
@@ -98,6 +100,24 @@ def make_params(**kw) -> bh_params:
     for k, v in {**defaults, **{k: v for k, v in kw.items() if k in defaults}}.items():
         setattr(p, k, v)
     return p
+
+
+def bh_sort_keys_static(keys, idx, keys_tmp, idx_tmp, stream=None):
+    """Stable sort of the uint64 keys (device tensors, int64 dtype holding the
+    bits) with idx (int32 dtype holding uint32) the input position of each
+    sorted key; keys_tmp / idx_tmp are device scratch of the same sizes.
+    Nothing is allocated by the library; see bh.h for the limits."""
+    import torch
+    lib = load()
+    n = keys.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    buf = ctypes.create_string_buffer(256)
+    rc = lib.bh_sort_keys_static(keys.data_ptr(), idx.data_ptr(), keys_tmp.data_ptr(), idx_tmp.data_ptr(), n,
+                                 ctypes.c_void_p(stream), buf, len(buf))
+    if rc != BH_OK:
+        raise BHError(rc, buf.value.decode())
+    return rc
 
 
 class Particles:

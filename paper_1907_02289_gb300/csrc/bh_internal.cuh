@@ -151,11 +151,18 @@ inline unsigned blocks_for(int64_t n, int threads) {
 // scan.cu: exclusive prefix sums; *total written to d_total (device) if given.
 int scan_u32(Ctx* c, const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* d_total);
 int scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, unsigned long long* d_total);
+int64_t scan_sums_count(int64_t n);
+cudaError_t scan_u32_with(cudaStream_t s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums);
 
 // sort.cu
 int stage_keys(Ctx* c, const bh_particles* p);     // root box + keys (+ status on NaN)
 int stage_sort(Ctx* c);                            // stable LSD radix sort of (key, idx)
 int stage_permute(Ctx* c, bh_particles* p);        // gather particle arrays into key order
+// context-free sort over caller buffers (sort.cu); scratch >= sort_scratch_words(n) words
+int64_t sort_scratch_words(int64_t n);
+cudaError_t sort_setup_device();
+cudaError_t sort_pairs_with(cudaStream_t s, uint64_t* keys, uint32_t* idx, uint64_t* ktmp, uint32_t* itmp,
+                            int64_t n, uint32_t* scratch);
 
 // tree.cu
 int stage_octree(Ctx* c);                          // level-by-level split; sets n_nodes

@@ -129,4 +129,17 @@ int scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, unsigned long l
     return scan_impl<int64_t>(c, in, out, n, d_total);
 }
 
+// Context-free form of scan_u32 over caller-provided block sums (at least
+// scan_sums_count(n) words); launches only, errors from cudaGetLastError.
+int64_t scan_sums_count(int64_t n) { return n <= 0 ? 0 : (n + kTile - 1) / kTile; }
+
+cudaError_t scan_u32_with(cudaStream_t s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = scan_sums_count(n);
+    k_reduce<uint32_t><<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums);
+    k_scan_sums<uint32_t><<<1, kThreads, 0, s>>>(sums, nb, nullptr);
+    k_scan_apply<uint32_t><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, sums);
+    return cudaGetLastError();
+}
+
 }  // namespace bh

@@ -329,4 +329,43 @@ int stage_permute(Ctx* c, bh_particles* p) {
     return BH_OK;
 }
 
+// Context-free form of stage_sort for callers that supply every buffer: all
+// eight passes run (no host read-back of the digit histogram, so nothing here
+// synchronises), ending in (keys, idx) again.  idx is set to 0..n-1 first.
+int64_t sort_scratch_words(int64_t n) {
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    return kRadix * ntiles + scan_sums_count(kRadix * ntiles);
+}
+
+cudaError_t sort_setup_device() {
+    return cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
+}
+
+namespace {
+__global__ void k_iota(uint32_t* __restrict__ idx, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) idx[i] = (uint32_t)i;
+}
+}  // namespace
+
+cudaError_t sort_pairs_with(cudaStream_t s, uint64_t* keys, uint32_t* idx, uint64_t* ktmp, uint32_t* itmp,
+                            int64_t n, uint32_t* scratch) {
+    if (n <= 0) return cudaSuccess;
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t* hist = scratch;
+    uint32_t* sums = scratch + (int64_t)kRadix * ntiles;
+    k_iota<<<blocks_for(n, 256), 256, 0, s>>>(idx, n);
+    uint64_t* kb[2] = {keys, ktmp};
+    uint32_t* ib[2] = {idx, itmp};
+    for (int pass = 0; pass < 8; ++pass) {
+        const int a = pass & 1, b = 1 - a;
+        k_upsweep<<<ntiles, kSortThreads, 0, s>>>(kb[a], n, 8 * pass, hist, ntiles);
+        cudaError_t e = scan_u32_with(s, hist, hist, (int64_t)kRadix * ntiles, sums);
+        if (e != cudaSuccess) return e;
+        k_downsweep<<<ntiles, kSortThreads, sizeof(DownSmem), s>>>(kb[a], ib[a], n, 8 * pass, hist, ntiles,
+                                                                   kb[b], ib[b]);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace bh
