@@ -106,6 +106,20 @@ typedef struct {
  * order not 1/2, precision not 0/1, rebuild_every < 1, key_frame != 0,
  * dt < 0. */
 int bh_create(const bh_params* p, void* stream, bh_ctx** out);
+
+/* Create a context for n_patches INDEPENDENT particle sets ("patches", e.g.
+ * separate ring sectors) that are stepped together: the particle arrays hold
+ * the patches one after another, patch q being [offsets[q], offsets[q+1]).
+ * Each patch gets its own root box, keys, sort, tree, groups and lists
+ * exactly as if it were alone (a patch never interacts with another), but
+ * every stage runs once over all patches: one sort, one tree pass per level,
+ * one walk, one force launch.  Trees form a forest whose roots are nodes
+ * 0..n_patches-1; node, group and list ids are global.  offsets is a host
+ * array of n_patches + 1 entries (copied): offsets[0] = 0, strictly
+ * increasing, offsets[n_patches] = the n passed later (< 2^31).
+ * Errors: as bh_create, plus BH_E_INVAL for n_patches < 1 or bad offsets.
+ * n_patches = 1 is bh_create. */
+int bh_batch_create(const bh_params* p, int n_patches, const int64_t* offsets, void* stream, bh_ctx** out);
 int bh_destroy(bh_ctx* ctx);
 const char* bh_last_error(const bh_ctx* ctx);
 int bh_set_stream(bh_ctx* ctx, void* stream);
@@ -151,7 +165,8 @@ int bh_sync(bh_ctx* ctx);
 int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp_entries,
                  int64_t* n_pc_entries, int64_t* n_list_particles);
 
-/* Read-backs into host buffers (n, n_nodes, n_groups, ... entries). */
+/* Read-backs into host buffers (n, n_nodes, n_groups, ... entries).
+ * bh_get_root writes one box per patch: lo3[3 q + a], L[q]. */
 int bh_get_keys(bh_ctx* ctx, uint64_t* keys, uint32_t* perm);
 int bh_get_root(bh_ctx* ctx, double* lo3, double* L);
 int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,

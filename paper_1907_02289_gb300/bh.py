@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbh.so")
 BH_OK, BH_E_INVAL, BH_E_NOMEM, BH_E_CUDA, BH_E_LIST_OVERFLOW, BH_E_TIMEOUT, BH_E_STATE = range(7)
 BH_PREC_FP64, BH_PREC_FP32 = 0, 1
 BH_FORCE_TREE_ONLY = 1
-SYMBOLS = ("bh_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
+SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
            "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_sort_keys_static")
@@ -64,6 +64,7 @@ def load(path: str = LIB_PATH):
     P = ctypes.c_void_p
     vp = ctypes.POINTER(ctypes.c_void_p)
     lib.bh_create.argtypes = [ctypes.POINTER(bh_params), P, vp]
+    lib.bh_batch_create.argtypes = [ctypes.POINTER(bh_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int64), P, vp]
     lib.bh_destroy.argtypes = [P]
     lib.bh_last_error.argtypes = [P]
     lib.bh_last_error.restype = ctypes.c_char_p
@@ -164,16 +165,26 @@ class HostParticles:
 
 
 class Context:
-    """Owns one bh_ctx; methods mirror the C entry points of the same names."""
+    """Owns one bh_ctx; methods mirror the C entry points of the same names.
+    offsets (patch particle offsets, n_patches + 1 entries) selects
+    bh_batch_create."""
 
-    def __init__(self, stream=None, **params):
+    def __init__(self, stream=None, offsets=None, **params):
         import torch
         self.lib = load()
         self.params = make_params(**params)
         h = ctypes.c_void_p()
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
-        rc = self.lib.bh_create(ctypes.byref(self.params), ctypes.c_void_p(stream), ctypes.byref(h))
+        self.n_patches = 1
+        if offsets is None:
+            rc = self.lib.bh_create(ctypes.byref(self.params), ctypes.c_void_p(stream), ctypes.byref(h))
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            self.n_patches = len(off) - 1
+            rc = self.lib.bh_batch_create(ctypes.byref(self.params), self.n_patches,
+                                          off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          ctypes.c_void_p(stream), ctypes.byref(h))
         if rc != BH_OK:
             raise BHError(rc, "bh_create failed (see stderr)")
         self.h = h
@@ -225,10 +236,13 @@ class Context:
         return k, p
 
     def bh_get_root(self):
-        lo = np.empty(3)
-        L = np.empty(1)
+        """(lo[3], L) for one patch; (lo[P, 3], L[P]) for a batch."""
+        lo = np.empty((self.n_patches, 3))
+        L = np.empty(self.n_patches)
         self._chk(self.lib.bh_get_root(self.h, _np(lo), _np(L)))
-        return lo, float(L[0])
+        if self.n_patches == 1:
+            return lo[0], float(L[0])
+        return lo, L
 
     def bh_get_tree(self):
         nn = self.bh_get_sizes()["n_nodes"]

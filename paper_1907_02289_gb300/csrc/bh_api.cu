@@ -73,6 +73,24 @@ int timing_end(Ctx* c) {
     return BH_OK;
 }
 
+// Patch layout: offsets on host and device, per-patch root boxes, sort tiles.
+int setup_patches(Ctx* c, int n_patches, const int64_t* off) {
+    c->n_patches = n_patches;
+    c->h_off.assign(off, off + n_patches + 1);
+    BH_TRY(grow(c, c->d_off, (size_t)n_patches + 1, "patch offsets"));
+    BH_CUDA(c, cudaMemcpyAsync(c->d_off.p, c->h_off.data(), c->h_off.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, c->stream));
+    if (n_patches > 1) {
+        std::vector<uint32_t> meta;
+        c->n_tiles = sort_tiles_for(c->h_off, &meta);
+        BH_TRY(grow(c, c->tile_meta, meta.size(), "sort tile table"));
+        BH_CUDA(c, cudaMemcpyAsync(c->tile_meta.p, meta.data(), meta.size() * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice, c->stream));
+    }
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BH_OK;
+}
+
 namespace {
 
 template <typename T>
@@ -120,18 +138,21 @@ int read_status(Ctx* c) {
 
 int build_tree(Ctx* c, bh_particles* p) {
     BH_TRY(check_particles(c, p, true));
+    if (c->n_patches > 1 && p->n != c->h_off.back())
+        return fail(c, BH_E_INVAL, "n = %lld but the patches hold %lld particles", (long long)p->n,
+                    (long long)c->h_off.back());
     c->n = p->n;
     c->have_tree = c->have_lists = false;
+    if (c->n_patches == 1 && (c->h_off.size() != 2 || c->h_off[1] != p->n)) {
+        const int64_t off[2] = {0, p->n};
+        BH_TRY(setup_patches(c, 1, off));
+    }
     BH_TRY(stage_keys(c, p));
     BH_TRY(read_status(c));
-    double box[5];
-    BH_CUDA(c, cudaMemcpyAsync(box, c->d_box, sizeof(box), cudaMemcpyDeviceToHost, c->stream));
+    c->h_box.resize(8 * (size_t)c->n_patches);
+    BH_CUDA(c, cudaMemcpyAsync(c->h_box.data(), c->d_box, c->h_box.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
     BH_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->h_lo[0] = box[0];
-    c->h_lo[1] = box[1];
-    c->h_lo[2] = box[2];
-    c->h_L = box[3];
-    c->h_S = box[4];
     BH_TRY(stage_sort(c));
     BH_TRY(stage_permute(c, p));
     BH_TRY(stage_octree(c));
@@ -173,13 +194,27 @@ using bh::Ctx;
 
 extern "C" {
 
-int bh_create(const bh_params* p, void* stream, bh_ctx** out) {
+static int create_ctx(const char* who, const bh_params* p, int n_patches, const int64_t* offsets, void* stream,
+                      bh_ctx** out) {
     if (!out) return BH_E_INVAL;
     *out = nullptr;
     Ctx tmp;
     int rc = bh::check_params(&tmp, p);
+    if (rc == BH_OK && n_patches > 1) {
+        if (!offsets) {
+            rc = bh::fail(&tmp, BH_E_INVAL, "offsets is NULL");
+        } else if (offsets[0] != 0) {
+            rc = bh::fail(&tmp, BH_E_INVAL, "offsets[0] must be 0");
+        } else {
+            for (int q = 0; q < n_patches && rc == BH_OK; ++q)
+                if (offsets[q + 1] <= offsets[q])
+                    rc = bh::fail(&tmp, BH_E_INVAL, "patch %d is empty or offsets decrease", q);
+            if (rc == BH_OK && offsets[n_patches] >= ((int64_t)1 << 31))
+                rc = bh::fail(&tmp, BH_E_INVAL, "total particle count must be < 2^31");
+        }
+    }
     if (rc != BH_OK) {
-        fprintf(stderr, "bh_create: %s\n", tmp.err.c_str());
+        fprintf(stderr, "%s: %s\n", who, tmp.err.c_str());
         return rc;
     }
     Ctx* c = new Ctx();
@@ -188,18 +223,37 @@ int bh_create(const bh_params* p, void* stream, bh_ctx** out) {
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_box, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_box, 8 * sizeof(double) * (size_t)n_patches);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_small, 64 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        fprintf(stderr, "bh_create: CUDA error: %s\n", cudaGetErrorString(e));
+        fprintf(stderr, "%s: CUDA error: %s\n", who, cudaGetErrorString(e));
         cudaGetLastError();
         bh_destroy((bh_ctx*)c);
         return BH_E_CUDA;
     }
+    if (n_patches > 1 && (rc = bh::setup_patches(c, n_patches, offsets)) != BH_OK) {
+        fprintf(stderr, "%s: %s\n", who, c->err.c_str());
+        bh_destroy((bh_ctx*)c);
+        return rc;
+    }
     *out = (bh_ctx*)c;
     return BH_OK;
+}
+
+int bh_create(const bh_params* p, void* stream, bh_ctx** out) {
+    return create_ctx("bh_create", p, 1, nullptr, stream, out);
+}
+
+int bh_batch_create(const bh_params* p, int n_patches, const int64_t* offsets, void* stream, bh_ctx** out) {
+    if (n_patches < 1) {
+        fprintf(stderr, "bh_batch_create: n_patches must be >= 1\n");
+        if (out) *out = nullptr;
+        return BH_E_INVAL;
+    }
+    if (n_patches == 1) return create_ctx("bh_batch_create", p, 1, nullptr, stream, out);
+    return create_ctx("bh_batch_create", p, n_patches, offsets, stream, out);
 }
 
 int bh_destroy(bh_ctx* ctx) {
@@ -210,6 +264,7 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq);
     for (int b = 0; b < 2; ++b) {
         release(c->key[b]);
         release(c->idx[b]);
@@ -346,8 +401,11 @@ int bh_get_root(bh_ctx* ctx, double* lo3, double* L) {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BH_E_INVAL;
     if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
-    if (lo3) for (int a = 0; a < 3; ++a) lo3[a] = c->h_lo[a];
-    if (L) *L = c->h_L;
+    for (int q = 0; q < c->n_patches; ++q) {
+        if (lo3)
+            for (int a = 0; a < 3; ++a) lo3[3 * q + a] = c->h_box[8 * q + a];
+        if (L) L[q] = c->h_box[8 * q + 3];
+    }
     return BH_OK;
 }
 

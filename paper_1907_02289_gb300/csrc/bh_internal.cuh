@@ -66,10 +66,19 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_force;
 
+    // patches: independent particle sets, each with its own root box and
+    // tree (a forest whose roots are nodes 0..n_patches-1); 1 for one set
+    int n_patches = 1;
+    std::vector<int64_t> h_off;         // particle offsets of the patches (n_patches + 1)
+    DBuf<int64_t> d_off;                // the same on the device
+    DBuf<uint32_t> tile_meta;           // sort tiles per patch (4 words per tile), n_patches > 1
+    int64_t n_tiles = 0;
+    DBuf<long long> d_rcq;              // per patch walk contact threshold
+
     // status and small device scalars
     int* d_status = nullptr;
-    double* d_box = nullptr;   // lo[3], L, S, spare
-    double h_lo[3] = {0, 0, 0}, h_L = 1.0, h_S = 0.0;
+    double* d_box = nullptr;   // per patch: lo[3], L, S, spare x3 (8 doubles)
+    std::vector<double> h_box; // host copy of d_box
     unsigned long long* d_small = nullptr;  // scan totals etc. (64 words)
 
     // keys and sort
@@ -158,6 +167,8 @@ cudaError_t scan_u32_with(cudaStream_t s, const uint32_t* in, uint32_t* out, int
 int stage_keys(Ctx* c, const bh_particles* p);     // root box + keys (+ status on NaN)
 int stage_sort(Ctx* c);                            // stable LSD radix sort of (key, idx)
 int stage_permute(Ctx* c, bh_particles* p);        // gather particle arrays into key order
+int setup_patches(Ctx* c, int n_patches, const int64_t* off);  // bh_api.cu
+int64_t sort_tiles_for(const std::vector<int64_t>& off, std::vector<uint32_t>* meta);  // sort.cu
 // context-free sort over caller buffers (sort.cu); scratch >= sort_scratch_words(n) words
 int64_t sort_scratch_words(int64_t n);
 cudaError_t sort_setup_device();

@@ -6,6 +6,8 @@
 // largest extent of the root box (1 if 0); key bit 3b+2/3b+1/3b = bit b of
 // q_x/q_y/q_z.  The subtraction and product are done with _rn intrinsics so
 // that no multiply-add contraction changes a key.
+#include <algorithm>
+
 #include "bh_internal.cuh"
 
 namespace bh {
@@ -99,14 +101,14 @@ __device__ __forceinline__ uint32_t quantise(double v, double lo, double S) {
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, int64_t n, const double* __restrict__ box,
-                       uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
+                       uint64_t* __restrict__ key, uint32_t* __restrict__ idx, uint32_t idx_base) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double S = box[4];
     uint32_t qx = quantise(x[i], box[0], S), qy = quantise(y[i], box[1], S),
              qz = quantise(z[i], box[2], S);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    idx[i] = (uint32_t)i;
+    idx[i] = idx_base + (uint32_t)i;
 }
 
 // ---------------------------------------------------------------------------
@@ -116,12 +118,45 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
 //   downsweep stable in-tile ranking (warp match + per-warp counters), local
 //             reorder through shared memory, coalesced scatter.
 // Stability: ranks follow (tile, warp, round, lane) = input order.
+//
+// Several patches (independent particle sets, each sorted on its own): tiles
+// never straddle a patch, and the histogram of patch p is stored as its own
+// digit-major block after those of patches 0..p-1, so the one scan orders
+// the output by (patch, digit, tile).  tmeta holds per tile {first key, key
+// count, first tile of its patch, tile count of its patch}; NULL means one
+// patch cut into uniform tiles.
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                       // per lane
 constexpr int kSortTile = kSortThreads * kSortItems; // 4096
 constexpr int kRadix = 256;
+
+struct TileInfo {
+    int64_t start;  // first key of the tile
+    int cnt;        // keys in the tile
+    int64_t hbase;  // histogram slot of (digit 0, this tile)
+    int nt;         // tile count of the tile's patch (histogram stride)
+};
+
+__device__ __forceinline__ TileInfo tile_info(const uint32_t* __restrict__ tmeta, int64_t n, int ntiles) {
+    const int t = blockIdx.x;
+    TileInfo ti;
+    if (tmeta) {
+        const uint4 m = reinterpret_cast<const uint4*>(tmeta)[t];
+        ti.start = m.x;
+        ti.cnt = (int)m.y;
+        ti.hbase = (int64_t)kRadix * m.z + (t - (int)m.z);
+        ti.nt = (int)m.w;
+    } else {
+        ti.start = (int64_t)t * kSortTile;
+        const int64_t r = n - ti.start;
+        ti.cnt = (int)(r < kSortTile ? r : kSortTile);
+        ti.hbase = t;
+        ti.nt = ntiles;
+    }
+    return ti;
+}
 
 __global__ void k_digit_hist(const uint64_t* __restrict__ key, int64_t n, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[8][kRadix];
@@ -140,18 +175,18 @@ __global__ void k_digit_hist(const uint64_t* __restrict__ key, int64_t n, uint32
 
 __global__ void __launch_bounds__(kSortThreads) k_upsweep(const uint64_t* __restrict__ key, int64_t n,
                                                          int shift, uint32_t* __restrict__ hist,
-                                                         int ntiles) {
+                                                         int ntiles, const uint32_t* __restrict__ tmeta) {
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const TileInfo ti = tile_info(tmeta, n, ntiles);
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
-        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(key[i] >> shift) & 0xff], 1u);
+        const int r = k * kSortThreads + threadIdx.x;
+        if (r < ti.cnt) atomicAdd(&h[(key[ti.start + r] >> shift) & 0xff], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    hist[ti.hbase + (int64_t)threadIdx.x * ti.nt] = h[threadIdx.x];
 }
 
 struct DownSmem {
@@ -166,15 +201,16 @@ struct DownSmem {
 __global__ void __launch_bounds__(kSortThreads) k_downsweep(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin, int64_t n, int shift,
     const uint32_t* __restrict__ offs, int ntiles, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ iout) {
+    uint32_t* __restrict__ iout, const uint32_t* __restrict__ tmeta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
-    S.goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    const TileInfo ti = tile_info(tmeta, n, ntiles);
+    S.goff[threadIdx.x] = offs[ti.hbase + (int64_t)threadIdx.x * ti.nt];
     __syncthreads();
 
-    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t tbase = ti.start, tend = ti.start + ti.cnt;
     const int64_t wbase = tbase + (int64_t)w * (32 * kSortItems);
     const unsigned lt = (1u << lane) - 1u;
     uint64_t kr[kSortItems];
@@ -182,7 +218,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int64_t pos = wbase + r * 32 + lane;
-        bool valid = pos < n;
+        bool valid = pos < tend;
         uint64_t k = valid ? kin[pos] : 0;
         uint32_t d = valid ? (uint32_t)((k >> shift) & 0xff) : 0x100u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -225,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int64_t pos = wbase + r * 32 + lane;
-        if (pos < n) {
+        if (pos < tend) {
             uint32_t d = (uint32_t)((kr[r] >> shift) & 0xff);
             uint32_t p = S.tstart[d] + S.whist[w][d] + lr[r];
             S.skey[p] = kr[r];
@@ -233,8 +269,7 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(
         }
     }
     __syncthreads();
-    int64_t tn = n - tbase;
-    if (tn > kSortTile) tn = kSortTile;
+    const int tn = ti.cnt;
     for (int q = threadIdx.x; q < tn; q += kSortThreads) {
         uint64_t k = S.skey[q];
         uint32_t d = (uint32_t)((k >> shift) & 0xff);
@@ -257,28 +292,37 @@ __global__ void k_gather8(const unsigned long long* __restrict__ src, unsigned l
 
 }  // namespace
 
+// Root box and keys of each patch (one patch: the whole set).  idx holds
+// global particle indices.
 int stage_keys(Ctx* c, const bh_particles* p) {
     const int64_t n = c->n;
-    const int nb = c->num_sms * 4;
-    BH_TRY(grow(c, c->pscratch, (size_t)(n > 6 * nb ? n : 6 * nb), "particle scratch"));
+    const int nbmax = c->num_sms * 4;
+    BH_TRY(grow(c, c->pscratch, (size_t)(n > 6 * nbmax ? n : 6 * nbmax), "particle scratch"));
     double* part = c->pscratch.p;
-    k_box_partial<<<nb, kBoxThreads, 0, c->stream>>>(p->x, p->y, p->z, n, part, c->d_status);
-    BH_LAUNCH(c);
-    k_box_final<<<1, 32, 0, c->stream>>>(part, nb, c->d_box);
-    BH_LAUNCH(c);
     for (int b = 0; b < 2; ++b) {
         BH_TRY(grow(c, c->key[b], (size_t)n, "keys"));
         BH_TRY(grow(c, c->idx[b], (size_t)n, "sort indices"));
     }
-    k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(p->x, p->y, p->z, n, c->d_box, c->key[0].p, c->idx[0].p);
-    BH_LAUNCH(c);
+    for (int q = 0; q < c->n_patches; ++q) {
+        const int64_t o = c->h_off[q], np = c->h_off[q + 1] - o;
+        const int nb = (int)std::min<int64_t>(nbmax, blocks_for(np, kBoxThreads));
+        double* box = c->d_box + 8 * q;
+        k_box_partial<<<nb, kBoxThreads, 0, c->stream>>>(p->x + o, p->y + o, p->z + o, np, part, c->d_status);
+        BH_LAUNCH(c);
+        k_box_final<<<1, 32, 0, c->stream>>>(part, nb, box);
+        BH_LAUNCH(c);
+        k_keys<<<blocks_for(np, 256), 256, 0, c->stream>>>(p->x + o, p->y + o, p->z + o, np, box,
+                                                           c->key[0].p + o, c->idx[0].p + o, (uint32_t)o);
+        BH_LAUNCH(c);
+    }
     c->key_cur = 0;
     return BH_OK;
 }
 
 int stage_sort(Ctx* c) {
     const int64_t n = c->n;
-    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    const uint32_t* tmeta = c->n_patches > 1 ? c->tile_meta.p : nullptr;
+    const int ntiles = c->n_patches > 1 ? (int)c->n_tiles : (int)((n + kSortTile - 1) / kSortTile);
     BH_TRY(grow(c, c->digit_hist, 8 * kRadix, "digit histogram"));
     BH_TRY(grow(c, c->sort_hist, (size_t)kRadix * ntiles, "sort histogram"));
     BH_CUDA(c, cudaMemsetAsync(c->digit_hist.p, 0, 8 * kRadix * sizeof(uint32_t), c->stream));
@@ -299,12 +343,12 @@ int stage_sort(Ctx* c) {
             if ((int64_t)h[pass * kRadix + d] == n) trivial = true;
         if (trivial) continue;  // every key has the same digit: order unchanged
         const int shift = 8 * pass, a = c->key_cur, b = 1 - a;
-        k_upsweep<<<ntiles, kSortThreads, 0, c->stream>>>(c->key[a].p, n, shift, c->sort_hist.p, ntiles);
+        k_upsweep<<<ntiles, kSortThreads, 0, c->stream>>>(c->key[a].p, n, shift, c->sort_hist.p, ntiles, tmeta);
         BH_LAUNCH(c);
         BH_TRY(scan_u32(c, c->sort_hist.p, c->sort_hist.p, (int64_t)kRadix * ntiles, nullptr));
         k_downsweep<<<ntiles, kSortThreads, smem, c->stream>>>(c->key[a].p, c->idx[a].p, n, shift,
                                                                c->sort_hist.p, ntiles, c->key[b].p,
-                                                               c->idx[b].p);
+                                                               c->idx[b].p, tmeta);
         BH_LAUNCH(c);
         c->key_cur = b;
     }
@@ -327,6 +371,24 @@ int stage_permute(Ctx* c, bh_particles* p) {
         BH_CUDA(c, cudaMemcpyAsync(arrs[a], c->pscratch.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
     return BH_OK;
+}
+
+// Sort tiles of the patches: 4 words per tile (see TileInfo).
+int64_t sort_tiles_for(const std::vector<int64_t>& off, std::vector<uint32_t>* meta) {
+    int64_t t = 0;
+    for (size_t q = 0; q + 1 < off.size(); ++q) {
+        const int64_t np = off[q + 1] - off[q], nt = (np + kSortTile - 1) / kSortTile, t0 = t;
+        for (int64_t u = 0; u < nt; ++u, ++t) {
+            if (meta) {
+                const int64_t st = off[q] + u * kSortTile, r = off[q + 1] - st;
+                meta->push_back((uint32_t)st);
+                meta->push_back((uint32_t)(r < kSortTile ? r : kSortTile));
+                meta->push_back((uint32_t)t0);
+                meta->push_back((uint32_t)nt);
+            }
+        }
+    }
+    return t;
 }
 
 // Context-free form of stage_sort for callers that supply every buffer: all
@@ -359,11 +421,11 @@ cudaError_t sort_pairs_with(cudaStream_t s, uint64_t* keys, uint32_t* idx, uint6
     uint32_t* ib[2] = {idx, itmp};
     for (int pass = 0; pass < 8; ++pass) {
         const int a = pass & 1, b = 1 - a;
-        k_upsweep<<<ntiles, kSortThreads, 0, s>>>(kb[a], n, 8 * pass, hist, ntiles);
+        k_upsweep<<<ntiles, kSortThreads, 0, s>>>(kb[a], n, 8 * pass, hist, ntiles, nullptr);
         cudaError_t e = scan_u32_with(s, hist, hist, (int64_t)kRadix * ntiles, sums);
         if (e != cudaSuccess) return e;
         k_downsweep<<<ntiles, kSortThreads, sizeof(DownSmem), s>>>(kb[a], ib[a], n, 8 * pass, hist, ntiles,
-                                                                   kb[b], ib[b]);
+                                                                   kb[b], ib[b], nullptr);
     }
     return cudaGetLastError();
 }

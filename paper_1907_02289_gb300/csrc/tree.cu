@@ -25,11 +25,15 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     return (uint32_t)x;
 }
 
-__global__ void k_root(uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent, uint32_t n) {
-    level[0] = 0;
-    begin[0] = 0;
-    end[0] = n;
-    parent[0] = -1;
+// Roots: node q is the root of patch q (particles [off[q], off[q+1])).
+__global__ void k_roots(uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,
+                        const int64_t* __restrict__ off, int np) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    level[q] = 0;
+    begin[q] = (uint32_t)off[q];
+    end[q] = (uint32_t)off[q + 1];
+    parent[q] = -1;
 }
 
 // Child boundaries of each node of one level: bnd[9 t + o] = first particle
@@ -375,10 +379,11 @@ int grow_nodes(Ctx* c, size_t need) {
 int stage_octree(Ctx* c) {
     const int64_t n = c->n;
     const uint64_t* key = c->key[c->key_cur].p;
-    BH_TRY(grow_nodes(c, (size_t)(n / 2 + 64)));
-    k_root<<<1, 1, 0, c->stream>>>(c->level.p, c->begin.p, c->end.p, c->parent.p, (uint32_t)n);
+    const int np = c->n_patches;
+    BH_TRY(grow_nodes(c, (size_t)(n / 2 + 64 + np)));
+    k_roots<<<blocks_for(np, 64), 64, 0, c->stream>>>(c->level.p, c->begin.p, c->end.p, c->parent.p, c->d_off.p, np);
     BH_LAUNCH(c);
-    c->lvl_start.assign({0, 1});
+    c->lvl_start.assign({0, (int64_t)np});
     for (int lev = 0;; ++lev) {
         const int64_t ls = c->lvl_start[lev], le = c->lvl_start[lev + 1], cnt = le - ls;
         BH_TRY(grow(c, c->split_cnt, (size_t)cnt, "split counts"));

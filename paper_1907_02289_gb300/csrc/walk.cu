@@ -11,8 +11,11 @@
 // delta^2.  A node of level l (side 2^(21-l) cells) is opened iff
 // fl(theta^2 * d2) < 4^(21-l), or d2 <= (r_coll * S)^2.  Both comparisons
 // are monotone in the integer d2, so the host turns them into integer
-// thresholds once per build: open iff d2 < D[l] or d2 <= RCQ.
+// thresholds once per build: open iff d2 < D[l] or d2 <= RCQ.  With several
+// patches a group walks the tree of its own patch (root = patch index), and
+// RCQ is per patch (each patch has its own key grid).
 #include <cmath>
+#include <vector>
 
 #include "bh_internal.cuh"
 
@@ -21,7 +24,9 @@ namespace {
 
 struct WalkParams {
     long long D[kLevels + 1];
-    long long rcq;
+    const long long* rcq;  // per patch
+    const int64_t* off;    // patch particle offsets (np + 1)
+    int np;
 };
 
 template <bool FILL>
@@ -48,9 +53,18 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
             pbase = np_io[k];
             cbase = nc_io[k];
         }
+        int root = 0;
+        for (int lo = 0, hi = wp.np - 1; lo < hi;) {  // last patch starting at or before gb
+            const int mid = (lo + hi + 1) >> 1;
+            if (wp.off[mid] <= (int64_t)gb)
+                lo = root = mid;
+            else
+                hi = mid - 1;
+        }
+        const long long rcq = wp.rcq[root];
         int sn[kLevels + 3], se[kLevels + 3];
         int sp = 0;
-        int node = 0;
+        int node = root;
         for (;;) {
             const WalkNode R = wn[node];
             const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
@@ -58,7 +72,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
             const int d1 = max(0, max((int)R.a.y - ghi1 - 1, glo1 - (int)R.b.y - 1));
             const int d2i = max(0, max((int)R.a.z - ghi2 - 1, glo2 - (int)R.b.z - 1));
             const long long d2 = (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2i * d2i;
-            const bool open = d2 < wp.D[lev] || d2 <= wp.rcq;
+            const bool open = d2 < wp.D[lev] || d2 <= rcq;
             if (open) {
                 if (nch == 0) {
                     if (FILL) P[pbase + np] = node;
@@ -165,9 +179,9 @@ WalkParams walk_params(const Ctx* c) {
         while (!(th2 * (double)d >= s2)) ++d;
         w.D[l] = d;
     }
-    const double rcq = c->prm.r_coll * c->h_S;
-    const double rcq2 = rcq * rcq;
-    w.rcq = (rcq2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(rcq2);
+    w.rcq = c->d_rcq.p;
+    w.off = c->d_off.p;
+    w.np = c->n_patches;
     return w;
 }
 
@@ -178,6 +192,15 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->cnt_p, (size_t)ng + 1, "list offsets P"));
     BH_TRY(grow(c, c->cnt_c, (size_t)ng + 1, "list offsets C"));
     BH_TRY(grow(c, c->cnt_j, (size_t)ng + 1, "list offsets J"));
+    std::vector<long long> rcq(c->n_patches);
+    for (int q = 0; q < c->n_patches; ++q) {
+        const double r = c->prm.r_coll * c->h_box[8 * q + 4];
+        const double r2 = r * r;
+        rcq[q] = (r2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(r2);
+    }
+    BH_TRY(grow(c, c->d_rcq, rcq.size(), "walk contact thresholds"));
+    BH_CUDA(c, cudaMemcpyAsync(c->d_rcq.p, rcq.data(), rcq.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                               c->stream));
     const WalkParams wp = walk_params(c);
     unsigned long long* inter = c->d_small + 8;
     BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));
