@@ -38,8 +38,9 @@ sys.path.insert(0, ROOT)
 
 # FP32 flops per interaction of the force kernel (FFMA/FFMA2 lane = 2,
 # FADD/FMUL = 1; rsqrt not counted): particle-particle with the two-float
-# separation 24, particle-cell with quadrupole 49, monopole only 18.
-FLOPS_PP, FLOPS_PC2, FLOPS_PC1 = 24, 49, 18
+# separation 24 (23 without softening, where the + eps^2 is not issued),
+# particle-cell with quadrupole 49, monopole only 18.
+FLOPS_PP, FLOPS_PP_NO_EPS, FLOPS_PC2, FLOPS_PC1 = 24, 23, 49, 18
 # The paper's convention (Sec. 5.1): 49 per particle-particle, 31 per particle-cell.
 PAPER_PP, PAPER_PC = 49, 31
 NUM_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -60,11 +61,29 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
     return ap.parse_args()
 
 
 def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over all ranks (timing: the job takes as long as its
+    slowest replica); x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank's replica: every rank steps its own, different ring."""
+    return base_seed + 1000 * rank
 
 
 class Clocks:
@@ -232,13 +251,29 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pr = synth.PRESETS[args.workload]
-    n = args.n or pr["n"]
     prm = dict(pr["params"])
-    P = synth.ring(n, pr["seed"] + 1000 * rank) if pr["kind"] == "ring" else synth.make(args.workload, n)[0]
+    offsets = None
+    if pr["kind"] == "patches":
+        parts, sizes = synth.patches(seed=replica_seed(pr["seed"], rank))
+        P = {f: np.concatenate([q[f] for q in parts]) for f in synth.FIELDS}
+        offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n = int(offsets[-1])
+    else:
+        n = args.n or pr["n"]
+        P = synth.ring(n, replica_seed(pr["seed"], rank)) if pr["kind"] == "ring" else synth.make(args.workload, n)[0]
     stream = torch.cuda.current_stream()
 
-    ctx = bh.Context(**prm)
+    ctx = bh.Context(offsets=offsets, **prm)
     D = bh.Particles(P)
+    tuning = None
+    if pr["kind"] == "patches" or args.autotune:
+        # the batched configuration: autotuned launch settings and n_g, one
+        # persistent launch per step, list-reusing steps as CUDA graphs
+        tuned_ms = ctx.bh_autotune(D)
+        if pr["kind"] == "patches":
+            ctx.bh_set_tuning(graph=1)
+        tuning = dict(ctx.bh_get_tuning(), autotuned_step_ms=tuned_ms)
+        prm["n_g"] = tuning["n_g"]
     # initial evaluation + warm-up steps (evaluations 0..W); timed steps then
     # start on a list-constructing evaluation when W = 3 and rebuild_every = 4
     ctx.bh_step(D, args.warmup)
@@ -268,24 +303,30 @@ def run_ours(args):
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     force_ms, force_launches = ctx.bh_get_timing(reset=True)
+    balance = None
+    if ctx.bh_get_tuning()["sched"] != bh.BH_SCHED_GRID and prm["precision"] == 1:
+        try:
+            balance = ctx.bh_get_balance()
+        except bh.BHError:
+            balance = None
     ctx.bh_set_timing(False)
     c1 = ctx.bh_get_counters()
     launches = c1["n_launches"] - c0["n_launches"]
     inter = pp + pc
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, "cuda")
     value = world * inter / elapsed
     flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
-    flops = pp * FLOPS_PP + pc * flops_pc
-    achieved = flops / (force_ms / 1e3) / 1e12 if force_ms > 0 else None
+    flops_pp = FLOPS_PP_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP
+    flops = pp * flops_pp + pc * flops_pc
+    # force launches timed by the library (graph-captured steps are not timed
+    # per launch): mean flops of an evaluation / mean time of a timed launch
+    achieved = (flops / args.steps) / (force_ms / force_launches / 1e3) / 1e12 if force_ms > 0 else None
     peak = fp32_peak_tflops(SM_MAX_MHZ)
     roofline = {"kernel": "k_force32" if prm["precision"] == 1 else "k_force64", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": recorded_traffic("k_force32", args.workload, n) if prm["precision"] == 1 else None,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
-                "flops_per_interaction": {"pp": FLOPS_PP, "pc": flops_pc},
+                "flops_per_interaction": {"pp": flops_pp, "pc": flops_pc},
                 "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}
     if clk.get("sm_mhz"):
         roofline["peak_at_median_clock"] = fp32_peak_tflops(clk["sm_mhz"])
@@ -295,12 +336,12 @@ def run_ours(args):
     err = None
     if not args.no_error and prm["precision"] == 1:
         Pnow = D.numpy()
-        ctxe = bh.Context(**dict(prm, precision=0))
+        ctxe = bh.Context(offsets=offsets, **dict(prm, precision=0))
         De = bh.Particles(Pnow)
         ctxe.bh_build_tree(De)
         ctxe.bh_make_lists()
         ctxe.bh_compute_forces(De, bh.BH_FORCE_TREE_ONLY)
-        ctx32 = bh.Context(**prm)
+        ctx32 = bh.Context(offsets=offsets, **prm)
         D32 = bh.Particles(De.numpy())
         ctx32.bh_build_tree(D32)
         ctx32.bh_make_lists()
@@ -332,7 +373,9 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        ctxh = bh.Context(**prm)
+        ctxh = bh.Context(offsets=offsets, **prm)
+        if tuning:
+            ctxh.bh_set_tuning(**{k: v for k, v in tuning.items() if k != "autotuned_step_ms"})
         H = bh.HostParticles(P, pinned=True)
         ctxh.bh_step_host(H, args.warmup)
         ctxh.bh_set_timing(False)
@@ -346,10 +389,7 @@ def run_ours(args):
             pce += c["n_pc"]
         barrier()
         te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, "cuda")
         e2e = {"value": world * (ppe + pce) / te, "unit": "interactions/s",
                "h2d_bytes_per_step": n * (10 * 8 + 8), "d2h_bytes_per_step": n * (10 * 8 + 8),
                "particle_steps_per_s": world * n * args.steps / te, "api": "bh_step_host (pinned host buffers)"}
@@ -357,11 +397,26 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        n_s = min(n, 1 << 21)
-        rate, inter_s, dt_s, cores = cpu_oracle_rate(oracle_sector(n_s, n, prm), prm)
+        if offsets is None:
+            n_s = min(n, 1 << 21)
+            rate, inter_s, dt_s, cores = cpu_oracle_rate(oracle_sector(n_s, n, prm), prm)
+            what = (f"one list-constructing force evaluation of a {n_s}-particle ring sector at the surface "
+                    f"density of the {n}-particle ring")
+        else:  # the first patches, about 2^20 particles
+            k = int(np.searchsorted(offsets, 1 << 20)) or 1
+            k = min(k, len(offsets) - 1)
+            sub = {f: P[f][:offsets[k]] for f in synth.FIELDS}
+            inter_s = dt_s = 0.0
+            for q in range(k):
+                part = {f: sub[f][offsets[q]:offsets[q + 1]] for f in synth.FIELDS}
+                _, i_q, t_q, cores = cpu_oracle_rate(part, prm)
+                inter_s += i_q
+                dt_s += t_q
+            rate = inter_s / dt_s
+            inter_s = int(inter_s)
+            what = f"one list-constructing force evaluation of each of the first {k} patches ({int(offsets[k])} particles)"
         cpu = {"value": rate, "unit": "interactions/s", "cores": cores, "kind": "oracle",
-               "sample": f"one list-constructing force evaluation of a {n_s}-particle ring sector at the surface "
-                         f"density of the {n}-particle ring ({inter_s} interactions, {dt_s:.1f} s)"}
+               "sample": f"{what} ({inter_s} interactions, {dt_s:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
@@ -373,13 +428,16 @@ def run_ours(args):
                            "precision": "FP32 group-relative forces, FP64 positions/velocities/updates"
                            if prm["precision"] == 1 else "FP64",
                            "l2": "inputs larger than L2 (particle arrays %.1f GB)" % (n * 88 / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           **({"patches": len(offsets) - 1} if offsets is not None else {}),
+                           **({"tuning": tuning} if tuning else {})},
                 "particle_steps_per_s": world * n * args.steps / elapsed,
                 "interactions_per_step": inter / args.steps,
                 "pct_fp32_peak": 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
                 "force_error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk,
+                **({"load_balance_busy_fraction": balance} if balance is not None else {})}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

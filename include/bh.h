@@ -183,6 +183,53 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out);
 int bh_set_timing(bh_ctx* ctx, int enable);
 int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset);
 
+/* Launch tuning (the persistent-kernel schedule of Sec. 4.6's load balance,
+ * and the knobs the autotuner searches).  Schedules of the FP32 force kernel:
+ *  BH_SCHED_GRID     one warp per group, grid sized to the groups;
+ *  BH_SCHED_STATIC   persistent grid (as many blocks as fit on the GPU), each
+ *                    warp takes every (warps in grid)-th group of the order;
+ *  BH_SCHED_DYNAMIC  persistent grid, each warp draws its next group from an
+ *                    atomic ticket counter (dynamic longest-first when
+ *                    order_by_cost is set).
+ * Groups are taken in order of size class, and, with order_by_cost, by
+ * decreasing estimated cost n_i (n_i + list particles + 2 list cells) within
+ * a class. */
+#define BH_SCHED_GRID 0
+#define BH_SCHED_STATIC 1
+#define BH_SCHED_DYNAMIC 2
+typedef struct {
+    int n_g;           /* group size limit; a change forces a list build at the next evaluation */
+    int chunk;         /* particles of a group per warp pass: 32, 64 or 96 */
+    int warps;         /* warps per block of the FP32 force kernel, 1..8 */
+    int sched;         /* BH_SCHED_* */
+    int order_by_cost; /* 0 or 1 */
+    int graph;         /* 1: bh_step issues each list-reusing step (kick-drift,
+                          moment refresh, force kernel, contact pass, kick) as
+                          one CUDA graph launch, captured after each list
+                          build; the contact pass then reads its count on the
+                          device, and an overflow of its buffer is reported
+                          (BH_E_LIST_OVERFLOW) at the next synchronising call */
+} bh_tuning;
+/* Errors: BH_E_INVAL for a value out of range (n_g < n_leaf included). */
+int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t);
+int bh_get_tuning(bh_ctx* ctx, bh_tuning* t);
+
+/* Autotuner: times candidate settings on the caller's particles and keeps
+ * the fastest.  First the launch settings (chunk x warps x schedule) on the
+ * current n_g, by force-kernel time; then n_g in {64, 96, 128, 192, 256}
+ * (those >= n_leaf) by the cost of one step, force time plus list-build time
+ * / rebuild_every.  Like a list build it reorders the particle arrays; on
+ * return the lists are built with the chosen settings, ax..az hold the
+ * acceleration at the current positions, and the list-reuse schedule starts
+ * afresh.  best_ms (may be NULL) receives the chosen setting's step cost.
+ * Synchronises.  graph is left as set. */
+int bh_autotune(bh_ctx* ctx, bh_particles* p, double* best_ms);
+
+/* Load balance of the last persistent force launch made with timing on
+ * (bh_set_timing): busy fraction = sum over warps of (finish - start) /
+ * (warps x (last finish - first start)).  BH_E_STATE if there is none. */
+int bh_get_balance(bh_ctx* ctx, double* busy_fraction);
+
 /* Stable radix sort that allocates nothing.  The paper has no counterpart:
  * this is the sort of bh_build_tree (Sec. 4.2 step 3a, same kernels, same
  * result) offered on its own to callers that must not allocate device

@@ -257,9 +257,12 @@ class State:
     extra: dict = field(default_factory=dict)
 
 
-def rebuild(P: dict, prm: Params) -> State:
+def rebuild(P: dict, prm: Params, group_subset=None) -> State:
     """List-constructing step (Sec. 4.2, steps 3a-3d): keys, sort, permute,
-    octree, boxes, moments, groups and interaction lists."""
+    octree, boxes, moments, groups and interaction lists.  group_subset
+    (optional) maps the array of all groups to the indices of the groups to
+    keep: lists (and tree forces) are then made for those groups only, for
+    checking a sample of a workload too large to walk whole."""
     x, y, z = P["x"], P["y"], P["z"]
     lo, L = root_box(x, y, z)
     k = keys(x, y, z, lo, L)
@@ -270,6 +273,8 @@ def rebuild(P: dict, prm: Params) -> State:
     qlo, qhi = qboxes(tree, key_coords(sk))
     mom = moments(tree, SP["x"], SP["y"], SP["z"], SP["m"], prm.order)
     grp = groups(tree, prm.n_g)
+    if group_subset is not None:
+        grp = np.ascontiguousarray(grp[group_subset(grp, tree)])
     lst = lists(tree, qlo, qhi, grp, prm.theta, prm.r_coll, L)
     return State(P=SP, lo=lo, L=L, skeys=sk, perm=perm, tree=tree, qlo=qlo, qhi=qhi, mom=mom,
                  groups=grp, lists=lst)

@@ -21,7 +21,9 @@ BH_FORCE_TREE_ONLY = 1
 SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_set_stream", "bh_build_tree", "bh_make_lists",
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
-           "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_sort_keys_static")
+           "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_set_tuning", "bh_get_tuning", "bh_autotune",
+           "bh_get_balance", "bh_sort_keys_static")
+BH_SCHED_GRID, BH_SCHED_STATIC, BH_SCHED_DYNAMIC = 0, 1, 2
 BH_SORT_STATIC_MAX_N = 4194304
 
 
@@ -42,6 +44,10 @@ class bh_particles(ctypes.Structure):
 class bh_counters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
                                                "n_contacts")]
+
+
+class bh_tuning(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph")]
 
 
 _lib = None
@@ -85,6 +91,10 @@ def load(path: str = LIB_PATH):
     lib.bh_get_counters.argtypes = [P, ctypes.POINTER(bh_counters)]
     lib.bh_set_timing.argtypes = [P, ctypes.c_int]
     lib.bh_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.bh_set_tuning.argtypes = [P, ctypes.POINTER(bh_tuning)]
+    lib.bh_get_tuning.argtypes = [P, ctypes.POINTER(bh_tuning)]
+    lib.bh_autotune.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.POINTER(ctypes.c_double)]
+    lib.bh_get_balance.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.bh_sort_keys_static.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_char_p, ctypes.c_size_t]
     _lib = lib
     return lib
@@ -285,6 +295,28 @@ class Context:
 
     def bh_set_timing(self, enable: bool = True):
         return self._chk(self.lib.bh_set_timing(self.h, 1 if enable else 0))
+
+    def bh_set_tuning(self, **kw):
+        """Change some tuning fields (n_g, chunk, warps, sched, order_by_cost, graph)."""
+        t = self.bh_get_tuning(as_struct=True)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        return self._chk(self.lib.bh_set_tuning(self.h, ctypes.byref(t)))
+
+    def bh_get_tuning(self, as_struct: bool = False):
+        t = bh_tuning()
+        self._chk(self.lib.bh_get_tuning(self.h, ctypes.byref(t)))
+        return t if as_struct else {f: getattr(t, f) for f, _ in bh_tuning._fields_}
+
+    def bh_autotune(self, P: "Particles"):
+        ms = ctypes.c_double()
+        self._chk(self.lib.bh_autotune(self.h, ctypes.byref(P.struct), ctypes.byref(ms)))
+        return ms.value
+
+    def bh_get_balance(self):
+        b = ctypes.c_double()
+        self._chk(self.lib.bh_get_balance(self.h, ctypes.byref(b)))
+        return b.value
 
     def bh_get_timing(self, reset: bool = True):
         ms = ctypes.c_double()

@@ -59,7 +59,7 @@ static cudaEvent_t take_event(Ctx* c) {
 }
 
 int timing_begin(Ctx* c) {
-    if (!c->timing) return BH_OK;
+    if (!c->timing || c->capturing) return BH_OK;
     cudaEvent_t a = take_event(c), b = take_event(c);
     if (!a || !b) return fail(c, BH_E_CUDA, "cudaEventCreate failed");
     BH_CUDA(c, cudaEventRecord(a, c->stream));
@@ -68,7 +68,7 @@ int timing_begin(Ctx* c) {
 }
 
 int timing_end(Ctx* c) {
-    if (!c->timing || c->ev_force.empty()) return BH_OK;
+    if (!c->timing || c->capturing || c->ev_force.empty()) return BH_OK;
     BH_CUDA(c, cudaEventRecord(c->ev_force.back().second, c->stream));
     return BH_OK;
 }
@@ -133,6 +133,8 @@ int read_status(Ctx* c) {
     if (st & kStatListOverflow) return fail(c, BH_E_LIST_OVERFLOW, "list buffer overflow");
     if (st & kStatTimeout) return fail(c, BH_E_TIMEOUT, "device wait timed out");
     if (st & kStatBounds) return fail(c, BH_E_STATE, "internal index check failed (access skipped)");
+    if (st & kStatRange)
+        return fail(c, BH_E_INVAL, "a contact acceleration term reached 1024 or was not finite (kappa, eta too large?)");
     return BH_OK;
 }
 
@@ -167,6 +169,7 @@ int make_lists(Ctx* c) {
     if (!c->have_tree) return fail(c, BH_E_STATE, "bh_make_lists needs a tree (call bh_build_tree)");
     BH_TRY(stage_lists(c));
     c->have_lists = true;
+    c->graph_ok = false;
     c->evals_since_build = 0;
     c->n_rebuilds++;
     return BH_OK;
@@ -185,6 +188,212 @@ int evaluate(Ctx* c, bh_particles* p) {
     c->k_eval++;
     c->evals_since_build++;
     return BH_OK;
+}
+
+bool same_arrays(const bh_particles& a, const bh_particles& b) {
+    return a.x == b.x && a.y == b.y && a.z == b.z && a.vx == b.vx && a.vy == b.vy && a.vz == b.vz && a.m == b.m &&
+           a.id == b.id && a.ax == b.ax && a.ay == b.ay && a.az == b.az && a.n == b.n;
+}
+
+// One list-reusing step (kick-drift, moment refresh, forces, kick) as a CUDA
+// graph launch; the graph is captured on the first such step after a list
+// build (or when the arrays change) and updated in place when possible.
+int graph_reuse_step(Ctx* c, bh_particles* p) {
+    const double dt = c->prm.dt;
+    if (!c->graph_ok || !same_arrays(c->graph_p, *p)) {
+        // capture on a private stream (the legacy default stream cannot be
+        // captured); the graph is then launched on the context's stream
+        if (!c->cap_stream) BH_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const cudaStream_t s0 = c->stream;
+        c->stream = c->cap_stream;
+        {
+            const cudaError_t eb = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (eb != cudaSuccess) {
+                c->stream = s0;
+                BH_CUDA(c, eb);
+            }
+        }
+        c->capturing = true;
+        const int64_t l0 = c->n_launches;
+        int rc = stage_kick_drift(c, p, 0.5 * dt, dt);
+        if (rc == BH_OK) rc = stage_moments(c, p);
+        if (rc == BH_OK) rc = stage_force(c, p, true);
+        if (rc == BH_OK) rc = stage_kick(c, p, 0.5 * dt);
+        c->capturing = false;
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        c->stream = s0;
+        c->graph_launches = c->n_launches - l0;
+        c->n_launches = l0;
+        if (rc != BH_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return fail(c, BH_E_CUDA, "stream capture of the step failed: %s", cudaGetErrorString(ec));
+        bool updated = false;
+        if (c->graph_exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(c->graph_exec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->graph_exec);
+                c->graph_exec = nullptr;
+            }
+        }
+        cudaError_t ei = cudaSuccess;
+        if (!updated) ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->graph_exec = nullptr;
+            return fail(c, BH_E_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ei));
+        }
+        c->graph_ok = true;
+        c->graph_p = *p;
+    }
+    BH_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->n_launches += c->graph_launches;
+    c->k_eval++;
+    c->evals_since_build++;
+    return BH_OK;
+}
+
+int check_tuning(Ctx* c, const bh_tuning* t) {
+    if (!t) return fail(c, BH_E_INVAL, "tuning is NULL");
+    if (t->n_g < c->prm.n_leaf) return fail(c, BH_E_INVAL, "n_g must be >= n_leaf");
+    if (t->chunk != 32 && t->chunk != 64 && t->chunk != 96) return fail(c, BH_E_INVAL, "chunk must be 32, 64 or 96");
+    if (t->warps < 1 || t->warps > 8) return fail(c, BH_E_INVAL, "warps must be 1..8");
+    if (t->sched < BH_SCHED_GRID || t->sched > BH_SCHED_DYNAMIC) return fail(c, BH_E_INVAL, "unknown schedule");
+    if ((t->order_by_cost != 0 && t->order_by_cost != 1) || (t->graph != 0 && t->graph != 1))
+        return fail(c, BH_E_INVAL, "order_by_cost and graph must be 0 or 1");
+    return BH_OK;
+}
+
+void apply_tuning(Ctx* c, const bh_tuning* t) {
+    const bool relist = t->n_g != c->prm.n_g || t->chunk != c->tune.chunk || t->order_by_cost != c->tune.order_by_cost;
+    if (t->n_g != c->prm.n_g) c->have_lists = false;
+    c->prm.n_g = t->n_g;
+    c->tune.chunk = t->chunk;
+    c->tune.warps = t->warps;
+    c->tune.sched = t->sched;
+    c->tune.order_by_cost = t->order_by_cost;
+    c->tune.graph = t->graph;
+    c->graph_ok = false;
+    (void)relist;
+}
+
+void read_tuning(const Ctx* c, bh_tuning* t) {
+    t->n_g = c->prm.n_g;
+    t->chunk = c->tune.chunk;
+    t->warps = c->tune.warps;
+    t->sched = c->tune.sched;
+    t->order_by_cost = c->tune.order_by_cost;
+    t->graph = c->tune.graph;
+}
+
+// Elapsed device time of fn() on the context's stream (ms).
+template <class F>
+int time_ms(Ctx* c, F fn, double* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    BH_CUDA(c, cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        BH_CUDA(c, e);
+    }
+    int rc = BH_OK;
+    e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) rc = fn();
+    if (e == cudaSuccess && rc == BH_OK) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess && rc == BH_OK) e = cudaEventSynchronize(b);
+    float f = 0.f;
+    if (e == cudaSuccess && rc == BH_OK) e = cudaEventElapsedTime(&f, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != BH_OK) return rc;
+    BH_CUDA(c, e);
+    *ms = f;
+    return BH_OK;
+}
+
+int autotune(Ctx* c, bh_particles* p, double* best_ms) {
+    BH_TRY(check_particles(c, p, true));
+    const bool timing = c->timing;
+    c->timing = false;
+    bh_tuning cur;
+    read_tuning(c, &cur);
+    const int graph = cur.graph;
+    cur.graph = 0;
+    apply_tuning(c, &cur);
+    double tb = 0.0;
+    auto build = [&]() -> int {
+        BH_TRY(build_tree(c, p));
+        return make_lists(c);
+    };
+    auto force = [&]() -> int {
+        BH_TRY(stage_moments(c, p));
+        return stage_force(c, p, false);
+    };
+    // (1) launch settings on the current n_g, by force-evaluation time
+    BH_TRY(time_ms(c, build, &tb));
+    double best_f = 1e300;
+    bh_tuning best = cur;
+    const int chunks[3] = {32, 64, 96}, warps[3] = {2, 4, 8};
+    for (int ci = 0; ci < 3; ++ci) {
+        bh_tuning t = cur;
+        t.chunk = chunks[ci];
+        apply_tuning(c, &t);
+        if (c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
+        for (int wi = 0; wi < 3; ++wi)
+            for (int sc = BH_SCHED_GRID; sc <= BH_SCHED_DYNAMIC; ++sc) {
+                t.warps = warps[wi];
+                t.sched = sc;
+                apply_tuning(c, &t);
+                double ms = 0.0, ms2 = 0.0;
+                BH_TRY(time_ms(c, force, &ms));
+                BH_TRY(time_ms(c, force, &ms2));
+                if (ms2 < ms) ms = ms2;
+                if (ms < best_f) {
+                    best_f = ms;
+                    best = t;
+                }
+                if (c->prm.precision != BH_PREC_FP32) goto done_launch;  // the FP64 kernel has no such settings
+            }
+    }
+done_launch:
+    // (2) n_g by the cost of a step: force time + list-build time / rebuild_every
+    {
+        double best_step = 1e300;
+        bh_tuning best_ng = best;
+        const int cand[5] = {64, 96, 128, 192, 256};
+        for (int q = 0; q < 5; ++q) {
+            if (cand[q] < c->prm.n_leaf) continue;
+            bh_tuning t = best;
+            t.n_g = cand[q];
+            apply_tuning(c, &t);
+            double b = 0.0, f = 0.0, f2 = 0.0;
+            BH_TRY(time_ms(c, build, &b));
+            BH_TRY(time_ms(c, force, &f));
+            BH_TRY(time_ms(c, force, &f2));
+            if (f2 < f) f = f2;
+            const double step = f + b / c->prm.rebuild_every;
+            if (step < best_step) {
+                best_step = step;
+                best_ng = t;
+            }
+        }
+        best = best_ng;
+        if (best_ms) *best_ms = best_step;
+    }
+    best.graph = graph;
+    apply_tuning(c, &best);
+    BH_TRY(build_tree(c, p));
+    BH_TRY(make_lists(c));
+    BH_TRY(stage_force(c, p, true));
+    c->k_eval = 1;
+    c->evals_since_build = 1;
+    c->have_acc = true;
+    c->timing = timing;
+    return read_status(c);
 }
 
 }  // namespace
@@ -260,11 +469,13 @@ int bh_destroy(bh_ctx* ctx) {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BH_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->d_status);
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq);
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->order_cnt); release(c->warp_time); release(c->contact_acc);
     for (int b = 0; b < 2; ++b) {
         release(c->key[b]);
         release(c->idx[b]);
@@ -334,10 +545,56 @@ int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps) {
         c->have_acc = true;
     }
     for (int s = 0; s < nsteps; ++s) {
+        if (c->tune.graph && c->have_lists && c->k_eval % c->prm.rebuild_every != 0) {
+            BH_TRY(bh::graph_reuse_step(c, p));
+            continue;
+        }
         BH_TRY(bh::stage_kick_drift(c, p, 0.5 * dt, dt));
         BH_TRY(bh::evaluate(c, p));
         BH_TRY(bh::stage_kick(c, p, 0.5 * dt));
     }
+    return BH_OK;
+}
+
+int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    BH_TRY(bh::check_tuning(c, t));
+    const bool reorder = t->chunk != c->tune.chunk || t->order_by_cost != c->tune.order_by_cost;
+    bh::apply_tuning(c, t);
+    if (reorder && c->have_lists && c->prm.precision == BH_PREC_FP32) BH_TRY(bh::build_order32(c));
+    return BH_OK;
+}
+
+int bh_get_tuning(bh_ctx* ctx, bh_tuning* t) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !t) return BH_E_INVAL;
+    bh::read_tuning(c, t);
+    return BH_OK;
+}
+
+int bh_autotune(bh_ctx* ctx, bh_particles* p, double* best_ms) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    return bh::autotune(c, p, best_ms);
+}
+
+int bh_get_balance(bh_ctx* ctx, double* busy_fraction) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !busy_fraction) return BH_E_INVAL;
+    if (c->warp_time_n <= 0 || !c->warp_time.p) return bh::fail(c, BH_E_STATE, "no timed persistent force launch");
+    std::vector<unsigned long long> t(2 * (size_t)c->warp_time_n);
+    BH_CUDA(c, cudaMemcpyAsync(t.data(), c->warp_time.p, t.size() * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned long long t0 = ~0ull, t1 = 0;
+    double busy = 0.0;
+    for (int64_t w = 0; w < c->warp_time_n; ++w) {
+        t0 = std::min(t0, t[2 * w]);
+        t1 = std::max(t1, t[2 * w + 1]);
+        busy += (double)(t[2 * w + 1] - t[2 * w]);
+    }
+    *busy_fraction = t1 > t0 ? busy / ((double)c->warp_time_n * (double)(t1 - t0)) : 1.0;
     return BH_OK;
 }
 

@@ -21,6 +21,7 @@ constexpr int kStatNonFinite = 1;
 constexpr int kStatListOverflow = 2;
 constexpr int kStatTimeout = 4;
 constexpr int kStatBounds = 8;  // an internal index check failed (access skipped)
+constexpr int kStatRange = 16;  // a contact term outside the fixed-point accumulator's range
 
 // Device buffer that only grows.
 template <typename T>
@@ -48,8 +49,18 @@ struct WalkNode {
     uint4 a, b;
 };
 
+// Launch tuning of the FP32 force kernel (bh_set_tuning / the autotuner).
+struct Tuning {
+    int chunk = 96;          // largest i-chunk per warp pass: 32, 64 or 96 particles
+    int warps = 4;           // warps per block, 1..8
+    int sched = BH_SCHED_GRID;
+    int order_by_cost = 1;   // within a size class, largest estimated cost first
+    int graph = 0;           // capture list-reusing steps of bh_step in a CUDA graph
+};
+
 struct Ctx {
     bh_params prm;
+    Tuning tune;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     std::string err;
@@ -107,6 +118,7 @@ struct Ctx {
     DBuf<float4> cell32;             // 3 per node: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz)
     DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
     DBuf<unsigned long long> contacts;  // (i, j) contact candidates for the FP64 pass
+    DBuf<unsigned long long> contact_acc;  // per particle fixed-point contact sums (3 per particle)
     int64_t n_contacts = 0;
 
     // groups
@@ -115,6 +127,17 @@ struct Ctx {
     DBuf<uint32_t> gflag, gpos;
     DBuf<int32_t> groups;            // node ids ordered by begin
     DBuf<int32_t> order;             // force-kernel processing order of groups
+    DBuf<unsigned long long> order_cnt;  // order buckets: counts/starts and cursors
+    int f32_attr_device = -1;            // device the FP32 kernels' smem limit was raised on
+    unsigned f32_blocks = 0;             // grid of the last FP32 force launch
+    DBuf<unsigned long long> warp_time;  // per warp (start, end) of the last persistent launch
+    int64_t warp_time_n = 0;
+    bool capturing = false;              // issuing work into a stream capture
+    cudaGraphExec_t graph_exec = nullptr;  // the captured list-reusing step
+    cudaStream_t cap_stream = nullptr;   // private stream the step is captured on
+    bool graph_ok = false;               // graph_exec matches the current lists and arrays
+    bh_particles graph_p{};              // particle arrays the graph was captured with
+    int64_t graph_launches = 0;          // kernels in the graph
 
     // lists
     int64_t n_pp = 0, n_pc = 0, n_jj = 0;

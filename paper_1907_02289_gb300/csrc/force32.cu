@@ -42,13 +42,12 @@
 namespace bh {
 namespace {
 
-#ifndef BH_F32_MINB
-#define BH_F32_MINB 4  // resident blocks per SM the register budget is sized for
+#ifndef BH_F32_MAXW
+#define BH_F32_MAXW 8  // most warps per block (the register budget is sized for 2 such blocks per SM)
 #endif
 #ifndef BH_F32_TILE
 #define BH_F32_TILE 1  // list particles per tile = 64 x this, list cells = 32 x this
 #endif
-constexpr int kW32 = 4;                   // warps per block
 constexpr int kTileJ = 64 * BH_F32_TILE;  // list particles per tile (2 per lane per 64)
 constexpr int kTileC = 32 * BH_F32_TILE;  // list cells per tile (1 per lane per 32)
 constexpr int kSlots = 3;                 // i-slots per lane (full slots + tail)
@@ -57,8 +56,10 @@ constexpr uint32_t kNone = 0xffffffffu;
 
 // Pair-term modes: contact candidates detected (r_coll > 0); plain (no
 // contact, r_coll^2 + eps^2 > 0); mask (r_coll = eps = 0: coincident pairs
-// masked out explicitly).
-constexpr int kContact = 0, kPlain = 1, kMask = 2;
+// masked out explicitly); contact without softening (r_coll > 0, eps = 0,
+// which saves the + eps^2 of every pair).
+constexpr int kContact = 0, kPlain = 1, kMask = 2, kContact0 = 3;
+__host__ __device__ constexpr bool has_contact(int mode) { return mode == kContact || mode == kContact0; }
 
 struct __align__(16) JPair {  // two list particles relative to the origin (hi/lo)
     float2 x, y, z, m, xl, yl, zl, pad;
@@ -114,6 +115,11 @@ struct Args {
     float floor2;   // r_coll^2 + eps^2 (or eps^2)
     float rc2chk;   // r^2 below this (FP32) may be a contact: r_coll^2 (1 + 1e-5)
     bool add_central;
+    // schedule: warps take list slots slot0, slot0 + stride, ... (grid or
+    // persistent static), or draw them from *ticket (persistent dynamic)
+    int chunk;                     // largest i-chunk (32, 64 or 96 particles)
+    unsigned long long* ticket;    // NULL: static
+    unsigned long long* warp_time; // optional: per warp (start, end) %globaltimer
 };
 
 __device__ __forceinline__ float rel(float hi, float lo, float ohi, float olo) {
@@ -229,6 +235,9 @@ __device__ __forceinline__ bool pp_body(const Args& A, const JPair& P, const uin
     float2 s2;
     if (MODE == kMask) {
         s2 = r2;
+    } else if (MODE == kContact0) {
+        s2.x = fmaxf(r2.x, A.floor2);
+        s2.y = fmaxf(r2.y, A.floor2);
     } else {
         s2.x = fmaxf(r2.x + A.fp.eps2f, A.floor2);
         s2.y = fmaxf(r2.y + A.fp.eps2f, A.floor2);
@@ -242,7 +251,7 @@ __device__ __forceinline__ bool pp_body(const Args& A, const JPair& P, const uin
     g[0] = __ffma2_rn(f, dx, g[0]);
     g[1] = __ffma2_rn(f, dy, g[1]);
     g[2] = __ffma2_rn(f, dz, g[2]);
-    if (MODE != kContact) return false;
+    if (!has_contact(MODE)) return false;
     if (SELF) return (r2.x < A.rc2chk && jid[0] != i) || (r2.y < A.rc2chk && jid[1] != i);
     return r2.x < A.rc2chk || r2.y < A.rc2chk;
 }
@@ -413,12 +422,12 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             bool any = false;
 #pragma unroll
             for (int r = 0; r < R; ++r) any |= pp_body<MODE, SELF>(A, P, jid, K.iv[r], K.nh[r], K.nl[r], K.g[r]);
-            if (MODE == kContact && __any_sync(0xffffffffu, any)) {
+            if (has_contact(MODE) && __any_sync(0xffffffffu, any)) {
                 if (lane == 0) S.trig[ntrig] = (uint8_t)q;
                 ++ntrig;
             }
         }
-        if (MODE == kContact) {
+        if (has_contact(MODE)) {
             __syncwarp();
 #pragma unroll 1
             for (int t = 0; t < ntrig; ++t) {
@@ -437,12 +446,12 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             bool any = false;
             if (q < npair)
                 any = pp_body<MODE, SELF>(A, S.t.p.jp[q], &S.t.p.jid[2 * q], K.iv[R], K.nh[R], K.nl[R], K.g[R]);
-            if (MODE == kContact && __any_sync(0xffffffffu, any)) {
+            if (has_contact(MODE) && __any_sync(0xffffffffu, any)) {
                 if (lane == 0) S.trig[ntrig] = (uint8_t)u;
                 ++ntrig;
             }
         }
-        if (MODE == kContact) {
+        if (has_contact(MODE)) {
             __syncwarp();
 #pragma unroll 1
             for (int t = 0; t < ntrig; ++t) {
@@ -568,7 +577,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
         cp_async_wait_all();
         __syncwarp();
     }
-    if (MODE == kContact && qn > 0) flush_queue(A, S, qn, lane);
+    if (has_contact(MODE) && qn > 0) flush_queue(A, S, qn, lane);
     // (3) list cells: data gathered one tile ahead, indices two
     {
         const int64_t c0 = A.pc_off[k], c1 = A.pc_off[k + 1];
@@ -627,23 +636,24 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     __syncwarp();
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One group (list slot) for one warp.
 template <int ORDER, int MODE>
-__global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem32* sm = reinterpret_cast<Smem32*>(smem_raw);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t slot = (int64_t)blockIdx.x * kW32 + w;
-    if (slot >= A.ng) return;
+__device__ __forceinline__ void force_group(const Args& A, Smem32& S, int64_t slot, int lane) {
     const int64_t k = A.order ? A.order[slot] : slot;  // groups of one size class run side by side
-    Smem32& S = sm[w];
     const int32_t g = A.groups[k];
     const uint32_t b = A.begin[g], e = A.end[g];
     // origin: the group node's centre of mass as an FP32 hi/lo pair
     const float4 o0 = A.cell32[3 * (int64_t)g], o1 = A.cell32[3 * (int64_t)g + 1];
     const float oh[3] = {o0.x, o0.y, o0.z}, ol[3] = {o1.x, o1.y, o1.z};
-    // chunks of at most 96 particles: R full slots plus a tail of at most 16
+    // chunks of at most A.chunk particles: R full slots plus a tail of at most 16
     for (uint32_t i0 = b; i0 < e;) {
-        const uint32_t rem = e - i0, cnt = min(rem, 96u);
+        const uint32_t rem = e - i0, cnt = min(rem, (uint32_t)A.chunk);
         int R = (int)(cnt >> 5), t = (int)(cnt & 31), T = 0;
         if (t > 16) {
             ++R;  // more than half a slot left: a full one
@@ -669,10 +679,37 @@ __global__ void __launch_bounds__(32 * kW32, BH_F32_MINB) k_force32(const Args A
     }
 }
 
+// Warps per block = blockDim.x / 32 (at most BH_F32_MAXW); one Smem32 per warp.
+template <int ORDER, int MODE>
+__global__ void __launch_bounds__(32 * BH_F32_MAXW, 2) k_force32(const Args A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem32* sm = reinterpret_cast<Smem32*>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t wid = (int64_t)blockIdx.x * nw + w;
+    Smem32& S = sm[w];
+    const unsigned long long t0 = A.warp_time ? global_ns() : 0ull;
+    if (A.ticket) {  // persistent, dynamic: the next list slot from the shared counter
+        for (;;) {
+            unsigned long long s = 0;
+            if (lane == 0) s = atomicAdd(A.ticket, 1ull);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            if ((int64_t)s >= A.ng) break;
+            force_group<ORDER, MODE>(A, S, (int64_t)s, lane);
+        }
+    } else {  // static: one slot per warp (grid) or every stride-th slot (persistent)
+        const int64_t stride = (int64_t)gridDim.x * nw;
+        for (int64_t s = wid; s < A.ng; s += stride) force_group<ORDER, MODE>(A, S, s, lane);
+    }
+    if (A.warp_time && lane == 0) {
+        A.warp_time[2 * wid] = t0;
+        A.warp_time[2 * wid + 1] = global_ns();
+    }
+}
+
 // Size class of a group = the (R, tail) variant of its last chunk; classes
 // are numbered so that larger work comes first.
-__device__ __forceinline__ int size_class(uint32_t n_i) {
-    const uint32_t rem = n_i - 96u * ((n_i - 1u) / 96u);
+__device__ __forceinline__ int size_class(uint32_t n_i, uint32_t chunk) {
+    const uint32_t rem = n_i - chunk * ((n_i - 1u) / chunk);
     int R = (int)(rem >> 5);
     const int t = (int)(rem & 31);
     bool tail = false;
@@ -684,69 +721,205 @@ __device__ __forceinline__ int size_class(uint32_t n_i) {
     return 5 - cls;
 }
 
+// Processing order: size class first (warps side by side run the same code),
+// then, with cost ordering on, largest estimated cost first within a class
+// (cost = n_i (n_i + list particles + 2 list cells), bucketed by log2), so the
+// list ends with the cheapest groups of each class.
+constexpr int kCostBuckets = 32;
+constexpr int kOrderBuckets = 6 * kCostBuckets;
+
+__device__ __forceinline__ int order_bucket(int64_t k, const int32_t* __restrict__ groups,
+                                            const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end,
+                                            const int64_t* __restrict__ jj_off, const int64_t* __restrict__ pc_off,
+                                            uint32_t chunk, bool by_cost) {
+    const int32_t g = groups[k];
+    const uint32_t ni = end[g] - begin[g];
+    int cb = 0;
+    if (by_cost) {
+        const unsigned long long cost =
+            (unsigned long long)ni * ((unsigned long long)ni + (unsigned long long)(jj_off[k + 1] - jj_off[k]) +
+                                      2ull * (unsigned long long)(pc_off[k + 1] - pc_off[k]));
+        const int lg = cost ? 63 - __clzll((long long)cost) : 0;
+        cb = kCostBuckets - 1 - min(lg, kCostBuckets - 1);
+    }
+    return size_class(ni, chunk) * kCostBuckets + cb;
+}
+
 __global__ void k_order_hist(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
-                             const uint32_t* __restrict__ end, unsigned long long* cnt) {
+                             const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
+                             const int64_t* __restrict__ pc_off, uint32_t chunk, bool by_cost,
+                             unsigned long long* cnt) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ng) return;
-    const int32_t g = groups[k];
-    atomicAdd(&cnt[size_class(end[g] - begin[g])], 1ull);
+    atomicAdd(&cnt[order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost)], 1ull);
+}
+
+// exclusive prefix of the bucket counts (one block of kOrderBuckets threads)
+__global__ void k_order_prefix(unsigned long long* cnt) {
+    __shared__ unsigned long long v[kOrderBuckets];
+    v[threadIdx.x] = cnt[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            const unsigned long long t = v[b];
+            v[b] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    cnt[threadIdx.x] = v[threadIdx.x];
 }
 
 __global__ void k_order_scatter(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
-                                const uint32_t* __restrict__ end, const unsigned long long* __restrict__ cnt,
-                                unsigned long long* cursor, int32_t* __restrict__ order) {
+                                const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
+                                const int64_t* __restrict__ pc_off, uint32_t chunk, bool by_cost,
+                                const unsigned long long* __restrict__ start, unsigned long long* cursor,
+                                int32_t* __restrict__ order) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ng) return;
-    const int32_t g = groups[k];
-    const int cls = size_class(end[g] - begin[g]);
-    unsigned long long off = 0;
-    for (int c = 0; c < cls; ++c) off += cnt[c];
-    order[off + atomicAdd(&cursor[cls], 1ull)] = (int32_t)k;
+    const int b = order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost);
+    order[start[b] + atomicAdd(&cursor[b], 1ull)] = (int32_t)k;
 }
 
 // FP64 pass over the contact candidates: Eq. (1) in the oracle's operation
 // order less the gravity the FP32 kernel already added for the pair (r_coll
 // or r clamp), i.e. the spring and dashpot term when r <= r_coll.
+//
+// The candidates arrive in no fixed order (warps append them as they go), so
+// the terms are summed per particle in 64-bit fixed point (units of 2^-50,
+// terms below 2^10 in magnitude): integer addition does not depend on the
+// order, which keeps every run bit-reproducible.  Three passes: clear the
+// accumulators of the particles involved, add the terms, then move each
+// particle's sum into its acceleration (the first pass to take it adds the
+// whole sum, every later one adds zero).
+constexpr double kFix = 1125899906842624.0;  // 2^50
+constexpr double kFixMax = 1024.0;
+
+__device__ __forceinline__ int64_t contact_count(const unsigned long long* count, int64_t cap, int* status,
+                                                 bool flag) {
+    int64_t np = (int64_t)*count;
+    if (np > cap) {
+        np = cap;
+        if (flag && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatListOverflow);
+    }
+    return np;
+}
+
+__global__ void k_contacts_clear(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
+                                 int64_t cap, unsigned long long* __restrict__ acc, int* status) {
+    const int64_t np = contact_count(count, cap, status, true);
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = pairs[u].x;
+        acc[3 * (int64_t)i] = acc[3 * (int64_t)i + 1] = acc[3 * (int64_t)i + 2] = 0ull;
+    }
+}
+
 __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
                              int64_t cap, ForceParams fp, const double* __restrict__ x,
                              const double* __restrict__ y, const double* __restrict__ z,
                              const double* __restrict__ vx, const double* __restrict__ vy,
-                             const double* __restrict__ vz, const double* __restrict__ m, double* ax, double* ay,
-                             double* az) {
-    int64_t np = (int64_t)*count;
-    if (np > cap) np = cap;
+                             const double* __restrict__ vz, const double* __restrict__ m,
+                             unsigned long long* __restrict__ acc, int* status) {
+    const int64_t np = contact_count(count, cap, status, false);
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
         const uint2 pr = pairs[u];
         const uint32_t i = pr.x, j = pr.y;
         double a[3] = {0.0, 0.0, 0.0};
         contact_term64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j], vz[j], m[j], a);
-        atomicAdd(&ax[i], a[0]);
-        atomicAdd(&ay[i], a[1]);
-        atomicAdd(&az[i], a[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = a[c];
+            if (!(fabs(v) < kFixMax)) {  // outside the fixed-point range (or not finite)
+                atomicOr(status, kStatRange);
+                v = 0.0;
+            }
+            atomicAdd(&acc[3 * (int64_t)i + c], (unsigned long long)__double2ll_rn(v * kFix));
+        }
     }
 }
 
-template <int ORDER, int MODE>
-void set_smem_attr(int smem) {
-    cudaFuncSetAttribute(k_force32<ORDER, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+__global__ void k_contacts_apply(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
+                                 int64_t cap, unsigned long long* __restrict__ acc, double* ax, double* ay,
+                                 double* az, int* status) {
+    const int64_t np = contact_count(count, cap, status, false);
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = pairs[u].x;
+        double* out[3] = {ax, ay, az};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long v = (long long)atomicExch(&acc[3 * (int64_t)i + c], 0ull);
+            if (v != 0) atomicAdd(&out[c][i], (double)v / kFix);
+        }
+    }
+}
+
+using Force32Fn = void (*)(const Args);
+
+Force32Fn force32_kernel(int order, int mode) {
+    if (order >= 2) {
+        switch (mode) {
+            case kContact: return k_force32<2, kContact>;
+            case kPlain: return k_force32<2, kPlain>;
+            case kMask: return k_force32<2, kMask>;
+            default: return k_force32<2, kContact0>;
+        }
+    }
+    switch (mode) {
+        case kContact: return k_force32<1, kContact>;
+        case kPlain: return k_force32<1, kPlain>;
+        case kMask: return k_force32<1, kMask>;
+        default: return k_force32<1, kContact0>;
+    }
+}
+
+int resident_blocks(Force32Fn kern, int warps) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * warps, warps * (int)sizeof(Smem32)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 }  // namespace
 
-// Processing order of the groups for the FP32 kernel (once per list build):
-// by size class, so that warps running side by side execute the same code.
+// Processing order of the groups for the FP32 kernel (once per list build).
 int build_order32(Ctx* c) {
     const int64_t ng = c->n_groups;
     BH_TRY(grow(c, c->order, (size_t)ng + 1, "group order"));
-    unsigned long long* cnt = c->d_small + 24;  // 6 counters + 6 cursors
-    BH_CUDA(c, cudaMemsetAsync(cnt, 0, 12 * sizeof(unsigned long long), c->stream));
-    k_order_hist<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, cnt);
+    BH_TRY(grow(c, c->order_cnt, 2 * (size_t)kOrderBuckets, "group order buckets"));
+    unsigned long long* cnt = c->order_cnt.p;
+    const uint32_t chunk = (uint32_t)c->tune.chunk;
+    const bool by_cost = c->tune.order_by_cost != 0;
+    BH_CUDA(c, cudaMemsetAsync(cnt, 0, 2 * kOrderBuckets * sizeof(unsigned long long), c->stream));
+    k_order_hist<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
+                                                             c->cnt_c.p, chunk, by_cost, cnt);
     BH_LAUNCH(c);
-    k_order_scatter<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, cnt, cnt + 6,
-                                                                c->order.p);
+    k_order_prefix<<<1, kOrderBuckets, 0, c->stream>>>(cnt);
+    BH_LAUNCH(c);
+    k_order_scatter<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
+                                                                c->cnt_c.p, chunk, by_cost, cnt,
+                                                                cnt + kOrderBuckets, c->order.p);
     BH_LAUNCH(c);
     return BH_OK;
 }
+
+namespace {
+int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, unsigned nb) {
+    unsigned long long* acc = c->contact_acc.p;
+    k_contacts_clear<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, c->d_status);
+    BH_LAUNCH(c);
+    k_contacts64<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, fp, p->x, p->y, p->z, p->vx, p->vy,
+                                            p->vz, p->m, acc, c->d_status);
+    BH_LAUNCH(c);
+    k_contacts_apply<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, p->ax, p->ay, p->az,
+                                                c->d_status);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+}  // namespace
 
 int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_central) {
     Args A;
@@ -771,6 +944,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     const bool contact = c->prm.r_coll > 0.0;
     const int64_t cap = c->n > 65536 ? c->n : 65536;
     if (contact && c->contacts.cap < (size_t)cap) BH_TRY(grow(c, c->contacts, (size_t)cap, "contact pairs"));
+    if (contact) BH_TRY(grow(c, c->contact_acc, 3 * (size_t)c->n, "contact sums"));
     A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
     A.contact_cap = (int64_t)c->contacts.cap;
     A.ncontact = c->d_small + 16;
@@ -782,31 +956,51 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.floor2 = (float)(fp.rc2 + fp.eps2);
     A.rc2chk = (float)(fp.rc2 * (1.0 + 1e-5));
     A.add_central = add_central;
-    const int mode = contact ? kContact : (A.floor2 > 0.f ? kPlain : kMask);
-    const unsigned nb = blocks_for(A.ng, kW32);
-    const int smem = (int)(kW32 * sizeof(Smem32));
-    static bool attr = false;
-    if (!attr) {
-        set_smem_attr<1, kContact>(smem);
-        set_smem_attr<1, kPlain>(smem);
-        set_smem_attr<1, kMask>(smem);
-        set_smem_attr<2, kContact>(smem);
-        set_smem_attr<2, kPlain>(smem);
-        set_smem_attr<2, kMask>(smem);
-        attr = true;
+    const int mode = contact ? (fp.eps2f == 0.f ? kContact0 : kContact) : (A.floor2 > 0.f ? kPlain : kMask);
+    const Force32Fn kern = force32_kernel(c->prm.order, mode);
+    const int W = c->tune.warps;
+    const int smem = (int)(W * sizeof(Smem32));
+    if (c->f32_attr_device != c->device) {  // once per device: room for the largest block
+        const int smax = (int)(BH_F32_MAXW * sizeof(Smem32));
+        for (int o = 1; o <= 2; ++o)
+            for (int m = 0; m < 4; ++m)
+                BH_CUDA(c, cudaFuncSetAttribute(force32_kernel(o, m), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                smax));
+        c->f32_attr_device = c->device;
     }
+    A.chunk = c->tune.chunk;
+    A.ticket = nullptr;
+    A.warp_time = nullptr;
+    unsigned nb;
+    if (c->tune.sched == BH_SCHED_GRID) {
+        nb = blocks_for(A.ng, W);
+    } else {
+        nb = (unsigned)(c->num_sms * resident_blocks(kern, W));
+        const int64_t need = (A.ng + W - 1) / W;
+        if ((int64_t)nb > need) nb = (unsigned)(need > 0 ? need : 1);
+        if (c->tune.sched == BH_SCHED_DYNAMIC) {
+            A.ticket = c->d_small + 17;
+            BH_CUDA(c, cudaMemsetAsync(A.ticket, 0, sizeof(unsigned long long), c->stream));
+        }
+        if (c->timing && !c->capturing) {
+            BH_TRY(grow(c, c->warp_time, 2 * (size_t)nb * W, "warp times"));
+            A.warp_time = c->warp_time.p;
+            c->warp_time_n = (int64_t)nb * W;
+        }
+    }
+    c->f32_blocks = nb;
     for (int attempt = 0; attempt < 2; ++attempt) {
         BH_TRY(timing_begin(c));
-#define BH_K32(O, M) k_force32<O, M><<<nb, 32 * kW32, smem, c->stream>>>(A)
-        if (c->prm.order >= 2) {
-            if (mode == kContact) BH_K32(2, kContact); else if (mode == kPlain) BH_K32(2, kPlain); else BH_K32(2, kMask);
-        } else {
-            if (mode == kContact) BH_K32(1, kContact); else if (mode == kPlain) BH_K32(1, kPlain); else BH_K32(1, kMask);
-        }
-#undef BH_K32
+        kern<<<nb, 32 * W, smem, c->stream>>>(A);
         BH_LAUNCH(c);
         BH_TRY(timing_end(c));
         if (!contact) break;
+        if (c->capturing) {
+            // inside a captured graph: no read-back; the pass takes the count
+            // from the device and flags an overflow in the status word
+            BH_TRY(contact_pass(c, A, fp, p, (unsigned)(c->num_sms * 4)));
+            break;
+        }
         // size the FP64 contact pass (one read-back per evaluation); on overflow
         // grow the list and evaluate again
         unsigned long long np = 0;
@@ -818,14 +1012,10 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
             A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
             A.contact_cap = (int64_t)c->contacts.cap;
             BH_CUDA(c, cudaMemsetAsync(A.ncontact, 0, sizeof(unsigned long long), c->stream));
+            if (A.ticket) BH_CUDA(c, cudaMemsetAsync(A.ticket, 0, sizeof(unsigned long long), c->stream));
             continue;
         }
-        if (np > 0) {
-            k_contacts64<<<blocks_for((int64_t)np, 128), 128, 0, c->stream>>>(
-                A.contacts, A.ncontact, A.contact_cap, fp, p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->ax,
-                p->ay, p->az);
-            BH_LAUNCH(c);
-        }
+        if (np > 0) BH_TRY(contact_pass(c, A, fp, p, blocks_for((int64_t)np, 128)));
         break;
     }
     return BH_OK;
