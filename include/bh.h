@@ -209,21 +209,44 @@ typedef struct {
                           build; the contact pass then reads its count on the
                           device, and an overflow of its buffer is reported
                           (BH_E_LIST_OVERFLOW) at the next synchronising call */
+    int order_window;  /* 0: one global size-class order; w > 0: the size-class
+                          order is applied within windows of w consecutive
+                          groups (list order = Morton order), so the warps in
+                          flight work on nearby groups whose list data share L2 */
 } bh_tuning;
 /* Errors: BH_E_INVAL for a value out of range (n_g < n_leaf included). */
 int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t);
 int bh_get_tuning(bh_ctx* ctx, bh_tuning* t);
 
 /* Autotuner: times candidate settings on the caller's particles and keeps
- * the fastest.  First the launch settings (chunk x warps x schedule) on the
- * current n_g, by force-kernel time; then n_g in {64, 96, 128, 192, 256}
- * (those >= n_leaf) by the cost of one step, force time plus list-build time
- * / rebuild_every.  Like a list build it reorders the particle arrays; on
+ * the fastest.  First the launch settings on the current n_g by force-kernel
+ * time, one knob at a time (schedule, then warps in {2, 4, 8}, chunk in
+ * {32, 64, 96}, order_window in {0, 2048, 8192}); then n_g in
+ * {64, 96, 128, 192, 256} (those >= n_leaf) by the cost of one step, force
+ * time plus list-build time / rebuild_every.  Like a list build it reorders the particle arrays; on
  * return the lists are built with the chosen settings, ax..az hold the
  * acceleration at the current positions, and the list-reuse schedule starts
  * afresh.  best_ms (may be NULL) receives the chosen setting's step cost.
  * Synchronises.  graph is left as set. */
 int bh_autotune(bh_ctx* ctx, bh_particles* p, double* best_ms);
+
+/* Diagnostics of the current state (the energy, momentum and collision
+ * statistics a ring simulation reports alongside its steps).  Sums over all
+ * particles of p (all patches), in FP64 with a fixed reduction order, so
+ * repeated calls on the same state give identical bits:
+ *   mass = sum m;  momentum = sum m v;  angular_momentum = sum m x cross v
+ *   (about the origin);  kinetic = sum m |v|^2 / 2;  potential_central =
+ *   -sum G M_central m / |x|.
+ * Self-gravity potential energy is not computed (the force kernels produce
+ * accelerations only).  Contact statistics of the last FP32 force evaluation
+ * (-1 on the FP64 path or without contacts, whose kernel evaluates contacts
+ * inline): contact_candidates = (i, j) pairs that went to the FP64 contact
+ * pass, contacts = unordered pairs found with r <= r_coll.  Synchronises. */
+typedef struct {
+    double mass, momentum[3], angular_momentum[3], kinetic, potential_central;
+    int64_t contact_candidates, contacts;
+} bh_diagnostics;
+int bh_get_diagnostics(bh_ctx* ctx, const bh_particles* p, bh_diagnostics* out);
 
 /* Load balance of the last persistent force launch made with timing on
  * (bh_set_timing): busy fraction = sum over warps of (finish - start) /

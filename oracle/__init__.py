@@ -320,3 +320,32 @@ def step(P: dict, prm: Params, nsteps: int):
             Q["v" + c] = Q["v" + c] + (0.5 * dt) * a[:, "xyz".index(c)]
         k += 1
     return S, a, k
+
+# --------------------------------------------------------------------------
+# Diagnostics: the plain definitions of the conserved sums
+# --------------------------------------------------------------------------
+def diagnostics(P: dict, G: float, M_central: float) -> dict:
+    """Mass, momentum sum m v, angular momentum sum m x cross v (about the
+    origin), kinetic energy sum m |v|^2 / 2 and central-mass potential energy
+    -sum G M_c m / |x|, in FP64 (numpy sums)."""
+    m = P["m"]
+    x = np.stack([P["x"], P["y"], P["z"]], 1)
+    v = np.stack([P["vx"], P["vy"], P["vz"]], 1)
+    r = np.linalg.norm(x, axis=1)
+    return {"mass": float(m.sum()), "momentum": (m[:, None] * v).sum(0),
+            "angular_momentum": (m[:, None] * np.cross(x, v)).sum(0),
+            "kinetic": float(0.5 * (m * (v * v).sum(1)).sum()),
+            "potential_central": float(np.where(r > 0, -G * M_central * m / np.where(r > 0, r, 1.0), 0.0).sum())}
+
+
+def contact_pairs(P: dict, r_coll: float) -> int:
+    """Unordered pairs with 0 < r <= r_coll, by brute force over all pairs."""
+    x = np.stack([P["x"], P["y"], P["z"]], 1)
+    n, cnt = len(x), 0
+    for i0 in range(0, n, 1024):
+        d = x[i0:i0 + 1024, None, :] - x[None, :, :]
+        r2 = (d * d).sum(2)
+        ii = np.arange(i0, min(n, i0 + 1024))[:, None]
+        jj = np.arange(n)[None, :]
+        cnt += int(((r2 > 0) & (r2 <= r_coll * r_coll) & (jj > ii)).sum())
+    return cnt

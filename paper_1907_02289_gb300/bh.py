@@ -22,7 +22,7 @@ SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_se
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
            "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_set_tuning", "bh_get_tuning", "bh_autotune",
-           "bh_get_balance", "bh_sort_keys_static")
+           "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static")
 BH_SCHED_GRID, BH_SCHED_STATIC, BH_SCHED_DYNAMIC = 0, 1, 2
 BH_SORT_STATIC_MAX_N = 4194304
 
@@ -46,8 +46,15 @@ class bh_counters(ctypes.Structure):
                                                "n_contacts")]
 
 
+class bh_diagnostics(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3),
+                ("angular_momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
+                ("potential_central", ctypes.c_double), ("contact_candidates", ctypes.c_int64),
+                ("contacts", ctypes.c_int64)]
+
+
 class bh_tuning(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph")]
+    _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph", "order_window")]
 
 
 _lib = None
@@ -95,6 +102,7 @@ def load(path: str = LIB_PATH):
     lib.bh_get_tuning.argtypes = [P, ctypes.POINTER(bh_tuning)]
     lib.bh_autotune.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_balance.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.bh_get_diagnostics.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.POINTER(bh_diagnostics)]
     lib.bh_sort_keys_static.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_char_p, ctypes.c_size_t]
     _lib = lib
     return lib
@@ -312,6 +320,13 @@ class Context:
         ms = ctypes.c_double()
         self._chk(self.lib.bh_autotune(self.h, ctypes.byref(P.struct), ctypes.byref(ms)))
         return ms.value
+
+    def bh_get_diagnostics(self, P: "Particles"):
+        d = bh_diagnostics()
+        self._chk(self.lib.bh_get_diagnostics(self.h, ctypes.byref(P.struct), ctypes.byref(d)))
+        return {"mass": d.mass, "momentum": np.array(d.momentum[:]), "angular_momentum": np.array(d.angular_momentum[:]),
+                "kinetic": d.kinetic, "potential_central": d.potential_central,
+                "contact_candidates": d.contact_candidates, "contacts": d.contacts}
 
     def bh_get_balance(self):
         b = ctypes.c_double()

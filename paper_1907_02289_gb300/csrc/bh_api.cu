@@ -265,6 +265,7 @@ int check_tuning(Ctx* c, const bh_tuning* t) {
     if (t->sched < BH_SCHED_GRID || t->sched > BH_SCHED_DYNAMIC) return fail(c, BH_E_INVAL, "unknown schedule");
     if ((t->order_by_cost != 0 && t->order_by_cost != 1) || (t->graph != 0 && t->graph != 1))
         return fail(c, BH_E_INVAL, "order_by_cost and graph must be 0 or 1");
+    if (t->order_window < 0) return fail(c, BH_E_INVAL, "order_window must be >= 0");
     return BH_OK;
 }
 
@@ -277,6 +278,7 @@ void apply_tuning(Ctx* c, const bh_tuning* t) {
     c->tune.sched = t->sched;
     c->tune.order_by_cost = t->order_by_cost;
     c->tune.graph = t->graph;
+    c->tune.order_window = t->order_window;
     c->graph_ok = false;
     (void)relist;
 }
@@ -288,6 +290,7 @@ void read_tuning(const Ctx* c, bh_tuning* t) {
     t->sched = c->tune.sched;
     t->order_by_cost = c->tune.order_by_cost;
     t->graph = c->tune.graph;
+    t->order_window = c->tune.order_window;
 }
 
 // Elapsed device time of fn() on the context's stream (ms).
@@ -333,33 +336,50 @@ int autotune(Ctx* c, bh_particles* p, double* best_ms) {
         BH_TRY(stage_moments(c, p));
         return stage_force(c, p, false);
     };
-    // (1) launch settings on the current n_g, by force-evaluation time
+    // (1) launch settings on the current n_g, by force-evaluation time, one
+    // knob at a time: schedule, warps per block, i-chunk, order window
     BH_TRY(time_ms(c, build, &tb));
     double best_f = 1e300;
     bh_tuning best = cur;
-    const int chunks[3] = {32, 64, 96}, warps[3] = {2, 4, 8};
-    for (int ci = 0; ci < 3; ++ci) {
-        bh_tuning t = cur;
-        t.chunk = chunks[ci];
+    auto try_force = [&](const bh_tuning& t) -> int {
+        const bool reorder = t.chunk != c->tune.chunk || t.order_window != c->tune.order_window;
         apply_tuning(c, &t);
-        if (c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
-        for (int wi = 0; wi < 3; ++wi)
-            for (int sc = BH_SCHED_GRID; sc <= BH_SCHED_DYNAMIC; ++sc) {
-                t.warps = warps[wi];
-                t.sched = sc;
-                apply_tuning(c, &t);
-                double ms = 0.0, ms2 = 0.0;
-                BH_TRY(time_ms(c, force, &ms));
-                BH_TRY(time_ms(c, force, &ms2));
-                if (ms2 < ms) ms = ms2;
-                if (ms < best_f) {
-                    best_f = ms;
-                    best = t;
-                }
-                if (c->prm.precision != BH_PREC_FP32) goto done_launch;  // the FP64 kernel has no such settings
-            }
+        if (reorder && c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
+        double ms = 0.0, ms2 = 0.0;
+        BH_TRY(time_ms(c, force, &ms));
+        BH_TRY(time_ms(c, force, &ms2));
+        if (ms2 < ms) ms = ms2;
+        if (ms < best_f) {
+            best_f = ms;
+            best = t;
+        }
+        return BH_OK;
+    };
+    if (c->prm.precision == BH_PREC_FP32) {
+        for (int sc = BH_SCHED_GRID; sc <= BH_SCHED_DYNAMIC; ++sc) {
+            bh_tuning t = best;
+            t.sched = sc;
+            BH_TRY(try_force(t));
+        }
+        const int warps[3] = {2, 4, 8}, chunks[3] = {32, 64, 96}, windows[3] = {0, 2048, 8192};
+        for (int q = 0; q < 3; ++q) {
+            bh_tuning t = best;
+            t.warps = warps[q];
+            BH_TRY(try_force(t));
+        }
+        for (int q = 0; q < 3; ++q) {
+            bh_tuning t = best;
+            t.chunk = chunks[q];
+            BH_TRY(try_force(t));
+        }
+        for (int q = 0; q < 3; ++q) {
+            bh_tuning t = best;
+            t.order_window = windows[q];
+            BH_TRY(try_force(t));
+        }
+    } else {
+        BH_TRY(try_force(best));  // the FP64 kernel has no launch settings
     }
-done_launch:
     // (2) n_g by the cost of a step: force time + list-build time / rebuild_every
     {
         double best_step = 1e300;
@@ -475,7 +495,12 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->order_cnt); release(c->warp_time); release(c->contact_acc);
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
+    for (int b = 0; b < 2; ++b) {
+        release(c->ord_key[b]);
+        release(c->ord_idx[b]);
+    }
+    release(c->ord_scratch);
     for (int b = 0; b < 2; ++b) {
         release(c->key[b]);
         release(c->idx[b]);
@@ -560,7 +585,8 @@ int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t) {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BH_E_INVAL;
     BH_TRY(bh::check_tuning(c, t));
-    const bool reorder = t->chunk != c->tune.chunk || t->order_by_cost != c->tune.order_by_cost;
+    const bool reorder = t->chunk != c->tune.chunk || t->order_by_cost != c->tune.order_by_cost ||
+                         t->order_window != c->tune.order_window;
     bh::apply_tuning(c, t);
     if (reorder && c->have_lists && c->prm.precision == BH_PREC_FP32) BH_TRY(bh::build_order32(c));
     return BH_OK;
@@ -577,6 +603,31 @@ int bh_autotune(bh_ctx* ctx, bh_particles* p, double* best_ms) {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BH_E_INVAL;
     return bh::autotune(c, p, best_ms);
+}
+
+int bh_get_diagnostics(bh_ctx* ctx, const bh_particles* p, bh_diagnostics* out) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !out) return BH_E_INVAL;
+    BH_TRY(bh::check_particles(c, p, true));
+    double s[11];
+    BH_TRY(bh::stage_diagnostics(c, p, s));
+    out->mass = s[0];
+    for (int a = 0; a < 3; ++a) {
+        out->momentum[a] = s[1 + a];
+        out->angular_momentum[a] = s[4 + a];
+    }
+    out->kinetic = s[7];
+    out->potential_central = s[8];
+    out->contact_candidates = -1;
+    out->contacts = -1;
+    if (c->contact_stats) {
+        unsigned long long h[3];
+        BH_CUDA(c, cudaMemcpyAsync(h, c->d_small + 16, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        out->contact_candidates = (int64_t)h[0];
+        out->contacts = (int64_t)(h[2] / 2);
+    }
+    return bh::read_status(c);
 }
 
 int bh_get_balance(bh_ctx* ctx, double* busy_fraction) {

@@ -53,9 +53,10 @@ struct WalkNode {
 struct Tuning {
     int chunk = 96;          // largest i-chunk per warp pass: 32, 64 or 96 particles
     int warps = 4;           // warps per block, 1..8
-    int sched = BH_SCHED_GRID;
+    int sched = BH_SCHED_DYNAMIC;
     int order_by_cost = 1;   // within a size class, largest estimated cost first
     int graph = 0;           // capture list-reusing steps of bh_step in a CUDA graph
+    int order_window = 0;    // > 0: size-class order within windows of this many groups
 };
 
 struct Ctx {
@@ -118,8 +119,10 @@ struct Ctx {
     DBuf<float4> cell32;             // 3 per node: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz)
     DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
     DBuf<unsigned long long> contacts;  // (i, j) contact candidates for the FP64 pass
+    DBuf<double> diag;                   // diagnostic partial sums
     DBuf<unsigned long long> contact_acc;  // per particle fixed-point contact sums (3 per particle)
     int64_t n_contacts = 0;
+    bool contact_stats = false;         // the device contact counters hold an FP32 evaluation's counts
 
     // groups
     int64_t n_groups = 0;
@@ -128,6 +131,10 @@ struct Ctx {
     DBuf<int32_t> groups;            // node ids ordered by begin
     DBuf<int32_t> order;             // force-kernel processing order of groups
     DBuf<unsigned long long> order_cnt;  // order buckets: counts/starts and cursors
+    DBuf<uint64_t> ord_key[2];           // windowed order: sort keys
+    DBuf<uint32_t> ord_idx[2];
+    DBuf<uint32_t> ord_scratch;
+    int sort_attr_device = -1;           // device the sort kernel's smem limit was raised on
     int f32_attr_device = -1;            // device the FP32 kernels' smem limit was raised on
     unsigned f32_blocks = 0;             // grid of the last FP32 force launch
     DBuf<unsigned long long> warp_time;  // per warp (start, end) of the last persistent launch
@@ -219,5 +226,6 @@ int timing_end(Ctx* c);
 // update.cu
 int stage_kick(Ctx* c, bh_particles* p, double h);
 int stage_kick_drift(Ctx* c, bh_particles* p, double h, double dt);
+int stage_diagnostics(Ctx* c, const bh_particles* p, double* host_out);  // 11 sums to the host
 
 }  // namespace bh

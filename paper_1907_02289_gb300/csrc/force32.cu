@@ -35,6 +35,7 @@
 // size class so that warps running side by side execute the same code.  The
 // group's own particles are evaluated first in a phase that excludes i = j;
 // the expanded list holds only the other particles.
+#include <algorithm>
 #include <cmath>
 
 #include "force_common.cuh"
@@ -45,12 +46,22 @@ namespace {
 #ifndef BH_F32_MAXW
 #define BH_F32_MAXW 8  // most warps per block (the register budget is sized for 2 such blocks per SM)
 #endif
+#ifndef BH_F32_UNROLL
+#define BH_F32_UNROLL 1  // list pairs per iteration of the particle loop
+#endif
+#ifndef BH_F32_PCUNROLL
+#define BH_F32_PCUNROLL 1  // list pairs per iteration of the cell loop
+#endif
+#ifndef BH_F32_MAXR
+#define BH_F32_MAXR 3  // most full i-slots per lane (chunks of up to 32 x this particles)
+#endif
 #ifndef BH_F32_TILE
 #define BH_F32_TILE 1  // list particles per tile = 64 x this, list cells = 32 x this
 #endif
 constexpr int kTileJ = 64 * BH_F32_TILE;  // list particles per tile (2 per lane per 64)
 constexpr int kTileC = 32 * BH_F32_TILE;  // list cells per tile (1 per lane per 32)
 constexpr int kSlots = 3;                 // i-slots per lane (full slots + tail)
+constexpr int kUnrollPP = BH_F32_UNROLL, kUnrollPC = BH_F32_PCUNROLL;
 constexpr int kQueueCap = 32 + 2 * kSlots * 32;
 constexpr uint32_t kNone = 0xffffffffu;
 
@@ -415,7 +426,7 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
                                         int& qn, int lane) {
     if constexpr (R > 0) {
         int ntrig = 0;
-#pragma unroll 1
+#pragma unroll kUnrollPP
         for (int q = 0; q < npair; ++q) {
             const JPair P = S.t.p.jp[q];
             const uint32_t* jid = &S.t.p.jid[2 * q];
@@ -469,7 +480,7 @@ template <int R, bool TAIL, int ORDER>
 __device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj) {
     const float2 eps2 = f2(A.fp.eps2f);
     if constexpr (R > 0)
-#pragma unroll 1
+#pragma unroll kUnrollPC
         for (int q = 0; q < npair; ++q) {
             const CPair& Cp = S.t.cp[q];
 #pragma unroll
@@ -672,7 +683,7 @@ __device__ __forceinline__ void force_group(const Args& A, Smem32& S, int64_t sl
             switch (R) {
                 case 1: group_chunk<MODE, 1, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
                 case 2: group_chunk<MODE, 2, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
-                default: group_chunk<MODE, 3, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
+                default: group_chunk<MODE, BH_F32_MAXR, false, ORDER>(A, S, k, b, e, i0, ce, 0, oh, ol, lane); break;
             }
         }
         i0 += cnt;
@@ -754,6 +765,19 @@ __global__ void k_order_hist(int64_t ng, const int32_t* __restrict__ groups, con
     atomicAdd(&cnt[order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost)], 1ull);
 }
 
+// Windowed order: key = (group index / window, bucket); a stable sort of the
+// keys keeps list (Morton) order within a window and a bucket, so the warps
+// running at one time work on one stretch of the ring (their list data
+// overlaps in L2) while the warps side by side still share a size class.
+__global__ void k_order_keys(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+                             const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
+                             const int64_t* __restrict__ pc_off, uint32_t chunk, bool by_cost, int64_t window,
+                             uint64_t* __restrict__ keys) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    keys[k] = ((uint64_t)(k / window) << 8) | (uint64_t)order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost);
+}
+
 // exclusive prefix of the bucket counts (one block of kOrderBuckets threads)
 __global__ void k_order_prefix(unsigned long long* cnt) {
     __shared__ unsigned long long v[kOrderBuckets];
@@ -820,13 +844,15 @@ __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned lon
                              const double* __restrict__ y, const double* __restrict__ z,
                              const double* __restrict__ vx, const double* __restrict__ vy,
                              const double* __restrict__ vz, const double* __restrict__ m,
-                             unsigned long long* __restrict__ acc, int* status) {
+                             unsigned long long* __restrict__ acc, unsigned long long* n_touch, int* status) {
     const int64_t np = contact_count(count, cap, status, false);
+    unsigned long long touching = 0;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
         const uint2 pr = pairs[u];
         const uint32_t i = pr.x, j = pr.y;
         double a[3] = {0.0, 0.0, 0.0};
-        contact_term64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j], vz[j], m[j], a);
+        touching += contact_term64(fp, x[i], y[i], z[i], vx[i], vy[i], vz[i], m[i], x[j], y[j], z[j], vx[j], vy[j],
+                                   vz[j], m[j], a);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double v = a[c];
@@ -837,6 +863,7 @@ __global__ void k_contacts64(const uint2* __restrict__ pairs, const unsigned lon
             atomicAdd(&acc[3 * (int64_t)i + c], (unsigned long long)__double2ll_rn(v * kFix));
         }
     }
+    if (touching) atomicAdd(n_touch, touching);
 }
 
 __global__ void k_contacts_apply(const uint2* __restrict__ pairs, const unsigned long long* __restrict__ count,
@@ -891,8 +918,29 @@ int build_order32(Ctx* c) {
     BH_TRY(grow(c, c->order, (size_t)ng + 1, "group order"));
     BH_TRY(grow(c, c->order_cnt, 2 * (size_t)kOrderBuckets, "group order buckets"));
     unsigned long long* cnt = c->order_cnt.p;
-    const uint32_t chunk = (uint32_t)c->tune.chunk;
+    const uint32_t chunk = (uint32_t)std::min(c->tune.chunk, 32 * BH_F32_MAXR);
     const bool by_cost = c->tune.order_by_cost != 0;
+    if (c->tune.order_window > 0 && ng > c->tune.order_window) {
+        for (int b = 0; b < 2; ++b) {
+            BH_TRY(grow(c, c->ord_key[b], (size_t)ng, "group order keys"));
+            BH_TRY(grow(c, c->ord_idx[b], (size_t)ng, "group order indices"));
+        }
+        BH_TRY(grow(c, c->ord_scratch, (size_t)sort_scratch_words(ng), "group order sort scratch"));
+        k_order_keys<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
+                                                                 c->cnt_c.p, chunk, by_cost, c->tune.order_window,
+                                                                 c->ord_key[0].p);
+        BH_LAUNCH(c);
+        if (c->sort_attr_device != c->device) {
+            BH_CUDA(c, sort_setup_device());
+            c->sort_attr_device = c->device;
+        }
+        BH_CUDA(c, sort_pairs_with(c->stream, c->ord_key[0].p, c->ord_idx[0].p, c->ord_key[1].p, c->ord_idx[1].p, ng,
+                                   c->ord_scratch.p));
+        c->n_launches += 1 + 8 * 5;
+        BH_CUDA(c, cudaMemcpyAsync(c->order.p, c->ord_idx[0].p, ng * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        return BH_OK;
+    }
     BH_CUDA(c, cudaMemsetAsync(cnt, 0, 2 * kOrderBuckets * sizeof(unsigned long long), c->stream));
     k_order_hist<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
                                                              c->cnt_c.p, chunk, by_cost, cnt);
@@ -912,7 +960,7 @@ int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, 
     k_contacts_clear<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, c->d_status);
     BH_LAUNCH(c);
     k_contacts64<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, fp, p->x, p->y, p->z, p->vx, p->vy,
-                                            p->vz, p->m, acc, c->d_status);
+                                            p->vz, p->m, acc, c->d_small + 18, c->d_status);
     BH_LAUNCH(c);
     k_contacts_apply<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, p->ax, p->ay, p->az,
                                                 c->d_status);
@@ -948,7 +996,9 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
     A.contact_cap = (int64_t)c->contacts.cap;
     A.ncontact = c->d_small + 16;
+    c->contact_stats = contact;
     BH_CUDA(c, cudaMemsetAsync(A.ncontact, 0, sizeof(unsigned long long), c->stream));
+    BH_CUDA(c, cudaMemsetAsync(c->d_small + 18, 0, sizeof(unsigned long long), c->stream));  // pairs in contact
     A.n = (uint32_t)c->n;
     A.nn = c->n_nodes;
     A.status = c->d_status;
@@ -968,7 +1018,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
                                                 smax));
         c->f32_attr_device = c->device;
     }
-    A.chunk = c->tune.chunk;
+    A.chunk = std::min(c->tune.chunk, 32 * BH_F32_MAXR);
     A.ticket = nullptr;
     A.warp_time = nullptr;
     unsigned nb;

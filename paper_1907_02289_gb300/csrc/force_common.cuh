@@ -46,12 +46,12 @@ __device__ __forceinline__ void exact_pair64(const ForceParams& fp, double xi, d
 // The spring and dashpot part of Eq. (1) alone (the gravity at r_coll is
 // added elsewhere): nonzero iff 0 < r <= r_coll, decided in FP64 in the
 // oracle's operation order.
-__device__ __forceinline__ void contact_term64(const ForceParams& fp, double xi, double yi, double zi, double vxi,
+__device__ __forceinline__ bool contact_term64(const ForceParams& fp, double xi, double yi, double zi, double vxi,
                                                double vyi, double vzi, double mi, double xj, double yj, double zj,
                                                double vxj, double vyj, double vzj, double mj, double* a) {
     const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    if (r2 == 0.0 || r2 > fp.rc2) return;
+    if (r2 == 0.0 || r2 > fp.rc2) return false;
     const double r = __dsqrt_rn(r2);
     const double dvx = __dsub_rn(vxj, vxi), dvy = __dsub_rn(vyj, vyi), dvz = __dsub_rn(vzj, vzi);
     const double rv = __dadd_rn(__dadd_rn(__dmul_rn(dx, dvx), __dmul_rn(dy, dvy)), __dmul_rn(dz, dvz));
@@ -61,6 +61,7 @@ __device__ __forceinline__ void contact_term64(const ForceParams& fp, double xi,
     a[0] += f * dx;
     a[1] += f * dy;
     a[2] += f * dz;
+    return true;
 }
 
 // Central mass at the origin: a += -G Mc x / |x|^3.

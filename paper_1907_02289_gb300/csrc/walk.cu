@@ -29,48 +29,26 @@ struct WalkParams {
     int np;
 };
 
-// Team walk: 8 lanes per group, 4 groups per warp.  A team evaluates a run of
-// siblings (the children of one node, at most 8) at once, one node per lane,
-// from one coalesced load of their records.  It emits, in order, the entries
-// of the siblings before the first one that is opened and has children,
-// keeps the rest of the run on its stack and descends into that one: the
-// depth-first octant order of a one-thread walk, so both lists come out in
-// order of first particle.
-constexpr int kTeam = 8;
-constexpr int kWalkThreads = 128;
-constexpr int kTeamsPerBlock = kWalkThreads / kTeam;
-constexpr int kStack = kLevels + 3;
-
 template <bool FILL>
-__global__ void __launch_bounds__(kWalkThreads) k_walk(int64_t ng, const int32_t* __restrict__ groups,
-                                                      const WalkNode* __restrict__ wn,
-                                                      const uint32_t* __restrict__ begin,
-                                                      const uint32_t* __restrict__ end, WalkParams wp,
-                                                      int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
-                                                      int64_t* __restrict__ nj_io, int32_t* __restrict__ P,
-                                                      int32_t* __restrict__ C, unsigned long long* inter,
-                                                      int64_t nn, int* status) {
-    __shared__ int2 stk[kTeamsPerBlock][kStack];
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int team = threadIdx.x / kTeam;  // team within the block
-    const int tl = threadIdx.x & (kTeam - 1);
-    const int tshift = lane & ~(kTeam - 1);  // the team's first lane in the warp
-    const int64_t k = (int64_t)blockIdx.x * kTeamsPerBlock + team;
+__global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
+                                              const WalkNode* __restrict__ wn,
+                                              const uint32_t* __restrict__ begin,
+                                              const uint32_t* __restrict__ end, WalkParams wp,
+                                              int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
+                                              int64_t* __restrict__ nj_io, int32_t* __restrict__ P,
+                                              int32_t* __restrict__ C, unsigned long long* inter,
+                                              int64_t nn, int* status) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < ng;
-    int64_t np = 0, nc = 0, nj = 0, nown = 0, ni = 0, pbase = 0, cbase = 0;
-    int glo0 = 0, glo1 = 0, glo2 = 0, ghi0 = 0, ghi1 = 0, ghi2 = 0;
-    uint32_t gb = 0, ge = 0;
-    long long rcq = 0;
-    int sp = 0;
+    int64_t np = 0, nc = 0, nj = 0, ni = 0, nown = 0;
     if (active) {
         const int32_t g = groups[k];
         const WalkNode G = wn[g];
-        gb = begin[g];
-        ge = end[g];
-        glo0 = (int)G.a.x; glo1 = (int)G.a.y; glo2 = (int)G.a.z;
-        ghi0 = (int)G.b.x; ghi1 = (int)G.b.y; ghi2 = (int)G.b.z;
-        ni = (int64_t)(ge - gb);
+        const uint32_t gb = begin[g], ge = end[g];
+        const int glo0 = (int)G.a.x, glo1 = (int)G.a.y, glo2 = (int)G.a.z;
+        const int ghi0 = (int)G.b.x, ghi1 = (int)G.b.y, ghi2 = (int)G.b.z;
+        ni = (int64_t)(end[g] - begin[g]);
+        int64_t pbase = 0, cbase = 0;
         if (FILL) {
             pbase = np_io[k];
             cbase = nc_io[k];
@@ -83,111 +61,59 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(int64_t ng, const int32_t
             else
                 hi = mid - 1;
         }
-        rcq = wp.rcq[root];
-        if (tl == 0) stk[team][0] = make_int2(root, root + 1);
-        sp = 1;
-    }
-    __syncwarp();
-    while (__any_sync(FULL, sp > 0)) {
-        const bool live = sp > 0;
-        int s = 0, e = 0;
-        if (live) {
-            const int2 r = stk[team][sp - 1];
-            s = r.x;
-            e = r.y;
-        }
-        const int node = s + tl;
-        bool has = live && node < e;
-        if (has && (node < 0 || node >= nn)) {  // never taken for a valid tree
-            atomicOr(status, kStatBounds);
-            has = false;
-        }
-        int cls = -1;  // 0: accepted (cell entry), 1: opened leaf, 2: opened with children
-        int nch = 0, fc = 0;
-        uint32_t lb = 0, le = 0;
-        if (has) {
+        const long long rcq = wp.rcq[root];
+        int sn[kLevels + 3], se[kLevels + 3];
+        int sp = 0;
+        int node = root;
+        for (;;) {
             const WalkNode R = wn[node];
-            const int lev = (int)(R.a.w & 0xffu);
-            nch = (int)(R.a.w >> 8);
-            fc = (int)R.b.w;
+            const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
             const int d0 = max(0, max((int)R.a.x - ghi0 - 1, glo0 - (int)R.b.x - 1));
             const int d1 = max(0, max((int)R.a.y - ghi1 - 1, glo1 - (int)R.b.y - 1));
             const int d2i = max(0, max((int)R.a.z - ghi2 - 1, glo2 - (int)R.b.z - 1));
             const long long d2 = (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2i * d2i;
             const bool open = d2 < wp.D[lev] || d2 <= rcq;
-            cls = open ? (nch == 0 ? 1 : 2) : 0;
-            if (cls == 1 && !FILL) {
-                lb = begin[node];
-                le = end[node];
-            }
-        }
-        const unsigned b_int = (__ballot_sync(FULL, cls == 2) >> tshift) & 0xffu;
-        const unsigned b_acc = (__ballot_sync(FULL, cls == 0) >> tshift) & 0xffu;
-        const unsigned b_leaf = (__ballot_sync(FULL, cls == 1) >> tshift) & 0xffu;
-        const int f = b_int ? __ffs(b_int) - 1 : kTeam;  // first sibling to descend into
-        const unsigned below = (1u << f) - 1u;           // siblings whose entries go out now
-        const unsigned emit_c = b_acc & below, emit_p = b_leaf & below;
-        const unsigned lt = (1u << tl) - 1u;
-        const bool my_c = (emit_c >> tl) & 1u, my_p = (emit_p >> tl) & 1u;
-        if (FILL) {
-            if (my_c) C[cbase + nc + __popc(emit_c & lt)] = node;
-            if (my_p) P[pbase + np + __popc(emit_p & lt)] = node;
-        } else if (my_p) {
-            if (lb >= gb && lb < ge)
-                nown += (int64_t)(le - lb);  // the group's own particles
-            else
-                nj += (int64_t)(le - lb);
-        }
-        nc += __popc(emit_c);
-        np += __popc(emit_p);
-        // children of the sibling descended into, from its lane
-        const int src = tshift + (b_int ? f : tl);
-        const int cfc = __shfl_sync(FULL, fc, src), cnch = __shfl_sync(FULL, nch, src);
-        __syncwarp();
-        if (live) {
-            if (b_int) {
-                if (s + f + 1 < e) {
-                    if (tl == 0) stk[team][sp - 1] = make_int2(s + f + 1, e);
+            if (open) {
+                if (nch == 0) {
+                    if (FILL) P[pbase + np] = node;
+                    ++np;
+                    const uint32_t lb = begin[node];
+                    if (lb >= gb && lb < ge)
+                        nown += (int64_t)(end[node] - lb);  // the group's own particles
+                    else
+                        nj += (int64_t)(end[node] - lb);
                 } else {
-                    --sp;
-                }
-                if (sp >= kStack || cfc < 0 || (int64_t)cfc + cnch > nn) {  // never taken for a valid tree
-                    if (tl == 0) atomicOr(status, kStatBounds);
-                    sp = 0;
-                } else {
-                    if (tl == 0) stk[team][sp] = make_int2(cfc, cfc + cnch);
+                    sn[sp] = (int)R.b.w;
+                    se[sp] = (int)R.b.w + nch;
                     ++sp;
                 }
             } else {
-                --sp;
+                if (FILL) C[cbase + nc] = node;
+                ++nc;
+            }
+            if (sp == 0) break;
+            node = sn[sp - 1]++;
+            if (sn[sp - 1] == se[sp - 1]) --sp;
+            if (node < 0 || node >= nn || sp > kLevels + 1) {  // never taken for a valid tree
+                atomicOr(status, kStatBounds);
+                break;
             }
         }
-        __syncwarp();
-    }
-    if (!FILL) {
-        // own/other particle counts of the opened leaves: sum over the team
-#pragma unroll
-        for (int o = kTeam / 2; o > 0; o >>= 1) {
-            nj += __shfl_xor_sync(FULL, nj, o);
-            nown += __shfl_xor_sync(FULL, nown, o);
-        }
-        if (active && tl == 0) {
+        if (!FILL) {
             np_io[k] = np;
             nc_io[k] = nc;
             nj_io[k] = nj;
         }
+    }
+    if (!FILL) {
         // interaction counts: n_i * (list particles) and n_i * (list cells)
-        unsigned long long ipp = 0, ipc = 0;
-        if (active && tl == 0) {
-            ipp = (unsigned long long)(ni * (nj + nown));
-            ipc = (unsigned long long)(ni * nc);
-        }
+        unsigned long long ipp = (unsigned long long)(ni * (nj + nown)), ipc = (unsigned long long)(ni * nc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            ipp += __shfl_xor_sync(FULL, ipp, o);
-            ipc += __shfl_xor_sync(FULL, ipc, o);
+            ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
+            ipc += __shfl_xor_sync(0xffffffffu, ipc, o);
         }
-        if (lane == 0) {
+        if ((threadIdx.x & 31) == 0) {
             atomicAdd(&inter[0], ipp);
             atomicAdd(&inter[1], ipc);
         }
@@ -278,8 +204,8 @@ int stage_lists(Ctx* c) {
     const WalkParams wp = walk_params(c);
     unsigned long long* inter = c->d_small + 8;
     BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));
-    const unsigned nb = blocks_for(ng, kTeamsPerBlock);
-    k_walk<false><<<nb, kWalkThreads, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
+    const unsigned nb = blocks_for(ng, 128);
+    k_walk<false><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
                                              c->cnt_c.p, c->cnt_j.p, nullptr, nullptr, inter,
                                              c->n_nodes, c->d_status);
     BH_LAUNCH(c);
@@ -300,7 +226,7 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->P, (size_t)c->n_pp + 1, "particle lists"));
     BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
     BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));
-    k_walk<true><<<nb, kWalkThreads, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
+    k_walk<true><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
                                             c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
                                             c->n_nodes, c->d_status);
     BH_LAUNCH(c);

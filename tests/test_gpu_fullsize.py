@@ -72,13 +72,21 @@ def _sampled_rows(S):
     return np.concatenate([np.arange(t["begin"][g], t["end"][g]) for g in S.groups])
 
 
-def test_ring_2p20_fp64_ten_steps():
-    """2^20 ring, FP64 path: structures at the rebuilds of evaluations 4 and
-    8 bit for bit, and positions/velocities after 10 steps within the force
-    tolerance propagated through the steps."""
+def test_ring_2p20_fp64_forces_and_ten_steps():
+    """2^20 ring, FP64 path: every particle's force of the first evaluation
+    within 1e-12 of the oracle; then 10 steps with list reuse, structures at
+    the rebuilds of evaluations 4 and 8 bit for bit, and positions/velocities
+    after 10 steps within the force tolerance propagated through the steps
+    (the accelerations after 10 steps are not compared: positions differing
+    in the last bit move contact forces, of stiffness kappa, by more than the
+    force tolerance)."""
     from paper_1907_02289_gb300 import bh
     P, prm = synth.make("ring1m_fp64")
     op = orc_params(prm)
+    ctx0, D0 = _gpu(P, prm, 0)
+    S0 = orc.rebuild(P, op)
+    _check_structures(ctx0, len(P["x"]), S0)
+    assert_force_close(accel_of(D0), orc.tree_forces(S0, op), 1e-12, "2^20 first evaluation")
     ctx = bh.Context(**prm)
     D = bh.Particles(P)
     ctx.bh_step(D, 4)
@@ -98,9 +106,6 @@ def test_ring_2p20_fp64_ten_steps():
     dv = max(np.abs(out[f] - S10.P[f]).max() for f in ("vx", "vy", "vz"))
     assert dv <= 20 * prm["dt"] * 1e-12 * a_tree + 1e-14
     assert dx <= 200 * prm["dt"] ** 2 * 1e-12 * a_tree + 1e-14
-    a = np.stack([out["ax"], out["ay"], out["az"]], 1)
-    ac = orc.central(out["x"], out["y"], out["z"], 1.0, 1.0)
-    assert_force_close(a - ac, aref - ac, 1e-12, "2^20 after 10 steps")
 
 
 def test_ring_2p24_fp32_vs_fp64_sample(capsys):

@@ -70,16 +70,26 @@ def test_chunks_and_orders_meet_gate(ring, chunk, by_cost):
     assert_force_close(accel_of(D), a_ref, 1e-5, f"chunk {chunk}")
 
 
+@pytest.mark.parametrize("window", [64, 256, 100000])
+def test_windowed_order_gives_same_forces(ring, window):
+    """The processing order never changes a group's arithmetic."""
+    P, prm, ref, a_ref = ring
+    _, D0 = _forces(P, prm)
+    _, D1 = _forces(P, prm, order_window=window)
+    np.testing.assert_allclose(accel_of(D1), accel_of(D0), rtol=1e-12, atol=1e-30)
+
+
 def test_tuning_validation(ring):
     from paper_1907_02289_gb300 import bh
     P, prm, _, _ = ring
     ctx = bh.Context(**prm)
-    for kw in (dict(chunk=48), dict(warps=0), dict(warps=9), dict(sched=3), dict(n_g=4), dict(graph=2)):
+    for kw in (dict(chunk=48), dict(warps=0), dict(warps=9), dict(sched=3), dict(n_g=4), dict(graph=2),
+               dict(order_window=-1)):
         with pytest.raises(bh.BHError) as e:
             ctx.bh_set_tuning(**kw)
         assert e.value.code == bh.BH_E_INVAL
     t = ctx.bh_get_tuning()
-    assert t == dict(n_g=64, chunk=96, warps=4, sched=0, order_by_cost=1, graph=0)
+    assert t == dict(n_g=64, chunk=96, warps=4, sched=2, order_by_cost=1, graph=0, order_window=0)
 
 
 @pytest.mark.parametrize("precision", [0, 1])

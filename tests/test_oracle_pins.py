@@ -448,3 +448,36 @@ def test_step_time_reversible_and_schedule():
     back = {f: S2.P[f][np.argsort(S2.P["id"])] for f in S2.P}
     x0 = np.stack([P["x"], P["y"], P["z"]], 1); x1 = np.stack([back["x"], back["y"], back["z"]], 1)
     assert np.max(np.abs(x1 - x0)) < 1e-12
+
+
+# ---- diagnostics ------------------------------------------------------------
+def test_diagnostics_circular_orbit_closed_form():
+    """One particle of mass m on a circular orbit of radius R about M_c:
+    K = m v^2 / 2 = G M_c m / (2R), W = -G M_c m / R, L = m R v along z."""
+    R, m, GM = 1.3, 2e-3, 1.0
+    v = np.sqrt(GM / R)
+    P = {"x": np.array([R]), "y": np.array([0.0]), "z": np.array([0.0]), "vx": np.array([0.0]),
+         "vy": np.array([v]), "vz": np.array([0.0]), "m": np.array([m])}
+    d = orc.diagnostics(P, 1.0, GM)
+    assert d["mass"] == m
+    assert np.isclose(d["kinetic"], GM * m / (2 * R), rtol=1e-15)
+    assert np.isclose(d["potential_central"], -GM * m / R, rtol=1e-15)
+    assert np.allclose(d["angular_momentum"], [0.0, 0.0, m * R * v], rtol=1e-15, atol=0)
+    assert np.allclose(d["momentum"], [0.0, m * v, 0.0], rtol=1e-15, atol=0)
+
+
+def test_diagnostics_opposite_pair_and_virial():
+    """Two equal masses with opposite velocities: zero momentum; for circular
+    Kepler orbits 2K + W = 0."""
+    R, GM = 0.9, 1.0
+    v = np.sqrt(GM / R)
+    P = {"x": np.array([R, -R]), "y": np.array([0.0, 0.0]), "z": np.array([0.0, 0.0]), "vx": np.array([0.0, 0.0]),
+         "vy": np.array([v, -v]), "vz": np.array([0.0, 0.0]), "m": np.array([1.0, 1.0])}
+    d = orc.diagnostics(P, 1.0, GM)
+    assert np.array_equal(d["momentum"], np.zeros(3))
+    assert np.isclose(2 * d["kinetic"] + d["potential_central"], 0.0, atol=1e-15)
+
+
+def test_contact_pairs_brute_force_small():
+    P = {"x": np.array([0.0, 1.5e-5, 3.5e-5, 1.0]), "y": np.zeros(4), "z": np.zeros(4)}
+    assert orc.contact_pairs(P, 2e-5) == 2  # (0,1) at 1.5e-5 and (1,2) at 2e-5 apart
