@@ -73,7 +73,14 @@ typedef struct bh_ctx bh_ctx;
  *  precision  BH_PREC_FP64 or BH_PREC_FP32 (Sec. 4.7).
  *  rebuild_every  force evaluation k rebuilds keys..lists iff
  *             k % rebuild_every == 0, otherwise refreshes moments only.
- *  key_frame  0 = Cartesian (the only value accepted).
+ *  key_frame  frame of the keys, the tree and the opening test (forces are
+ *             always Cartesian): 0 = (x, y, z); 1 = cylindrical (phi, r, z),
+ *             Sec. 4.3, for a narrow ring about the z axis near r ~ 1, where
+ *             those coordinates measure distance like Cartesian ones.  phi is
+ *             periodic in the opening test, and the contact clause uses
+ *             r_coll / r_min (r_min: the smallest particle radius of the
+ *             patch), so no contact pair is missed.  Needs r > 0 for every
+ *             particle (BH_E_INVAL otherwise, at the list build).
  *  list_capacity  reserved, 0. */
 typedef struct {
     double theta, eps, G, M_central, r_coll, kappa, eta, dt;
@@ -103,7 +110,7 @@ typedef struct {
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: BH_E_INVAL for theta < 0, n_g < 1, n_leaf < 1, n_leaf > n_g,
- * order not 1/2, precision not 0/1, rebuild_every < 1, key_frame != 0,
+ * order not 1/2, precision not 0/1, rebuild_every < 1, key_frame not 0/1,
  * dt < 0. */
 int bh_create(const bh_params* p, void* stream, bh_ctx** out);
 
@@ -117,7 +124,8 @@ int bh_create(const bh_params* p, void* stream, bh_ctx** out);
  * 0..n_patches-1; node, group and list ids are global.  offsets is a host
  * array of n_patches + 1 entries (copied): offsets[0] = 0, strictly
  * increasing, offsets[n_patches] = the n passed later (< 2^31).
- * Errors: as bh_create, plus BH_E_INVAL for n_patches < 1 or bad offsets.
+ * Errors: as bh_create, plus BH_E_INVAL for n_patches outside 1..65535 or bad
+ * offsets.
  * n_patches = 1 is bh_create. */
 int bh_batch_create(const bh_params* p, int n_patches, const int64_t* offsets, void* stream, bh_ctx** out);
 int bh_destroy(bh_ctx* ctx);

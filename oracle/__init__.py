@@ -87,6 +87,7 @@ class Params:
     eta: float = 0.0
     dt: float = 1e-3
     rebuild_every: int = 4
+    key_frame: int = 0          # 0 Cartesian, 1 cylindrical (phi, r, z) tree (Sec. 4.3)
 
 
 # --------------------------------------------------------------------------
@@ -172,15 +173,40 @@ def groups(tree, n_g):
 
 
 def lists(tree, qlo, qhi, grp, theta, r_coll, L):
+    """Cartesian frame: contact threshold (r_coll S)^2 on the grid."""
+    S = 2097152.0 / L
+    rcq = r_coll * S
+    return lists_ex(tree, qlo, qhi, grp, theta, rcq * rcq, 0)
+
+
+def cyl_geometry(r_coll, r_min, L):
+    """Cylindrical frame: (contact threshold on the grid, phi period in cells)."""
+    rcq2 = np.zeros(1)
+    period = np.zeros(1, np.int64)
+    lib().orc_cyl_geometry(_dbl(r_coll), _dbl(r_min), _dbl(L), _p(rcq2), _p(period))
+    return float(rcq2[0]), int(period[0])
+
+
+def cyl_coords(x, y):
+    """(phi, r) of every particle (Sec. 4.3 tree coordinates)."""
+    n = len(x)
+    phi = np.empty(n)
+    r = np.empty(n)
+    lib().orc_cyl(_i64(n), _p(np.ascontiguousarray(x, dtype=np.float64)),
+                  _p(np.ascontiguousarray(y, dtype=np.float64)), _p(phi), _p(r))
+    return phi, r
+
+
+def lists_ex(tree, qlo, qhi, grp, theta, rcq2, period):
     ng = len(grp)
     pp_off = np.zeros(ng + 1, np.int64)
     pc_off = np.zeros(ng + 1, np.int64)
     args = [_i64(ng), _p(grp), _p(tree["level"]), _p(tree["first_child"]), _p(tree["nchild"]),
-            _p(qlo), _p(qhi), _dbl(theta), _dbl(r_coll), _dbl(L)]
-    lib().orc_lists(*args, _p(pp_off), None, _p(pc_off), None)
+            _p(qlo), _p(qhi), _dbl(theta), _dbl(rcq2), _i64(period)]
+    lib().orc_lists_ex(*args, _p(pp_off), None, _p(pc_off), None)
     P = np.empty(max(int(pp_off[-1]), 1), np.int32)
     C = np.empty(max(int(pc_off[-1]), 1), np.int32)
-    lib().orc_lists(*args, _p(pp_off), _p(P), _p(pc_off), _p(C))
+    lib().orc_lists_ex(*args, _p(pp_off), _p(P), _p(pc_off), _p(C))
     return {"pp_off": pp_off, "P": P[: pp_off[-1]].copy(), "pc_off": pc_off, "C": C[: pc_off[-1]].copy()}
 
 
@@ -264,6 +290,8 @@ def rebuild(P: dict, prm: Params, group_subset=None) -> State:
     keep: lists (and tree forces) are then made for those groups only, for
     checking a sample of a workload too large to walk whole."""
     x, y, z = P["x"], P["y"], P["z"]
+    if prm.key_frame == 1:  # Sec. 4.3: tree in (phi, r, z)
+        x, y = cyl_coords(x, y)
     lo, L = root_box(x, y, z)
     k = keys(x, y, z, lo, L)
     perm = sort_perm(k)
@@ -275,7 +303,13 @@ def rebuild(P: dict, prm: Params, group_subset=None) -> State:
     grp = groups(tree, prm.n_g)
     if group_subset is not None:
         grp = np.ascontiguousarray(grp[group_subset(grp, tree)])
-    lst = lists(tree, qlo, qhi, grp, prm.theta, prm.r_coll, L)
+    if prm.key_frame == 1:
+        if not lo[1] > 0.0:
+            raise ValueError("the cylindrical key frame needs every particle off the axis (r > 0)")
+        rcq2, period = cyl_geometry(prm.r_coll, lo[1], L)
+        lst = lists_ex(tree, qlo, qhi, grp, prm.theta, rcq2, period)
+    else:
+        lst = lists(tree, qlo, qhi, grp, prm.theta, prm.r_coll, L)
     return State(P=SP, lo=lo, L=L, skeys=sk, perm=perm, tree=tree, qlo=qlo, qhi=qhi, mom=mom,
                  groups=grp, lists=lst)
 

@@ -125,6 +125,58 @@ void orc_keys(int64_t n, const double* x, const double* y, const double* z,
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Sec. 4.3: keys, tree and opening test in cylindrical coordinates
+ * (phi, r, z), which for a narrow ring at r ~ 1 measure distance like
+ * (x, y, z) (the paper's Eq. for ds^2); forces stay Cartesian.
+ *
+ * phi comes from atan reduced to [0, tan(pi/12)] by
+ * atan(t) = pi/6 + atan((sqrt(3) t - 1) / (t + sqrt(3))) and the Taylor
+ * series u - u^3/3 + ... - u^11/11 (truncation below 3e-9 rad), then placed
+ * in its octant.  Only IEEE-rounded +, -, *, / are used, in a fixed order, so
+ * the angle (and the key) is a deterministic function of (x, y).
+ * r = sqrt(x^2 + y^2) (correctly rounded).
+ * ---------------------------------------------------------------------- */
+static double orc_atan01(double t)
+{
+    const double sqrt3 = 1.7320508075688772, tan15 = 0.2679491924311227, pi6 = 0.5235987755982988;
+    double base = 0.0, u = t;
+    if (t > tan15) {
+        u = (t * sqrt3 - 1.0) / (t + sqrt3);
+        base = pi6;
+    }
+    double u2 = u * u;
+    double p = -1.0 / 11.0;
+    p = p * u2 + 1.0 / 9.0;
+    p = p * u2 + -1.0 / 7.0;
+    p = p * u2 + 1.0 / 5.0;
+    p = p * u2 + -1.0 / 3.0;
+    p = p * u2 + 1.0;
+    return base + u * p;
+}
+
+static double orc_phi(double x, double y)
+{
+    const double pi2 = 1.5707963267948966, pi = 3.141592653589793, twopi = 6.283185307179586;
+    double ax = fabs(x), ay = fabs(y);
+    double mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
+    if (mx == 0.0) return 0.0;
+    double a = orc_atan01(mn / mx);
+    if (ay > ax) a = pi2 - a;
+    if (x < 0.0) a = pi - a;
+    if (y < 0.0) a = twopi - a;
+    return a;
+}
+
+void orc_cyl(int64_t n, const double* x, const double* y, double* phi, double* r)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        phi[i] = orc_phi(x[i], y[i]);
+        r[i] = sqrt(x[i] * x[i] + y[i] * y[i]);
+    }
+}
+
 /* Grid coordinates recovered from keys: q[3*i + axis]. */
 void orc_key_coords(int64_t n, const uint64_t* key, uint32_t* q)
 {
@@ -374,7 +426,7 @@ int64_t orc_groups(int64_t n_nodes, const uint32_t* begin, const uint32_t* end,
  * the second clause keeping every possible contact partner a particle.
  * ---------------------------------------------------------------------- */
 static int orc_mac_open(const uint32_t* glo, const uint32_t* ghi, const uint32_t* clo,
-                        const uint32_t* chi, int level, double th2, double rcq2)
+                        const uint32_t* chi, int level, double th2, double rcq2, int64_t period)
 {
     int64_t d2 = 0;
     for (int a = 0; a < 3; ++a) {
@@ -383,6 +435,13 @@ static int orc_mac_open(const uint32_t* glo, const uint32_t* ghi, const uint32_t
         int64_t t2 = (int64_t)glo[a] - (int64_t)chi[a] - 1;
         if (t1 > delta) delta = t1;
         if (t2 > delta) delta = t2;
+        if (a == 0 && period > 0 && delta > 0) {
+            /* periodic phi axis: the shorter way round */
+            int64_t w = (t1 > 0) ? (int64_t)glo[a] + period - (int64_t)chi[a] - 1
+                                 : (int64_t)clo[a] + period - (int64_t)ghi[a] - 1;
+            if (w < 0) w = 0;
+            if (w < delta) delta = w;
+        }
         d2 += delta * delta;
     }
     double s = ldexp(1.0, ORC_LEVELS - level);
@@ -397,6 +456,7 @@ typedef struct {
     const uint32_t* qlo;
     const uint32_t* qhi;
     double th2, rcq2;
+    int64_t period;
 } orc_walk_tree;
 
 /* Depth-first walk in octant order for group node g (Sec. 4.2 step 3d:
@@ -408,7 +468,7 @@ static void orc_walk_rec(const orc_walk_tree* t, int32_t g, int32_t node, int32_
     const uint32_t* glo = t->qlo + 3 * (int64_t)g;
     const uint32_t* ghi = t->qhi + 3 * (int64_t)g;
     if (orc_mac_open(glo, ghi, t->qlo + 3 * (int64_t)node, t->qhi + 3 * (int64_t)node,
-                     t->level[node], t->th2, t->rcq2)) {
+                     t->level[node], t->th2, t->rcq2, t->period)) {
         if (t->nchild[node] == 0) {
             if (P) P[*np] = node;
             (*np)++;
@@ -424,10 +484,10 @@ static void orc_walk_rec(const orc_walk_tree* t, int32_t g, int32_t node, int32_
 
 /* Interaction lists of every group, in CSR form.  Call once with P and C NULL
  * to get pp_off / pc_off (sizes ng+1), then again with the arrays. */
-void orc_lists(int64_t ng, const int32_t* groups, const uint8_t* level,
-               const int32_t* first_child, const uint8_t* nchild, const uint32_t* qlo,
-               const uint32_t* qhi, double theta, double r_coll, double L, int64_t* pp_off,
-               int32_t* P, int64_t* pc_off, int32_t* C)
+void orc_lists_ex(int64_t ng, const int32_t* groups, const uint8_t* level,
+                  const int32_t* first_child, const uint8_t* nchild, const uint32_t* qlo,
+                  const uint32_t* qhi, double theta, double rcq2, int64_t period, int64_t* pp_off,
+                  int32_t* P, int64_t* pc_off, int32_t* C)
 {
     orc_walk_tree t;
     t.level = level;
@@ -436,9 +496,8 @@ void orc_lists(int64_t ng, const int32_t* groups, const uint8_t* level,
     t.qlo = qlo;
     t.qhi = qhi;
     t.th2 = theta * theta;
-    double S = 2097152.0 / L;
-    double rcq = r_coll * S;
-    t.rcq2 = rcq * rcq;
+    t.rcq2 = rcq2;
+    t.period = period;
     if (P == NULL) {
         pp_off[0] = 0;
         pc_off[0] = 0;
@@ -460,6 +519,33 @@ void orc_lists(int64_t ng, const int32_t* groups, const uint8_t* level,
         int64_t np = 0, nc = 0;
         orc_walk_rec(&t, groups[k], 0, P + pp_off[k], &np, C + pc_off[k], &nc);
     }
+}
+
+/* Cartesian frame: contact threshold (r_coll S)^2 in grid units, no period. */
+void orc_lists(int64_t ng, const int32_t* groups, const uint8_t* level,
+               const int32_t* first_child, const uint8_t* nchild, const uint32_t* qlo,
+               const uint32_t* qhi, double theta, double r_coll, double L, int64_t* pp_off,
+               int32_t* P, int64_t* pc_off, int32_t* C)
+{
+    double S = 2097152.0 / L;
+    double rcq = r_coll * S;
+    orc_lists_ex(ng, groups, level, first_child, nchild, qlo, qhi, theta, rcq * rcq, 0, pp_off, P, pc_off,
+                 C);
+}
+
+/* Cylindrical frame (phi, r, z grid with scale S = 2^21 / L): two particles
+ * within r_coll have |dr|, |dz| <= r_coll and a phi difference of at most
+ * ~r_coll / r_min, so (r_coll / r_min + 2e-8) S, squared, bounds their grid
+ * distance (2e-8 covers the angle's approximation error); the phi axis has
+ * period floor(2 pi S) cells. */
+void orc_cyl_geometry(double r_coll, double r_min, double L, double* rcq2, int64_t* period)
+{
+    double S = 2097152.0 / L;
+    double a = r_coll / r_min;
+    a = a + 2e-8;
+    a = a * S;
+    *rcq2 = a * a;
+    *period = (int64_t)floor(6.283185307179586 * S);
 }
 
 /* ------------------------------------------------------------------------

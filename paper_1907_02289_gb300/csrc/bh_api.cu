@@ -109,7 +109,8 @@ int check_params(Ctx* c, const bh_params* p) {
     if (p->precision != BH_PREC_FP64 && p->precision != BH_PREC_FP32)
         return fail(c, BH_E_INVAL, "precision must be BH_PREC_FP64 or BH_PREC_FP32");
     if (p->rebuild_every < 1) return fail(c, BH_E_INVAL, "rebuild_every must be >= 1");
-    if (p->key_frame != 0) return fail(c, BH_E_INVAL, "only the Cartesian key frame (0) is available");
+    if (p->key_frame != 0 && p->key_frame != 1)
+        return fail(c, BH_E_INVAL, "key_frame must be 0 (Cartesian) or 1 (cylindrical)");
     if (!(p->eps >= 0.0) || !(p->r_coll >= 0.0) || !(p->dt >= 0.0))
         return fail(c, BH_E_INVAL, "eps, r_coll and dt must be >= 0");
     return BH_OK;
@@ -155,6 +156,10 @@ int build_tree(Ctx* c, bh_particles* p) {
     BH_CUDA(c, cudaMemcpyAsync(c->h_box.data(), c->d_box, c->h_box.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
     BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->prm.key_frame == 1)
+        for (int q = 0; q < c->n_patches; ++q)
+            if (!(c->h_box[8 * q + 1] > 0.0))
+                return fail(c, BH_E_INVAL, "the cylindrical key frame needs every particle off the axis (r > 0)");
     BH_TRY(stage_sort(c));
     BH_TRY(stage_permute(c, p));
     BH_TRY(stage_octree(c));
@@ -476,8 +481,8 @@ int bh_create(const bh_params* p, void* stream, bh_ctx** out) {
 }
 
 int bh_batch_create(const bh_params* p, int n_patches, const int64_t* offsets, void* stream, bh_ctx** out) {
-    if (n_patches < 1) {
-        fprintf(stderr, "bh_batch_create: n_patches must be >= 1\n");
+    if (n_patches < 1 || n_patches > 65535) {
+        fprintf(stderr, "bh_batch_create: n_patches must be in 1..65535\n");
         if (out) *out = nullptr;
         return BH_E_INVAL;
     }
@@ -495,7 +500,7 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
     for (int b = 0; b < 2; ++b) {
         release(c->ord_key[b]);
         release(c->ord_idx[b]);

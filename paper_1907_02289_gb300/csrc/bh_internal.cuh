@@ -86,6 +86,7 @@ struct Ctx {
     DBuf<uint32_t> tile_meta;           // sort tiles per patch (4 words per tile), n_patches > 1
     int64_t n_tiles = 0;
     DBuf<long long> d_rcq;              // per patch walk contact threshold
+    DBuf<long long> d_period;           // per patch phi period in grid cells (cylindrical frame; 0 = none)
 
     // status and small device scalars
     int* d_status = nullptr;
@@ -100,6 +101,8 @@ struct Ctx {
     DBuf<uint32_t> sort_hist;
     DBuf<uint32_t> digit_hist; // 8 x 256 global digit counts
     DBuf<double> pscratch;     // permutation scratch (8 bytes per particle)
+    DBuf<double> cyl;          // cylindrical frame: phi[n], r[n]
+    DBuf<double> box_part;     // root-box partials (6 per block)
     DBuf<uint8_t> scan_tmp;
 
     // tree

@@ -23,14 +23,16 @@ __device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
     }
 }
 
-// Per-block min/max of each axis -> part[6 * block + {mn x,y,z, mx x,y,z}].
+// Per-block min/max of each axis of patch blockIdx.y (particles
+// [off[q], off[q+1])) -> part[6 * (q * gridDim.x + block) + {mn x,y,z, mx x,y,z}].
 __global__ void k_box_partial(const double* __restrict__ x, const double* __restrict__ y,
-                              const double* __restrict__ z, int64_t n, double* __restrict__ part,
-                              int* status) {
+                              const double* __restrict__ z, const int64_t* __restrict__ off,
+                              double* __restrict__ part, int* status) {
     __shared__ double s[6][kBoxThreads / 32];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+    const int64_t e = off[blockIdx.y + 1];
+    for (int64_t i = off[blockIdx.y] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
          i += (int64_t)gridDim.x * blockDim.x) {
         double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
@@ -55,12 +57,15 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
         double r = s[threadIdx.x][0];
         for (int k = 1; k < kBoxThreads / 32; ++k)
             r = threadIdx.x < 3 ? fmin(r, s[threadIdx.x][k]) : fmax(r, s[threadIdx.x][k]);
-        part[6 * blockIdx.x + threadIdx.x] = r;
+        part[6 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] = r;
     }
 }
 
-// box = {lo_x, lo_y, lo_z, L, S}
-__global__ void k_box_final(const double* __restrict__ part, int nb, double* box) {
+// box of patch q = blockIdx.x from its nb partials: {lo_x, lo_y, lo_z, L, S}
+// at box + 8 q
+__global__ void k_box_final(const double* __restrict__ part_all, int nb, double* box_all) {
+    const double* part = part_all + 6 * (int64_t)blockIdx.x * nb;
+    double* box = box_all + 8 * blockIdx.x;
     __shared__ double r[6];
     if (threadIdx.x < 6) {
         double v = part[threadIdx.x];
@@ -82,6 +87,47 @@ __global__ void k_box_final(const double* __restrict__ part, int nb, double* box
     }
 }
 
+// Sec. 4.3: tree coordinates (phi, r, z) for a ring.  phi from atan of the
+// octant-reduced ratio, itself reduced to [0, tan(pi/12)] with
+// atan(t) = pi/6 + atan((sqrt(3) t - 1) / (t + sqrt(3))) and summed as the
+// Taylor series to u^11 (truncation below 3e-9 rad); every operation is an
+// IEEE-rounded +, -, *, / in a fixed order, so phi is a deterministic
+// function of (x, y).  r = sqrt(x^2 + y^2), correctly rounded.
+__device__ __forceinline__ double atan01(double t) {
+    const double sqrt3 = 1.7320508075688772, tan15 = 0.2679491924311227, pi6 = 0.5235987755982988;
+    double base = 0.0, u = t;
+    if (t > tan15) {
+        u = __ddiv_rn(__dsub_rn(__dmul_rn(t, sqrt3), 1.0), __dadd_rn(t, sqrt3));
+        base = pi6;
+    }
+    const double u2 = __dmul_rn(u, u);
+    double p = -1.0 / 11.0;
+    p = __dadd_rn(__dmul_rn(p, u2), 1.0 / 9.0);
+    p = __dadd_rn(__dmul_rn(p, u2), -1.0 / 7.0);
+    p = __dadd_rn(__dmul_rn(p, u2), 1.0 / 5.0);
+    p = __dadd_rn(__dmul_rn(p, u2), -1.0 / 3.0);
+    p = __dadd_rn(__dmul_rn(p, u2), 1.0);
+    return __dadd_rn(base, __dmul_rn(u, p));
+}
+
+__global__ void k_cyl(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                      double* __restrict__ phi, double* __restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double X = x[i], Y = y[i];
+    const double ax = fabs(X), ay = fabs(Y);
+    const double mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
+    double a = 0.0;
+    if (mx != 0.0) {
+        a = atan01(__ddiv_rn(mn, mx));
+        if (ay > ax) a = __dsub_rn(1.5707963267948966, a);
+        if (X < 0.0) a = __dsub_rn(3.141592653589793, a);
+        if (Y < 0.0) a = __dsub_rn(6.283185307179586, a);
+    }
+    phi[i] = a;
+    r[i] = __dsqrt_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)));
+}
+
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
     uint64_t x = v & kQMax;
     x = (x | (x << 32)) & 0x001f00000000ffffull;
@@ -99,16 +145,27 @@ __device__ __forceinline__ uint32_t quantise(double v, double lo, double S) {
     return (uint32_t)t;
 }
 
+// Keys of every particle on its patch's grid (patch by binary search of the
+// offsets); idx = the particle's index.
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, int64_t n, const double* __restrict__ box,
-                       uint64_t* __restrict__ key, uint32_t* __restrict__ idx, uint32_t idx_base) {
+                       const double* __restrict__ z, int64_t n, const int64_t* __restrict__ off, int np,
+                       const double* __restrict__ boxes, uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    int q = 0;
+    for (int lo = 0, hi = np - 1; lo < hi;) {  // last patch starting at or before i
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = q = mid;
+        else
+            hi = mid - 1;
+    }
+    const double* box = boxes + 8 * q;
     const double S = box[4];
     uint32_t qx = quantise(x[i], box[0], S), qy = quantise(y[i], box[1], S),
              qz = quantise(z[i], box[2], S);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    idx[i] = idx_base + (uint32_t)i;
+    idx[i] = (uint32_t)i;
 }
 
 // ---------------------------------------------------------------------------
@@ -297,24 +354,32 @@ __global__ void k_gather8(const unsigned long long* __restrict__ src, unsigned l
 int stage_keys(Ctx* c, const bh_particles* p) {
     const int64_t n = c->n;
     const int nbmax = c->num_sms * 4;
-    BH_TRY(grow(c, c->pscratch, (size_t)(n > 6 * nbmax ? n : 6 * nbmax), "particle scratch"));
-    double* part = c->pscratch.p;
     for (int b = 0; b < 2; ++b) {
         BH_TRY(grow(c, c->key[b], (size_t)n, "keys"));
         BH_TRY(grow(c, c->idx[b], (size_t)n, "sort indices"));
     }
-    for (int q = 0; q < c->n_patches; ++q) {
-        const int64_t o = c->h_off[q], np = c->h_off[q + 1] - o;
-        const int nb = (int)std::min<int64_t>(nbmax, blocks_for(np, kBoxThreads));
-        double* box = c->d_box + 8 * q;
-        k_box_partial<<<nb, kBoxThreads, 0, c->stream>>>(p->x + o, p->y + o, p->z + o, np, part, c->d_status);
+    // tree coordinates: (x, y, z), or (phi, r, z) in the cylindrical frame
+    const double *cx = p->x, *cy = p->y;
+    if (c->prm.key_frame == 1) {
+        BH_TRY(grow(c, c->cyl, 2 * (size_t)n, "cylindrical coordinates"));
+        k_cyl<<<blocks_for(n, 256), 256, 0, c->stream>>>(p->x, p->y, n, c->cyl.p, c->cyl.p + n);
         BH_LAUNCH(c);
-        k_box_final<<<1, 32, 0, c->stream>>>(part, nb, box);
-        BH_LAUNCH(c);
-        k_keys<<<blocks_for(np, 256), 256, 0, c->stream>>>(p->x + o, p->y + o, p->z + o, np, box,
-                                                           c->key[0].p + o, c->idx[0].p + o, (uint32_t)o);
-        BH_LAUNCH(c);
+        cx = c->cyl.p;
+        cy = c->cyl.p + n;
     }
+    // all patches at once: nb blocks per patch for the boxes, then one pass
+    // for the keys
+    const int np = c->n_patches;
+    const int64_t per = n / np;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nbmax / std::min(np, nbmax), blocks_for(per, 4 * kBoxThreads)));
+    BH_TRY(grow(c, c->box_part, 6 * (size_t)nb * np, "box partials"));
+    k_box_partial<<<dim3(nb, np), kBoxThreads, 0, c->stream>>>(cx, cy, p->z, c->d_off.p, c->box_part.p, c->d_status);
+    BH_LAUNCH(c);
+    k_box_final<<<np, 32, 0, c->stream>>>(c->box_part.p, nb, c->d_box);
+    BH_LAUNCH(c);
+    k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(cx, cy, p->z, n, c->d_off.p, np, c->d_box, c->key[0].p,
+                                                      c->idx[0].p);
+    BH_LAUNCH(c);
     c->key_cur = 0;
     return BH_OK;
 }

@@ -25,6 +25,7 @@ namespace {
 struct WalkParams {
     long long D[kLevels + 1];
     const long long* rcq;  // per patch
+    const long long* period;  // per patch period of grid axis 0 (cylindrical frame), 0 = none
     const int64_t* off;    // patch particle offsets (np + 1)
     int np;
 };
@@ -62,13 +63,17 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                 hi = mid - 1;
         }
         const long long rcq = wp.rcq[root];
+        const int period = (int)wp.period[root];
         int sn[kLevels + 3], se[kLevels + 3];
         int sp = 0;
         int node = root;
         for (;;) {
             const WalkNode R = wn[node];
             const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
-            const int d0 = max(0, max((int)R.a.x - ghi0 - 1, glo0 - (int)R.b.x - 1));
+            const int t1 = (int)R.a.x - ghi0 - 1, t2 = glo0 - (int)R.b.x - 1;
+            int d0 = max(0, max(t1, t2));
+            if (period > 0 && d0 > 0)  // periodic phi axis: the shorter way round
+                d0 = min(d0, max(0, t1 > 0 ? glo0 + period - (int)R.b.x - 1 : (int)R.a.x + period - ghi0 - 1));
             const int d1 = max(0, max((int)R.a.y - ghi1 - 1, glo1 - (int)R.b.y - 1));
             const int d2i = max(0, max((int)R.a.z - ghi2 - 1, glo2 - (int)R.b.z - 1));
             const long long d2 = (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2i * d2i;
@@ -180,6 +185,7 @@ WalkParams walk_params(const Ctx* c) {
         w.D[l] = d;
     }
     w.rcq = c->d_rcq.p;
+    w.period = c->d_period.p;
     w.off = c->d_off.p;
     w.np = c->n_patches;
     return w;
@@ -192,15 +198,34 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->cnt_p, (size_t)ng + 1, "list offsets P"));
     BH_TRY(grow(c, c->cnt_c, (size_t)ng + 1, "list offsets C"));
     BH_TRY(grow(c, c->cnt_j, (size_t)ng + 1, "list offsets J"));
-    std::vector<long long> rcq(c->n_patches);
+    // contact thresholds on each patch's grid (S = 2^21 / L).  Cartesian:
+    // (r_coll S)^2.  Cylindrical (phi, r, z): two particles within r_coll have
+    // |dr|, |dz| <= r_coll and a phi difference of at most ~r_coll / r_min, so
+    // (r_coll / r_min + 2e-8) S bounds their grid distance (2e-8 covers the
+    // angle's approximation error); the phi axis wraps after floor(2 pi S) cells.
+    std::vector<long long> rcq(c->n_patches), period(c->n_patches, 0);
     for (int q = 0; q < c->n_patches; ++q) {
-        const double r = c->prm.r_coll * c->h_box[8 * q + 4];
-        const double r2 = r * r;
+        const double L = c->h_box[8 * q + 3];
+        const double S = 2097152.0 / L;
+        double r2;
+        if (c->prm.key_frame == 1) {
+            double a = c->prm.r_coll / c->h_box[8 * q + 1];
+            a = a + 2e-8;
+            a = a * S;
+            r2 = a * a;
+            period[q] = (long long)std::floor(6.283185307179586 * S);
+        } else {
+            const double r = c->prm.r_coll * S;
+            r2 = r * r;
+        }
         rcq[q] = (r2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(r2);
     }
     BH_TRY(grow(c, c->d_rcq, rcq.size(), "walk contact thresholds"));
+    BH_TRY(grow(c, c->d_period, period.size(), "walk periods"));
     BH_CUDA(c, cudaMemcpyAsync(c->d_rcq.p, rcq.data(), rcq.size() * sizeof(long long), cudaMemcpyHostToDevice,
                                c->stream));
+    BH_CUDA(c, cudaMemcpyAsync(c->d_period.p, period.data(), period.size() * sizeof(long long),
+                               cudaMemcpyHostToDevice, c->stream));
     const WalkParams wp = walk_params(c);
     unsigned long long* inter = c->d_small + 8;
     BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));

@@ -481,3 +481,117 @@ def test_diagnostics_opposite_pair_and_virial():
 def test_contact_pairs_brute_force_small():
     P = {"x": np.array([0.0, 1.5e-5, 3.5e-5, 1.0]), "y": np.zeros(4), "z": np.zeros(4)}
     assert orc.contact_pairs(P, 2e-5) == 2  # (0,1) at 1.5e-5 and (1,2) at 2e-5 apart
+
+
+# ------------------------------------------------- cylindrical frame (Sec. 4.3) ----
+def test_cyl_angle_against_atan2_and_special_angles():
+    rng = np.random.default_rng(41)
+    x = rng.normal(size=20000)
+    y = rng.normal(size=20000)
+    phi, r = orc.cyl_coords(x, y)
+    ref = np.mod(np.arctan2(y, x), 2 * np.pi)
+    assert np.abs(phi - ref).max() < 3.5e-9  # Taylor truncation of the reduced atan
+    assert np.all((phi >= 0) & (phi < 2 * np.pi))
+    assert np.allclose(r, np.hypot(x, y), rtol=1e-15, atol=0)
+    # axes and diagonals
+    xs = np.array([1.0, 0.0, -1.0, 0.0, 1.0, -1.0, -1.0, 1.0, 0.0])
+    ys = np.array([0.0, 1.0, 0.0, -1.0, 1.0, 1.0, -1.0, -1.0, 0.0])
+    phi, _ = orc.cyl_coords(xs, ys)
+    want = np.array([0, 0.5, 1, 1.5, 0.25, 0.75, 1.25, 1.75, 0]) * np.pi
+    assert np.abs(phi - want).max() < 3.5e-9
+
+
+def test_cyl_angle_monotone_around_the_circle():
+    t = np.sort(np.random.default_rng(42).uniform(0, 2 * np.pi, 200000))
+    phi, _ = orc.cyl_coords(np.cos(t), np.sin(t))
+    assert np.all(np.diff(phi) >= 0)
+
+
+def _cyl_state(n, seed=7, **kw):
+    P = synth.ring(n, seed)
+    prm = orc.Params(**{**dict(theta=0.5, n_g=64, n_leaf=8, order=2, r_coll=2e-5, key_frame=1), **kw})
+    return P, prm, orc.rebuild(P, prm)
+
+
+def test_cyl_lists_brute_force_periodic_definition():
+    """Same ancestor definition as the Cartesian case, with the opening test
+    written out independently: phi gap the shorter way round a period of
+    floor(2 pi S) cells, contact clause ((r_coll / r_min + 2e-8) S)^2."""
+    P, prm, S = _cyl_state(64, n_g=8, n_leaf=2, theta=0.7)
+    t = S.tree
+    nn = len(t["level"])
+    Sg = 2097152.0 / S.L
+    period = int(np.floor(2 * np.pi * Sg))
+    rmin = np.sqrt(S.P["x"] ** 2 + S.P["y"] ** 2).min()
+    rc = (prm.r_coll / rmin + 2e-8) * Sg
+    rcq2 = rc * rc
+
+    def gap(lo_c, hi_c, lo_g, hi_g, periodic):
+        if lo_c > hi_g:
+            d = lo_c - hi_g - 1
+            w = lo_g + period - hi_c - 1
+        elif lo_g > hi_c:
+            d = lo_g - hi_c - 1
+            w = lo_c + period - hi_g - 1
+        else:
+            return 0
+        return max(0, min(d, w)) if periodic else max(0, d)
+
+    def opened(g, c):
+        d2 = sum(gap(int(S.qlo[c][a]), int(S.qhi[c][a]), int(S.qlo[g][a]), int(S.qhi[g][a]), a == 0) ** 2
+                 for a in range(3))
+        s = 2.0 ** (21 - int(t["level"][c]))
+        return prm.theta * prm.theta * float(d2) < s * s or float(d2) <= rcq2
+
+    for k, g in enumerate(S.groups):
+        Pset, Cset = [], []
+        for c in range(nn):
+            anc, a = [], t["parent"][c]
+            while a >= 0:
+                anc.append(a); a = t["parent"][a]
+            if not all(opened(g, a) for a in anc):
+                continue
+            if opened(g, c):
+                if t["nchild"][c] == 0:
+                    Pset.append(c)
+            else:
+                Cset.append(c)
+        L = S.lists
+        key = lambda c: t["begin"][c]
+        assert list(L["P"][L["pp_off"][k]:L["pp_off"][k + 1]]) == sorted(Pset, key=key)
+        assert list(L["C"][L["pc_off"][k]:L["pc_off"][k + 1]]) == sorted(Cset, key=key)
+
+
+def test_cyl_contacts_always_particles_and_seam_neighbours_near():
+    """Every particle within r_coll of a group particle is in the group's
+    particle list, including pairs across the phi = 0 / 2 pi seam."""
+    n = 3000
+    rng = np.random.default_rng(43)
+    phi = np.concatenate([rng.uniform(0, 3e-3, n // 2), rng.uniform(2 * np.pi - 3e-3, 2 * np.pi, n - n // 2)])
+    r = rng.uniform(0.9995, 1.0005, n)
+    P = {"x": r * np.cos(phi), "y": r * np.sin(phi), "z": rng.normal(0, 1e-5, n), "vx": np.zeros(n),
+         "vy": np.zeros(n), "vz": np.zeros(n), "m": np.full(n, 1e-12), "id": np.arange(n)}
+    prm = orc.Params(theta=0.6, n_g=32, n_leaf=4, order=2, r_coll=5e-5, key_frame=1)
+    S = orc.rebuild(P, prm)
+    X = np.stack([S.P["x"], S.P["y"], S.P["z"]], 1)
+    t = S.tree
+    across = 0
+    for k in range(len(S.groups)):
+        g = S.groups[k]; gb, ge = t["begin"][g], t["end"][g]
+        inP = np.zeros(n, bool)
+        for b, e, kind, c in _ranges(S, k):
+            if kind == "P":
+                inP[b:e] = True
+        d = np.sqrt(((X[gb:ge, None, :] - X[None, :, :]) ** 2).sum(-1)).min(0)
+        assert np.all(inP[d <= prm.r_coll])
+        ph = np.mod(np.arctan2(X[:, 1], X[:, 0]), 2 * np.pi)
+        if ph[gb:ge].max() < 1.0:
+            across += int(np.sum((d <= prm.r_coll) & (ph > np.pi)))
+    assert across > 0  # the case tested really has contact pairs across the seam
+
+
+def test_cyl_theta_zero_tree_force_equals_direct_sum():
+    P, prm, S = _cyl_state(600, theta=0.0, n_g=32, r_coll=0.0, order=1)
+    a = orc.tree_forces(S, prm)
+    d = orc.direct(S.P, prm)
+    assert np.array_equal(a, d)
