@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the workload's preset launch settings")
+    ap.add_argument("--key-frame", type=int, default=None, choices=[0, 1],
+                    help="tree frame: 0 Cartesian, 1 cylindrical (default: the workload's)")
+    ap.add_argument("--n-g", type=int, default=None, help="override the group size limit")
+    ap.add_argument("--n-leaf", type=int, default=None, help="override the leaf size limit")
     return ap.parse_args()
 
 
@@ -132,10 +137,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def recorded_traffic(kernel: str, workload: str, n: int):
+def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, n_g: int):
     """DRAM bytes per launch of the force kernel from the committed ncu
-    capture, if it was taken on this workload with the kernel source as it
-    is now (else None)."""
+    capture, if it was taken on this workload (size, frame, n_g) with the
+    kernel source as it is now (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -146,7 +151,8 @@ def recorded_traffic(kernel: str, workload: str, n: int):
     for f in ("force32.cu", "force_common.cuh"):
         with open(os.path.join(ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n:
+    if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n
+            or rec.get("key_frame") != key_frame or rec.get("n_g") != n_g):
         return None
     return rec["bytes_per_launch"]
 
@@ -252,6 +258,12 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pr = synth.PRESETS[args.workload]
     prm = dict(pr["params"])
+    if args.key_frame is not None:
+        prm["key_frame"] = args.key_frame
+    if args.n_g is not None:
+        prm["n_g"] = args.n_g
+    if args.n_leaf is not None:
+        prm["n_leaf"] = args.n_leaf
     offsets = None
     if pr["kind"] == "patches":
         parts, sizes = synth.patches(seed=replica_seed(pr["seed"], rank))
@@ -266,9 +278,9 @@ def run_ours(args):
     ctx = bh.Context(offsets=offsets, **prm)
     D = bh.Particles(P)
     tuning = None
-    if pr["kind"] == "patches" or args.autotune:
-        # the batched configuration: autotuned launch settings and n_g, one
-        # persistent launch per step, list-reusing steps as CUDA graphs
+    if (pr.get("autotune") and not args.no_autotune) or args.autotune:
+        # autotuned launch settings and n_g (the batched configuration also
+        # issues its list-reusing steps as CUDA graphs)
         tuned_ms = ctx.bh_autotune(D)
         if pr["kind"] == "patches":
             ctx.bh_set_tuning(graph=1)
@@ -324,7 +336,8 @@ def run_ours(args):
     peak = fp32_peak_tflops(SM_MAX_MHZ)
     roofline = {"kernel": "k_force32" if prm["precision"] == 1 else "k_force64", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
-                "traffic": recorded_traffic("k_force32", args.workload, n) if prm["precision"] == 1 else None,
+                "traffic": recorded_traffic("k_force32", args.workload, n, prm.get("key_frame", 0), prm["n_g"])
+                if prm["precision"] == 1 else None,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
                 "flops_per_interaction": {"pp": flops_pp, "pc": flops_pc},
                 "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}
@@ -333,14 +346,17 @@ def run_ours(args):
         roofline["frac_at_median_clock"] = achieved / roofline["peak_at_median_clock"] if achieved else None
 
     # force error of this path against the plain FP64 GPU path on the same lists
-    err = None
+    err = fp64 = None
     if not args.no_error and prm["precision"] == 1:
         Pnow = D.numpy()
         ctxe = bh.Context(offsets=offsets, **dict(prm, precision=0))
         De = bh.Particles(Pnow)
         ctxe.bh_build_tree(De)
         ctxe.bh_make_lists()
+        ctxe.bh_set_timing(True)
         ctxe.bh_compute_forces(De, bh.BH_FORCE_TREE_ONLY)
+        ms64, _ = ctxe.bh_get_timing(reset=True)
+        ce = ctxe.bh_get_counters()
         ctx32 = bh.Context(offsets=offsets, **prm)
         D32 = bh.Particles(De.numpy())
         ctx32.bh_build_tree(D32)
@@ -372,6 +388,11 @@ def run_ours(args):
                "n_above_gate": int(above.sum()),
                "largest_abs_a_over_median_above_gate": float(rn[above].max() / np.median(rn)) if above.any() else None,
                "gate": gate, "gate_used": used, "gate_passed": passed}
+        # the plain FP64 kernel on the same particles and lists, for the ratio
+        rate64 = (ce["n_pp"] + ce["n_pc"]) / (ms64 / 1e3)
+        rate32 = (pp + pc) / args.steps / (force_ms / force_launches / 1e3)
+        fp64 = {"kernel": "k_force64", "kernel_ms": ms64, "interactions_per_s": rate64,
+                "fp32_kernel_interactions_per_s": rate32, "fp32_over_fp64": rate32 / rate64}
         for x in (ctxe, ctx32):
             x.close()
         del De, D32
@@ -429,6 +450,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prm["precision"] == 1 else "f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "N": n, "theta": prm["theta"], "n_g": prm["n_g"],
+                           "n_leaf": prm["n_leaf"],
+                           "key_frame": "cylindrical (phi, r, z)" if prm.get("key_frame", 0) == 1 else "Cartesian",
                            "order": prm["order"], "rebuild_every": prm["rebuild_every"],
                            "precision": "FP32 group-relative forces, FP64 positions/velocities/updates"
                            if prm["precision"] == 1 else "FP64",
@@ -440,7 +463,7 @@ def run_ours(args):
                 "interactions_per_step": inter / args.steps,
                 "pct_fp32_peak": 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
-                "force_error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk,
                 **({"load_balance_busy_fraction": balance} if balance is not None else {})}
         print(json.dumps(line), flush=True)

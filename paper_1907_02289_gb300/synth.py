@@ -110,9 +110,11 @@ PRESETS = {
     # ring 2^24, FP32 group-relative vs FP64 on the same lists
     "ring16m_fp32": dict(n=1 << 24, seed=2, kind="ring", params=_ring_params(0.5, 128, 1, 10)),
     # 64 independent patches, 20 steps
-    "patches64": dict(n=None, seed=3, kind="patches", params=_ring_params(0.5, 128, 1, 20)),
-    # ring 2^26, FP32 group-relative forces, theta 0.4, 10 steps
-    "ring64m_fp32": dict(n=1 << 26, seed=4, kind="ring", params=_ring_params(0.4, 128, 1, 10)),
+    "patches64": dict(n=None, seed=3, kind="patches", autotune=True, params=_ring_params(0.5, 128, 1, 20)),
+    # ring 2^26, FP32 group-relative forces, theta 0.4, 10 steps; the paper's
+    # cylindrical tree (Sec. 4.3) and an autotuned n_g
+    "ring64m_fp32": dict(n=1 << 26, seed=4, kind="ring", autotune=True,
+                         params=dict(_ring_params(0.4, 128, 1, 10), key_frame=1)),
 }
 
 
