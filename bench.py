@@ -67,6 +67,7 @@ def parse():
                     help="tree frame: 0 Cartesian, 1 cylindrical (default: the workload's)")
     ap.add_argument("--n-g", type=int, default=None, help="override the group size limit")
     ap.add_argument("--n-leaf", type=int, default=None, help="override the leaf size limit")
+    ap.add_argument("--tune", default="", help="launch settings to apply, e.g. chunk=64,order_window=8192")
     return ap.parse_args()
 
 
@@ -137,10 +138,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, n_g: int):
+def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning: dict):
     """DRAM bytes per launch of the force kernel from the committed ncu
-    capture, if it was taken on this workload (size, frame, n_g) with the
-    kernel source as it is now (else None)."""
+    capture, if it was taken on this workload (size, frame, n_g and launch
+    settings) with the kernel source as it is now (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -152,7 +153,10 @@ def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, n_g: in
         with open(os.path.join(ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n
-            or rec.get("key_frame") != key_frame or rec.get("n_g") != n_g):
+            or rec.get("key_frame") != key_frame):
+        return None
+    if any(rec.get("tuning", {}).get(k) != tuning.get(k) for k in ("n_g", "chunk", "warps", "sched", "order_window",
+                                                                    "order_by_cost")):
         return None
     return rec["bytes_per_launch"]
 
@@ -286,6 +290,9 @@ def run_ours(args):
             ctx.bh_set_tuning(graph=1)
         tuning = dict(ctx.bh_get_tuning(), autotuned_step_ms=tuned_ms)
         prm["n_g"] = tuning["n_g"]
+    if args.tune:
+        ctx.bh_set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+        tuning = dict(ctx.bh_get_tuning(), **({"autotuned_step_ms": tuning["autotuned_step_ms"]} if tuning else {}))
     # initial evaluation + warm-up steps (evaluations 0..W); timed steps then
     # start on a list-constructing evaluation when W = 3 and rebuild_every = 4
     ctx.bh_step(D, args.warmup)
@@ -336,8 +343,8 @@ def run_ours(args):
     peak = fp32_peak_tflops(SM_MAX_MHZ)
     roofline = {"kernel": "k_force32" if prm["precision"] == 1 else "k_force64", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
-                "traffic": recorded_traffic("k_force32", args.workload, n, prm.get("key_frame", 0), prm["n_g"])
-                if prm["precision"] == 1 else None,
+                "traffic": recorded_traffic("k_force32", args.workload, n, prm.get("key_frame", 0),
+                                            ctx.bh_get_tuning()) if prm["precision"] == 1 else None,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
                 "flops_per_interaction": {"pp": flops_pp, "pc": flops_pc},
                 "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}

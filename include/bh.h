@@ -231,7 +231,9 @@ int bh_get_tuning(bh_ctx* ctx, bh_tuning* t);
  * time, one knob at a time (schedule, then warps in {2, 4, 8}, chunk in
  * {32, 64, 96}, order_window in {0, 2048, 8192}); then n_g in
  * {64, 96, 128, 192, 256} (those >= n_leaf) by the cost of one step, force
- * time plus list-build time / rebuild_every.  Like a list build it reorders the particle arrays; on
+ * time plus list-build time / rebuild_every; then every pair of chunk and
+ * order_window on the chosen n_g.  Each candidate keeps the best of three timed
+ * evaluations, after untimed ones following each list build.  Like a list build it reorders the particle arrays; on
  * return the lists are built with the chosen settings, ax..az hold the
  * acceleration at the current positions, and the list-reuse schedule starts
  * afresh.  best_ms (may be NULL) receives the chosen setting's step cost.

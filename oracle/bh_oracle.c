@@ -30,7 +30,10 @@
  *  - Eq. (1) read as an acceleration, with Plummer softening eps added to the
  *    gravity part and gravity held at its r_coll value inside r_coll;
  *  - cell term: monopole about the centre of mass (Sec. 5.1) plus the
- *    textbook traceless quadrupole (order 2).
+ *    textbook traceless quadrupole (order 2);
+ *  - cylindrical frame (Sec. 4.3): keys, tree and opening test on
+ *    (phi, r, z), phi from a fixed-operation atan (see orc_phi()), periodic
+ *    in phi, contact clause from r_coll / r_min (see orc_cyl_geometry()).
  * Parity pins for every function live in tests/test_oracle_*.py.
  * Parity unpinned: the values of kappa and eta (the paper prints only the
  * radial restitution coefficient 0.5) and the accuracy of the tree force at

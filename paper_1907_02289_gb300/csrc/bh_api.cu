@@ -346,20 +346,30 @@ int autotune(Ctx* c, bh_particles* p, double* best_ms) {
     BH_TRY(time_ms(c, build, &tb));
     double best_f = 1e300;
     bh_tuning best = cur;
+    // the first force evaluations after a list build run slower (fresh lists
+    // and particle order), so each phase starts with untimed evaluations and
+    // every candidate keeps the best of three
+    auto settle = [&]() -> int {
+        for (int w = 0; w < 2; ++w) BH_TRY(force());
+        return BH_OK;
+    };
     auto try_force = [&](const bh_tuning& t) -> int {
         const bool reorder = t.chunk != c->tune.chunk || t.order_window != c->tune.order_window;
         apply_tuning(c, &t);
         if (reorder && c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
-        double ms = 0.0, ms2 = 0.0;
-        BH_TRY(time_ms(c, force, &ms));
-        BH_TRY(time_ms(c, force, &ms2));
-        if (ms2 < ms) ms = ms2;
+        double ms = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            double m = 0.0;
+            BH_TRY(time_ms(c, force, &m));
+            if (m < ms) ms = m;
+        }
         if (ms < best_f) {
             best_f = ms;
             best = t;
         }
         return BH_OK;
     };
+    BH_TRY(settle());
     if (c->prm.precision == BH_PREC_FP32) {
         for (int sc = BH_SCHED_GRID; sc <= BH_SCHED_DYNAMIC; ++sc) {
             bh_tuning t = best;
@@ -395,11 +405,14 @@ int autotune(Ctx* c, bh_particles* p, double* best_ms) {
             bh_tuning t = best;
             t.n_g = cand[q];
             apply_tuning(c, &t);
-            double b = 0.0, f = 0.0, f2 = 0.0;
+            double b = 0.0, f = 1e300;
             BH_TRY(time_ms(c, build, &b));
-            BH_TRY(time_ms(c, force, &f));
-            BH_TRY(time_ms(c, force, &f2));
-            if (f2 < f) f = f2;
+            BH_TRY(settle());
+            for (int rep = 0; rep < 3; ++rep) {
+                double m = 0.0;
+                BH_TRY(time_ms(c, force, &m));
+                if (m < f) f = m;
+            }
             const double step = f + b / c->prm.rebuild_every;
             if (step < best_step) {
                 best_step = step;
@@ -408,6 +421,28 @@ int autotune(Ctx* c, bh_particles* p, double* best_ms) {
         }
         best = best_ng;
         if (best_ms) *best_ms = best_step;
+    }
+    // (3) the i-chunk and the order window together, on the chosen n_g (the
+    // best chunk depends on the group sizes -- groups of 2 x 96 run uniform
+    // chunks -- and on the window)
+    if (c->prm.precision == BH_PREC_FP32) {
+        apply_tuning(c, &best);
+        double b = 0.0;
+        BH_TRY(time_ms(c, build, &b));
+        BH_TRY(settle());
+        best_f = 1e300;
+        BH_TRY(try_force(best));
+        const double f_best = best_f;
+        const int chunks[3] = {32, 64, 96}, windows[3] = {0, 2048, 8192};
+        const bh_tuning base = best;
+        for (int q = 0; q < 3; ++q)  // all pairs: the best chunk depends on the window
+            for (int w = 0; w < 3; ++w) {
+                bh_tuning t = base;
+                t.chunk = chunks[q];
+                t.order_window = windows[w];
+                BH_TRY(try_force(t));
+            }
+        if (best_ms) *best_ms += best_f - f_best;
     }
     best.graph = graph;
     apply_tuning(c, &best);
