@@ -41,6 +41,11 @@ sys.path.insert(0, ROOT)
 # separation 24 (23 without softening, where the + eps^2 is not issued),
 # particle-cell with quadrupole 49, monopole only 18.
 FLOPS_PP, FLOPS_PP_NO_EPS, FLOPS_PC2, FLOPS_PC1 = 24, 23, 49, 18
+# The plain FP64 kernel (absolute coordinates, rsqrt not counted): pp 18
+# (3 sub, r^2 5, + eps^2 1, 3 mul, 3 FMA), pc with quadrupole 53, monopole 21.
+FLOPS64_PP, FLOPS64_PC2, FLOPS64_PC1 = 18, 53, 21
+# FP64 peak: the nominal 1.25 TFLOP/s of this part (no measured figure).
+FP64_PEAK_TFLOPS = 1.25
 # The paper's convention (Sec. 5.1): 49 per particle-particle, 31 per particle-cell.
 PAPER_PP, PAPER_PC = 49, 31
 NUM_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -334,21 +339,27 @@ def run_ours(args):
     inter = pp + pc
     elapsed = max_over_ranks(elapsed, "cuda")
     value = world * inter / elapsed
-    flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
-    flops_pp = FLOPS_PP_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP
+    if prm["precision"] == 1:
+        flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
+        flops_pp = FLOPS_PP_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP
+    else:
+        flops_pc = FLOPS64_PC2 if prm["order"] >= 2 else FLOPS64_PC1
+        flops_pp = FLOPS64_PP
     flops = pp * flops_pp + pc * flops_pc
     # force launches timed by the library (graph-captured steps are not timed
     # per launch): mean flops of an evaluation / mean time of a timed launch
     achieved = (flops / args.steps) / (force_ms / force_launches / 1e3) / 1e12 if force_ms > 0 else None
-    peak = fp32_peak_tflops(SM_MAX_MHZ)
-    roofline = {"kernel": "k_force32" if prm["precision"] == 1 else "k_force64", "bound": "alu",
+    f32 = prm["precision"] == 1
+    peak = fp32_peak_tflops(SM_MAX_MHZ) if f32 else FP64_PEAK_TFLOPS
+    roofline = {"kernel": "k_force32" if f32 else "k_force64", "bound": "alu" if f32 else "fp64",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": recorded_traffic("k_force32", args.workload, n, prm.get("key_frame", 0),
                                             ctx.bh_get_tuning()) if prm["precision"] == 1 else None,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)" if f32
+                else "nominal FP64 rate of the part (1.25 TFLOP/s), not measured",
                 "flops_per_interaction": {"pp": flops_pp, "pc": flops_pc},
                 "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}
-    if clk.get("sm_mhz"):
+    if clk.get("sm_mhz") and f32:
         roofline["peak_at_median_clock"] = fp32_peak_tflops(clk["sm_mhz"])
         roofline["frac_at_median_clock"] = achieved / roofline["peak_at_median_clock"] if achieved else None
 
@@ -468,7 +479,7 @@ def run_ours(args):
                            **({"tuning": tuning} if tuning else {})},
                 "particle_steps_per_s": world * n * args.steps / elapsed,
                 "interactions_per_step": inter / args.steps,
-                "pct_fp32_peak": 100 * roofline["frac"] if roofline["frac"] else None,
+                ("pct_fp32_peak" if f32 else "pct_fp64_peak"): 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
                 "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk,
