@@ -174,7 +174,13 @@ int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp
                  int64_t* n_pc_entries, int64_t* n_list_particles);
 
 /* Read-backs into host buffers (n, n_nodes, n_groups, ... entries).
- * bh_get_root writes one box per patch: lo3[3 q + a], L[q]. */
+ * bh_get_keys: the sorted keys and perm[i] = index, before the last sort, of
+ * the particle now at i.  bh_get_root writes one box per patch: lo3[3 q + a],
+ * L[q] (in (phi, r, z) for the cylindrical frame).  bh_get_moments: M[node],
+ * centre of mass c3[a * n_nodes + node], traceless quadrupole
+ * Q6[6 node + {xx, yy, zz, xy, xz, yz}]; on the FP64 path the FP64 moments,
+ * on the FP32 path the FP32 records widened to FP64 (centre = hi + lo).  bh_get_lists: CSR offsets (n_groups + 1) and
+ * node ids, particle list = opened leaves, cell list = accepted nodes. */
 int bh_get_keys(bh_ctx* ctx, uint64_t* keys, uint32_t* perm);
 int bh_get_root(bh_ctx* ctx, double* lo3, double* L);
 int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,
@@ -185,9 +191,10 @@ int bh_get_lists(bh_ctx* ctx, int64_t* pp_off, int32_t* pp_ids, int64_t* pc_off,
 int bh_get_counters(bh_ctx* ctx, bh_counters* out);
 
 /* Measurement hooks.  bh_set_timing(ctx, 1) makes every force-kernel launch
- * record a pair of CUDA events on the context's stream; bh_get_timing
- * synchronises the stream and returns the summed kernel time (ms) and the
- * number of timed launches, clearing them when reset != 0. */
+ * record a pair of CUDA events on the context's stream (launches inside a
+ * captured graph step are not timed); bh_get_timing synchronises the stream
+ * and returns the summed kernel time (ms) and the number of timed launches,
+ * clearing them when reset != 0. */
 int bh_set_timing(bh_ctx* ctx, int enable);
 int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset);
 

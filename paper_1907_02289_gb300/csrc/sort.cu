@@ -396,11 +396,10 @@ int stage_sort(Ctx* c) {
     uint32_t h[8 * kRadix];
     BH_CUDA(c, cudaMemcpyAsync(h, c->digit_hist.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     BH_CUDA(c, cudaStreamSynchronize(c->stream));
-    static bool attr_set = false;
     const int smem = (int)sizeof(DownSmem);
-    if (!attr_set) {
+    if (c->sort_attr_device != c->device) {  // once per device
         BH_CUDA(c, cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_set = true;
+        c->sort_attr_device = c->device;
     }
     for (int pass = 0; pass < 8; ++pass) {
         bool trivial = false;
