@@ -479,6 +479,7 @@ def run_ours(args):
                            **({"tuning": tuning} if tuning else {})},
                 "particle_steps_per_s": world * n * args.steps / elapsed,
                 "interactions_per_step": inter / args.steps,
+                "pp_pc_per_step": [pp / args.steps, pc / args.steps],
                 ("pct_fp32_peak" if f32 else "pct_fp64_peak"): 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
                 "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
