@@ -189,6 +189,10 @@ int evaluate(Ctx* c, bh_particles* p) {
     } else {
         BH_TRY(stage_moments(c, p));
     }
+    if (c->want_pos_event) {  // x..id are final for this step from here on
+        BH_CUDA(c, cudaEventRecord(c->pos_event, c->stream));
+        c->pos_event_recorded = true;
+    }
     BH_TRY(stage_force(c, p, true));
     c->k_eval++;
     c->evals_since_build++;
@@ -206,6 +210,12 @@ bool same_arrays(const bh_particles& a, const bh_particles& b) {
 int graph_reuse_step(Ctx* c, bh_particles* p) {
     const double dt = c->prm.dt;
     if (!c->graph_ok || !same_arrays(c->graph_p, *p)) {
+        // inside the graph the contact pass cannot grow its buffer: leave room
+        // for twice the candidates of the last eager evaluation
+        if (c->prm.precision == BH_PREC_FP32 && c->prm.r_coll > 0.0) {
+            const size_t want = (size_t)(2 * c->n_contacts + 65536);
+            if (c->contacts.cap < want) BH_TRY(grow(c, c->contacts, want, "contact pairs"));
+        }
         // capture on a private stream (the legacy default stream cannot be
         // captured); the graph is then launched on the context's stream
         if (!c->cap_stream) BH_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -531,6 +541,8 @@ int bh_destroy(bh_ctx* ctx) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->pos_event) cudaEventDestroy(c->pos_event);
     cudaFree(c->d_status);
     cudaFree(c->d_box);
     cudaFree(c->d_small);
@@ -610,6 +622,7 @@ int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps) {
         c->have_acc = true;
     }
     for (int s = 0; s < nsteps; ++s) {
+        c->pos_event_recorded = false;  // only the last step's evaluation counts
         if (c->tune.graph && c->have_lists && c->k_eval % c->prm.rebuild_every != 0) {
             BH_TRY(bh::graph_reuse_step(c, p));
             continue;
@@ -707,10 +720,31 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     for (int a = 0; a < ncopy; ++a)
         BH_CUDA(c, cudaMemcpyAsync(ds[a], hs[a], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     BH_CUDA(c, cudaMemcpyAsync(d.id, h->id, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-    BH_TRY(bh_step(ctx, &d, nsteps));
-    for (int a = 0; a < 10; ++a)
+    if (!c->copy_stream) BH_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->pos_event) BH_CUDA(c, cudaEventCreateWithFlags(&c->pos_event, cudaEventDisableTiming));
+    c->want_pos_event = true;
+    c->pos_event_recorded = false;
+    const int rc = bh_step(ctx, &d, nsteps);
+    c->want_pos_event = false;
+    BH_TRY(rc);
+    // positions, masses and ids: copied back on the second stream as soon as
+    // the last evaluation has fixed them (while its force kernel runs);
+    // velocities and accelerations after the final kick
+    const bool early = c->pos_event_recorded;
+    const int late_from = early ? 3 : 0;
+    if (early) {
+        BH_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->pos_event, 0));
+        const int pos[4] = {0, 1, 2, 6};
+        for (int a : pos)
+            BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream));
+        BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->copy_stream));
+    }
+    for (int a = late_from; a < 10; ++a) {
+        if (early && a == 6) continue;
         BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (!early) BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    if (early) BH_CUDA(c, cudaStreamSynchronize(c->copy_stream));
     return bh_sync(ctx);
 }
 

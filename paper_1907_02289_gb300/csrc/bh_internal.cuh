@@ -145,6 +145,12 @@ struct Ctx {
     bool capturing = false;              // issuing work into a stream capture
     cudaGraphExec_t graph_exec = nullptr;  // the captured list-reusing step
     cudaStream_t cap_stream = nullptr;   // private stream the step is captured on
+    // host-buffer stepping: positions, masses and ids are final once the last
+    // evaluation's tree/moments stage is enqueued; their copy back overlaps
+    // the force kernel on a second stream
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pos_event = nullptr;
+    bool want_pos_event = false, pos_event_recorded = false;
     bool graph_ok = false;               // graph_exec matches the current lists and arrays
     bh_particles graph_p{};              // particle arrays the graph was captured with
     int64_t graph_launches = 0;          // kernels in the graph

@@ -92,11 +92,17 @@ def test_tuning_validation(ring):
     assert t == dict(n_g=64, chunk=96, warps=4, sched=2, order_by_cost=1, graph=0, order_window=0)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_graph_steps_equal_eager_steps(precision):
+@pytest.mark.parametrize("precision,dense", [(0, False), (1, False), (1, True)])
+def test_graph_steps_equal_eager_steps(precision, dense):
+    """dense: ~1e5 contact candidates, far above the contact buffer's initial
+    size, so the graph steps rely on the room left before capture."""
     from paper_1907_02289_gb300 import bh
-    P = synth.ring(20000, 22)
-    prm = _prm(precision=precision)
+    if dense:
+        P = synth.ring(6000, 9, r_in=0.99995, r_out=1.00005, phi_max=4e-4, sigma_z=5e-6)
+        prm = _prm(precision=precision, n_g=32, theta=0.6)
+    else:
+        P = synth.ring(20000, 22)
+        prm = _prm(precision=precision)
     outs = []
     for graph in (0, 1):
         ctx = bh.Context(**prm)
