@@ -327,6 +327,8 @@ def run_ours(args):
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     force_ms, force_launches = ctx.bh_get_timing(reset=True)
+    free_b, total_b = torch.cuda.mem_get_info()
+    mem_used_gb = (total_b - free_b) / 1e9  # device memory in use after the timed steps (all holders)
     balance = None
     if ctx.bh_get_tuning()["sched"] != bh.BH_SCHED_GRID and prm["precision"] == 1:
         try:
@@ -483,7 +485,7 @@ def run_ours(args):
                 ("pct_fp32_peak" if f32 else "pct_fp64_peak"): 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
                 "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "device_memory_used_gb": mem_used_gb,
                 **({"load_balance_busy_fraction": balance} if balance is not None else {})}
         print(json.dumps(line), flush=True)
     if world > 1:

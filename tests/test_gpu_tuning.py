@@ -94,12 +94,13 @@ def test_tuning_validation(ring):
 
 @pytest.mark.parametrize("precision,dense", [(0, False), (1, False), (1, True)])
 def test_graph_steps_equal_eager_steps(precision, dense):
-    """dense: ~1e5 contact candidates, far above the contact buffer's initial
-    size, so the graph steps rely on the room left before capture."""
+    """dense: ~9e4 contact candidates (4.4 contacts per particle), above the
+    contact buffer's initial size of 65,536 pairs, so the graph steps rely on
+    the room left before capture."""
     from paper_1907_02289_gb300 import bh
     if dense:
-        P = synth.ring(6000, 9, r_in=0.99995, r_out=1.00005, phi_max=4e-4, sigma_z=5e-6)
-        prm = _prm(precision=precision, n_g=32, theta=0.6)
+        P = synth.ring(20000, 9, r_in=0.99995, r_out=1.00005, phi_max=0.033, sigma_z=1e-5)
+        prm = _prm(precision=precision)
     else:
         P = synth.ring(20000, 22)
         prm = _prm(precision=precision)
