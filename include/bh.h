@@ -27,6 +27,10 @@
  *    checked at the next synchronising call (or bh_sync).
  *  - bh_get_* read-back functions copy into CALLER-OWNED HOST buffers sized
  *    from bh_get_sizes, and synchronise the stream.
+ *  - A context is used by one host thread at a time (calls on one context
+ *    are not synchronised against each other); separate contexts are
+ *    independent.  Make every call with the device current that was
+ *    current at bh_create (the context's buffers live there).
  */
 #ifndef BH_H
 #define BH_H

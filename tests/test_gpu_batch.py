@@ -174,3 +174,25 @@ def test_bad_offsets_rejected():
     with pytest.raises(bh.BHError) as e:
         ctx.bh_build_tree(D)
     assert e.value.code == bh.BH_E_INVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tiny_and_uneven_patches(prec):
+    """Patches of 1, 2 and 3 particles beside a large one: the forest, the
+    segmented sort and the per-patch walk still give each patch its own
+    result (a lone particle feels nothing from the tree)."""
+    from paper_1907_02289_gb300 import bh
+    sizes = [1, 5000, 2, 3, 4097]
+    parts = [synth.ring(n, 800 + q, phi_max=2 * math.pi * max(n, 64) / (1 << 20), id0=sum(sizes[:q]))
+             for q, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    prm = _params(precision=prec)
+    ctx, D = _run(_concat(parts), prm, offsets=off)
+    a = accel_of(D)
+    out = D.numpy()
+    assert np.all(a[0] == 0.0)
+    for q, p in enumerate(parts):
+        sc, sD = _run(p, prm)
+        so = sD.numpy()
+        assert np.array_equal(out["id"][off[q]:off[q + 1]], so["id"])
+        np.testing.assert_allclose(a[off[q]:off[q + 1]], accel_of(sD), rtol=1e-13, atol=0)
