@@ -14,10 +14,11 @@
 // Gravity inside r_coll (Eq. 1) is G m_j r / (r_coll^2 + eps^2)^(3/2), so
 // max(r^2, r_coll^2) + eps^2 in the fast loop gives it for every pair (and
 // 0 for i = j).  Pairs that may be in contact are queued per warp and
-// appended to a global list; a separate FP64 kernel adds their contact term
+// appended to a global list; a separate FP64 pass adds their contact term
 // of Eq. (1) in the oracle's operation order (the r <= r_coll decision
 // included), with every lane busy -- FP64 inside the warp loop would leave
-// 31 lanes idle at 1/64 of the FP32 rate.
+// 31 lanes idle at 1/64 of the FP32 rate -- summing each particle's terms
+// in fixed point so that the result does not depend on the list's order.
 //
 // Summation: FP32 partial sums per tile (even and odd list entries apart),
 // folded after every tile into a compensated (TwoSum) hi/lo accumulator in
@@ -31,10 +32,18 @@
 // and the pair (j, j+1) is evaluated with packed f32x2 instructions (FADD2,
 // FFMA2, FMUL2) against the i-particle held as (x_i, x_i), which halves the
 // issue slots per interaction.  The next tile is gathered with cp.async
-// while the current one is evaluated.  Groups are processed in order of
-// size class so that warps running side by side execute the same code.  The
-// group's own particles are evaluated first in a phase that excludes i = j;
-// the expanded list holds only the other particles.
+// while the current one is evaluated.  Groups larger than the i-chunk (at
+// most 96) are evaluated chunk by chunk.  The group's own particles are
+// evaluated first in a phase that excludes i = j; the expanded list holds
+// only the other particles.
+//
+// Scheduling: groups are taken in order of size class (warps running side
+// by side execute the same code), by decreasing estimated cost within a
+// class, optionally within windows of consecutive groups; the grid is one
+// warp per group, or persistent (resident blocks only) with warps taking
+// groups round robin or from an atomic ticket counter.  Warps per block and
+// the i-chunk are runtime settings; the compile-time options below exist for
+// experiments.
 #include <algorithm>
 #include <cmath>
 
