@@ -1,0 +1,39 @@
+"""Host logic of the benchmark (no GPU): the recorded DRAM traffic is used
+only for the exact kernel source and settings it was captured with, and the
+derived FP32 peak follows the unit counts and the clock."""
+import json
+
+import bench
+
+
+def _rec():
+    return json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_force32"]
+
+
+def test_recorded_traffic_matches_only_its_configuration():
+    rec = _rec()
+    tuning = dict(rec["tuning"])
+    got = bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], tuning)
+    assert got == rec["bytes_per_launch"]
+    for key, other in (("n_g", 128), ("chunk", 64), ("order_window", 8192), ("sched", 0), ("warps", 8)):
+        t = dict(tuning, **{key: other})
+        assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], t) is None, key
+    assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"] // 2, rec["key_frame"], tuning) is None
+    assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], 1 - rec["key_frame"], tuning) is None
+    assert bench.recorded_traffic("k_force32", "patches64", rec["N"], rec["key_frame"], tuning) is None
+
+
+def test_traffic_record_follows_the_kernel_source():
+    """The committed record carries the hash of the force kernel's source as
+    it is now (a change to the kernel must retake or drop the number)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("force32.cu", "force_common.cuh"):
+        with open(bench.os.path.join(bench.ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    assert _rec()["source_sha256"] == h.hexdigest()
+
+
+def test_fp32_peak_from_unit_counts():
+    assert abs(bench.fp32_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    assert bench.fp32_peak_tflops(1035.0) * 2 == bench.fp32_peak_tflops(2070.0)
