@@ -56,3 +56,32 @@ def test_load_fails_loudly_when_missing(tmp_path):
             bh.load(str(tmp_path / "libbh.so"))
     finally:
         bh._lib = saved
+
+
+def test_header_is_plain_c_and_struct_sizes_agree(tmp_path):
+    """bh.h compiles as C99 (a C caller needs no C++), and the sizes and
+    field offsets a C compiler gives the ABI structs are the binding's."""
+    import subprocess
+    from paper_1907_02289_gb300 import bh
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "probe.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "bh.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bh_params), sizeof(bh_particles), sizeof(bh_counters),
+           sizeof(bh_tuning), sizeof(bh_diagnostics), offsetof(bh_params, n_g), offsetof(bh_params, list_capacity));
+    return 0;
+}
+""")
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(bh.bh_params), ctypes.sizeof(bh.bh_particles), ctypes.sizeof(bh.bh_counters),
+            ctypes.sizeof(bh.bh_tuning), ctypes.sizeof(bh.bh_diagnostics), bh.bh_params.n_g.offset,
+            bh.bh_params.list_capacity.offset]
+    assert got == want
