@@ -201,7 +201,8 @@ def run_reference(args):
 
     import oracle as orc
     pr = synth.PRESETS[args.workload]
-    full_n = args.n or pr["n"]
+    # the patches have the surface density of the 2^20 ring
+    full_n = args.n or pr["n"] or (1 << 20)
     prm = dict(pr["params"])
     n_s = min(full_n, 1 << 18)
     P = oracle_sector(n_s, full_n, prm)
