@@ -444,7 +444,16 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        if offsets is None:
+        if pr["kind"] == "cube":  # small enough for the whole set, plus the direct sum
+            import oracle as orc
+            rate, inter_s, dt_s, cores = cpu_oracle_rate(P, prm)
+            op = orc.Params(**{k: v for k, v in prm.items() if k in orc.Params.__dataclass_fields__})
+            t0 = time.perf_counter()
+            orc.direct(P, op)
+            t_direct = time.perf_counter() - t0
+            what = (f"one list-constructing force evaluation of the whole {n}-particle set; direct sum "
+                    f"{n * (n - 1) / t_direct:.3e} pairs/s")
+        elif offsets is None:
             n_s = min(n, 1 << 21)
             rate, inter_s, dt_s, cores = cpu_oracle_rate(oracle_sector(n_s, n, prm), prm)
             what = (f"one list-constructing force evaluation of a {n_s}-particle ring sector at the surface "
