@@ -183,3 +183,30 @@ def test_batch_dynamic_graph_matches_single_patches():
         assert np.array_equal(out["id"][off[q]:off[q + 1]], so["id"])
         for f in ("x", "y", "z", "vx", "vy", "vz"):
             np.testing.assert_allclose(out[f][off[q]:off[q + 1]], so[f], rtol=1e-12, atol=1e-30, err_msg=f)
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_host_steps_equal_device_steps_cylindrical(graph):
+    """bh_step_host (whose copy back of positions overlaps the last force
+    kernel, or waits for the step when that step ran as a graph) gives the
+    bits of bh_step, in the cylindrical frame with the autotuned kernel."""
+    from paper_1907_02289_gb300 import bh
+    P = synth.ring(30000, 24, r_in=0.999, r_out=1.001, phi_max=0.08)
+    prm = _prm(key_frame=1)
+    outs = []
+    for host in (False, True):
+        ctx = bh.Context(**prm)
+        ctx.bh_set_tuning(graph=graph, sched=2)
+        if host:
+            H = bh.HostParticles(P, pinned=True)
+            for _ in range(6):
+                ctx.bh_step_host(H, 1)
+            outs.append({f: H.a[f].copy() for f in bh.Particles.FIELDS})
+        else:
+            D = bh.Particles(P)
+            for _ in range(6):
+                ctx.bh_step(D, 1)
+            ctx.bh_sync()
+            outs.append(D.numpy())
+    for f in bh.Particles.FIELDS:
+        assert np.array_equal(outs[0][f], outs[1][f]), f
