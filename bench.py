@@ -39,8 +39,11 @@ sys.path.insert(0, ROOT)
 # FP32 flops per interaction of the force kernel (FFMA/FFMA2 lane = 2,
 # FADD/FMUL = 1; rsqrt not counted): particle-particle with the two-float
 # separation 24 (23 without softening, where the + eps^2 is not issued),
+# particle-particle with a far list particle (single-float separation) 18
+# (17 without softening: its r^2 chain adds eps^2 = 0, not counted),
 # particle-cell with quadrupole 49, monopole only 18.
 FLOPS_PP, FLOPS_PP_NO_EPS, FLOPS_PC2, FLOPS_PC1 = 24, 23, 49, 18
+FLOPS_PP_FAR, FLOPS_PP_FAR_NO_EPS = 18, 17
 # The plain FP64 kernel (absolute coordinates, rsqrt not counted): pp 18
 # (3 sub, r^2 5, + eps^2 1, 3 mul, 3 FMA), pc with quadrupole 53, monopole 21.
 FLOPS64_PP, FLOPS64_PC2, FLOPS64_PC1 = 18, 53, 21
@@ -143,6 +146,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# Sources whose change invalidates a recorded traffic figure: the force
+# kernel and the list expansion (which fixes the order the kernel reads).
+TRAFFIC_SOURCES = ("force32.cu", "force_common.cuh", "walk.cu")
+
+
 def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning: dict):
     """DRAM bytes per launch of the force kernel from the committed ncu
     capture, if it was taken on this workload (size, frame, n_g and launch
@@ -154,7 +162,7 @@ def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning:
     except (OSError, KeyError, ValueError):
         return None
     h = hashlib.sha256()
-    for f in ("force32.cu", "force_common.cuh"):
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n
@@ -313,7 +321,7 @@ def run_ours(args):
     ctx.bh_set_timing(True)
     ctx.bh_get_timing(reset=True)
     c0 = ctx.bh_get_counters()
-    inter = pp = pc = 0
+    inter = pp = pc = pp_far = 0
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -323,6 +331,7 @@ def run_ours(args):
         c = ctx.bh_get_counters()
         pp += c["n_pp"]
         pc += c["n_pc"]
+        pp_far += c["n_pp_far"]
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -345,10 +354,11 @@ def run_ours(args):
     if prm["precision"] == 1:
         flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
         flops_pp = FLOPS_PP_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP
+        flops_far = FLOPS_PP_FAR_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP_FAR
     else:
         flops_pc = FLOPS64_PC2 if prm["order"] >= 2 else FLOPS64_PC1
-        flops_pp = FLOPS64_PP
-    flops = pp * flops_pp + pc * flops_pc
+        flops_pp = flops_far = FLOPS64_PP
+    flops = (pp - pp_far) * flops_pp + pp_far * flops_far + pc * flops_pc
     # force launches timed by the library (graph-captured steps are not timed
     # per launch): mean flops of an evaluation / mean time of a timed launch
     achieved = (flops / args.steps) / (force_ms / force_launches / 1e3) / 1e12 if force_ms > 0 else None
@@ -360,7 +370,7 @@ def run_ours(args):
                                             ctx.bh_get_tuning()) if prm["precision"] == 1 else None,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)" if f32
                 else "nominal FP64 rate of the part (1.25 TFLOP/s), not measured",
-                "flops_per_interaction": {"pp": flops_pp, "pc": flops_pc},
+                "flops_per_interaction": {"pp": flops_pp, "pp_far": flops_far, "pc": flops_pc},
                 "kernel_ms_per_launch": force_ms / max(force_launches, 1), "launches": force_launches}
     if clk.get("sm_mhz") and f32:
         roofline["peak_at_median_clock"] = fp32_peak_tflops(clk["sm_mhz"])
@@ -492,6 +502,7 @@ def run_ours(args):
                 "particle_steps_per_s": world * n * args.steps / elapsed,
                 "interactions_per_step": inter / args.steps,
                 "pp_pc_per_step": [pp / args.steps, pc / args.steps],
+                "pp_far_per_step": pp_far / args.steps,
                 ("pct_fp32_peak" if f32 else "pct_fp64_peak"): 100 * roofline["frac"] if roofline["frac"] else None,
                 "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
                 "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

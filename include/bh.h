@@ -110,6 +110,11 @@ typedef struct {
     int64_t n_rebuilds; /* list-constructing evaluations so far                   */
     int64_t n_launches; /* CUDA kernels launched by this context                  */
     int64_t n_contacts; /* contact candidates of the last FP32 force evaluation   */
+    int64_t n_pp_far;   /* FP32 path: the part of n_pp whose list particle is "far"
+                         * (beyond contact reach and at least a quarter of the
+                         * group's largest side away), evaluated with a single
+                         * FP32 separation relative to the group origin; 0 on
+                         * the FP64 path                                       */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).

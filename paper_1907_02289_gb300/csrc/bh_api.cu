@@ -547,7 +547,7 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
     for (int b = 0; b < 2; ++b) {
         release(c->ord_key[b]);
         release(c->ord_idx[b]);
@@ -563,7 +563,7 @@ int bh_destroy(bh_ctx* ctx) {
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
     release(c->cz); release(c->Q); release(c->cell32); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
-    release(c->cnt_c); release(c->cnt_j); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
+    release(c->cnt_c); release(c->cnt_j); release(c->cnt_jm); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
     release(c->hbuf); release(c->hid);
     for (auto& pr : c->ev_force) {
         cudaEventDestroy(pr.first);
@@ -876,6 +876,7 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_rebuilds = c->n_rebuilds;
     out->n_launches = c->n_launches;
     out->n_contacts = c->n_contacts;
+    out->n_pp_far = c->n_int_pp_far;
     return BH_OK;
 }
 

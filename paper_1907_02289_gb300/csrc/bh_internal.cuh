@@ -86,6 +86,7 @@ struct Ctx {
     DBuf<uint32_t> tile_meta;           // sort tiles per patch (4 words per tile), n_patches > 1
     int64_t n_tiles = 0;
     DBuf<long long> d_rcq;              // per patch walk contact threshold
+    DBuf<long long> d_rfar;             // per patch far threshold of the split expansion
     DBuf<long long> d_period;           // per patch phi period in grid cells (cylindrical frame; 0 = none)
 
     // status and small device scalars
@@ -158,7 +159,9 @@ struct Ctx {
     // lists
     int64_t n_pp = 0, n_pc = 0, n_jj = 0;
     int64_t n_int_pp = 0, n_int_pc = 0;
+    int64_t n_int_pp_far = 0;            // FP32 path: pp interactions with far list particles
     DBuf<int64_t> cnt_p, cnt_c, cnt_j;   // per group counts, then offsets (ng + 1)
+    DBuf<int64_t> cnt_jm;                // FP32 path: per group index of the first far list particle
     DBuf<int32_t> P, C;
     DBuf<uint32_t> JJ;
     DBuf<int64_t> ipp;                   // per group interaction counts (scratch)

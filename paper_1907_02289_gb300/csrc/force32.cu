@@ -9,7 +9,12 @@
 // the origin as FP32 hi/lo pairs, and the separation of a pair is formed as
 // (x_hi,j - x_hi,i) + (x_lo,j - x_lo,i): exact to an FP32 rounding of the
 // separation itself, however wide the group is.  List cells, which the
-// opening test keeps at least a cell size away, use the hi part alone.
+// opening test keeps at least a cell size away, use the hi part alone, and
+// so do "far" list particles (beyond contact reach and at least a quarter of
+// the group's largest side away; the list expansion puts them after the
+// near ones): their separation is the difference of the two rounded FP32
+// coordinates, as in Sec. 4.7, correct to a few FP32 roundings of itself
+// at that distance, and they need no contact test.
 //
 // Gravity inside r_coll (Eq. 1) is G m_j r / (r_coll^2 + eps^2)^(3/2), so
 // max(r^2, r_coll^2) + eps^2 in the fast loop gives it for every pair (and
@@ -117,6 +122,7 @@ struct Args {
     const uint32_t* begin;
     const uint32_t* end;
     const int64_t* jj_off;
+    const int64_t* jj_mid;  // per group index of the first far list particle (NULL: none)
     const uint32_t* JJ;
     const int64_t* pc_off;
     const int32_t* C;
@@ -276,6 +282,20 @@ __device__ __forceinline__ bool pp_body(const Args& A, const JPair& P, const uin
     return r2.x < A.rc2chk || r2.y < A.rc2chk;
 }
 
+// Far particle-particle term (G-free): single-float separation, no contact
+// test; r > r_coll is certain, so neither the floor nor a mask applies.
+__device__ __forceinline__ void pp_far_body(const JPair& P, const float2 (&nh)[3], float2 (&g)[3], float2 eps2) {
+    const float2 dx = __fadd2_rn(P.x, nh[0]);
+    const float2 dy = __fadd2_rn(P.y, nh[1]);
+    const float2 dz = __fadd2_rn(P.z, nh[2]);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    const float2 f = __fmul2_rn(__fmul2_rn(P.m, ri), __fmul2_rn(ri, ri));
+    g[0] = __ffma2_rn(f, dx, g[0]);
+    g[1] = __ffma2_rn(f, dy, g[1]);
+    g[2] = __ffma2_rn(f, dz, g[2]);
+}
+
 template <int ORDER>
 __device__ __forceinline__ void pc_body(const CPair& Cp, const float2 (&nh)[3], float2 (&g)[3], float2 eps2) {
     const float2 dx = __fadd2_rn(Cp.x, nh[0]);
@@ -346,7 +366,9 @@ __device__ __forceinline__ void gather_particle(const Args& A, Smem32& S, int u,
 }
 
 // Raw slot u -> entry u of the particle tile, relative to the origin as
-// hi/lo pairs (padding when !real).
+// hi/lo pairs (padding when !real); FAR: the hi parts (the rounded relative
+// coordinates) and the mass only.
+template <bool FAR>
 __device__ __forceinline__ void put_particle(Smem32& S, int u, bool real, const float (&oh)[3],
                                              const float (&ol)[3]) {
     float ph[3], pl[3], pm;
@@ -367,6 +389,7 @@ __device__ __forceinline__ void put_particle(Smem32& S, int u, bool real, const 
     base[2 + hh] = ph[1];
     base[4 + hh] = ph[2];
     base[6 + hh] = pm;
+    if (FAR) return;
     base[8 + hh] = pl[0];
     base[10 + hh] = pl[1];
     base[12 + hh] = pl[2];
@@ -485,6 +508,21 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
     }
 }
 
+template <int R, bool TAIL>
+__device__ __forceinline__ void pp_far_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj) {
+    const float2 eps2 = f2(A.fp.eps2f);
+    if constexpr (R > 0)
+#pragma unroll kUnrollPP
+        for (int q = 0; q < npair; ++q) {
+            const JPair& P = S.t.p.jp[q];
+#pragma unroll
+            for (int r = 0; r < R; ++r) pp_far_body(P, K.nh[r], K.g[r], eps2);
+        }
+    if constexpr (TAIL)
+#pragma unroll 1
+        for (int q = tj; q < npair; q += J) pp_far_body(S.t.p.jp[q], K.nh[R], K.g[R], eps2);
+}
+
 template <int R, bool TAIL, int ORDER>
 __device__ __forceinline__ void pc_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj) {
     const float2 eps2 = f2(A.fp.eps2f);
@@ -547,7 +585,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
 #pragma unroll
             for (int s = 0; s < PJ; ++s) {
                 const int u = lane + 32 * s;
-                if (u < 2 * npair) put_particle(S, u, u < nt, oh, ol);
+                if (u < 2 * npair) put_particle<false>(S, u, u < nt, oh, ol);
             }
             __syncwarp();
 #pragma unroll
@@ -566,6 +604,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
     // (2) the other list particles: data gathered one tile ahead, indices two
     {
         const int64_t j0 = A.jj_off[k], j1 = A.jj_off[k + 1];
+        const int64_t jm = A.jj_mid ? A.jj_mid[k] : j1;  // tiles from jm on are far
         uint32_t ib[PJ];
 #pragma unroll
         for (int s = 0; s < PJ; ++s) {
@@ -576,12 +615,18 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
         for (int64_t t0 = j0; t0 < j1; t0 += kTileJ) {
             const int nt = (int)min((int64_t)kTileJ, j1 - t0);
             const int npair = (nt + 1) >> 1;
+            const bool far = t0 >= jm;
             cp_async_wait_all();
             __syncwarp();
 #pragma unroll
             for (int s = 0; s < PJ; ++s) {
                 const int u = lane + 32 * s;
-                if (u < 2 * npair) put_particle(S, u, u < nt, oh, ol);
+                if (u < 2 * npair) {
+                    if (far)
+                        put_particle<true>(S, u, u < nt, oh, ol);
+                    else
+                        put_particle<false>(S, u, u < nt, oh, ol);
+                }
             }
             __syncwarp();
 #pragma unroll
@@ -590,7 +635,10 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
                 ib[s] = list_index(A, t0 + 2 * kTileJ + lane + 32 * s, j1, b);
             }
             cp_async_commit();
-            pp_tile<MODE, R, TAIL, false>(A, S, K, npair, J, tj, qn, lane);
+            if (far)
+                pp_far_tile<R, TAIL>(A, S, K, npair, J, tj);
+            else
+                pp_tile<MODE, R, TAIL, false>(A, S, K, npair, J, tj, qn, lane);
             fold_all<R, TAIL>(S, K, lane);
             __syncwarp();
         }
@@ -986,6 +1034,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.begin = c->begin.p;
     A.end = c->end.p;
     A.jj_off = c->cnt_j.p;
+    A.jj_mid = c->cnt_jm.p;
     A.JJ = c->JJ.p;
     A.pc_off = c->cnt_c.p;
     A.C = c->C.p;

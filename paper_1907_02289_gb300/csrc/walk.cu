@@ -14,6 +14,14 @@
 // thresholds once per build: open iff d2 < D[l] or d2 <= RCQ.  With several
 // patches a group walks the tree of its own patch (root = patch index), and
 // RCQ is per patch (each patch has its own key grid).
+//
+// For the FP32 kernel the expansion puts a group's list particles in two
+// runs: "near" leaves first, then "far" leaves, far meaning beyond contact
+// reach with a margin (so no pair in them can touch) and a gap of at least a
+// quarter of the group's largest side.  The kernel forms far separations from
+// single FP32 coordinates relative to the group origin (the arithmetic of
+// Sec. 4.7), whose error relative to the separation is then bounded by a
+// few FP32 roundings, and skips the contact test for them.
 #include <cmath>
 #include <vector>
 
@@ -25,10 +33,37 @@ namespace {
 struct WalkParams {
     long long D[kLevels + 1];
     const long long* rcq;  // per patch
+    const long long* rfar;    // per patch: d2 above this cannot hold a contact pair (margin included)
     const long long* period;  // per patch period of grid axis 0 (cylindrical frame), 0 = none
     const int64_t* off;    // patch particle offsets (np + 1)
     int np;
 };
+
+// Patch holding particle index gb: the last patch starting at or before it.
+__device__ __forceinline__ int patch_of(const WalkParams& wp, uint32_t gb) {
+    int root = 0;
+    for (int lo = 0, hi = wp.np - 1; lo < hi;) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wp.off[mid] <= (int64_t)gb)
+            lo = root = mid;
+        else
+            hi = mid - 1;
+    }
+    return root;
+}
+
+// Squared gap in whole cells between node box R and the group box [glo, ghi]
+// (axis 0 periodic with the given period in cells when period > 0).
+__device__ __forceinline__ long long box_gap2(const WalkNode& R, const int (&glo)[3], const int (&ghi)[3],
+                                              int period) {
+    const int t1 = (int)R.a.x - ghi[0] - 1, t2 = glo[0] - (int)R.b.x - 1;
+    int d0 = max(0, max(t1, t2));
+    if (period > 0 && d0 > 0)  // periodic phi axis: the shorter way round
+        d0 = min(d0, max(0, t1 > 0 ? glo[0] + period - (int)R.b.x - 1 : (int)R.a.x + period - ghi[0] - 1));
+    const int d1 = max(0, max((int)R.a.y - ghi[1] - 1, glo[1] - (int)R.b.y - 1));
+    const int d2 = max(0, max((int)R.a.z - ghi[2] - 1, glo[2] - (int)R.b.z - 1));
+    return (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2 * d2;
+}
 
 template <bool FILL>
 __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
@@ -46,22 +81,15 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
         const int32_t g = groups[k];
         const WalkNode G = wn[g];
         const uint32_t gb = begin[g], ge = end[g];
-        const int glo0 = (int)G.a.x, glo1 = (int)G.a.y, glo2 = (int)G.a.z;
-        const int ghi0 = (int)G.b.x, ghi1 = (int)G.b.y, ghi2 = (int)G.b.z;
+        const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
+        const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
         ni = (int64_t)(end[g] - begin[g]);
         int64_t pbase = 0, cbase = 0;
         if (FILL) {
             pbase = np_io[k];
             cbase = nc_io[k];
         }
-        int root = 0;
-        for (int lo = 0, hi = wp.np - 1; lo < hi;) {  // last patch starting at or before gb
-            const int mid = (lo + hi + 1) >> 1;
-            if (wp.off[mid] <= (int64_t)gb)
-                lo = root = mid;
-            else
-                hi = mid - 1;
-        }
+        const int root = patch_of(wp, gb);
         const long long rcq = wp.rcq[root];
         const int period = (int)wp.period[root];
         int sn[kLevels + 3], se[kLevels + 3];
@@ -70,13 +98,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
         for (;;) {
             const WalkNode R = wn[node];
             const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
-            const int t1 = (int)R.a.x - ghi0 - 1, t2 = glo0 - (int)R.b.x - 1;
-            int d0 = max(0, max(t1, t2));
-            if (period > 0 && d0 > 0)  // periodic phi axis: the shorter way round
-                d0 = min(d0, max(0, t1 > 0 ? glo0 + period - (int)R.b.x - 1 : (int)R.a.x + period - ghi0 - 1));
-            const int d1 = max(0, max((int)R.a.y - ghi1 - 1, glo1 - (int)R.b.y - 1));
-            const int d2i = max(0, max((int)R.a.z - ghi2 - 1, glo2 - (int)R.b.z - 1));
-            const long long d2 = (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2i * d2i;
+            const long long d2 = box_gap2(R, glo, ghi, period);
             const bool open = d2 < wp.D[lev] || d2 <= rcq;
             if (open) {
                 if (nch == 0) {
@@ -127,35 +149,87 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
 
 // One warp per group: particle entries -> particle indices, leaving out the
 // group's own particles (the force kernels evaluate those in a separate phase
-// that excludes i = j).
+// that excludes i = j).  SPLIT: near leaves first, far leaves after them
+// (each run in list order); jm[k] = index of the first far particle, and
+// the far interactions n_i x (far particles) are summed into *n_far.
+template <bool SPLIT>
 __global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const int64_t* __restrict__ pp_off,
                          const int32_t* __restrict__ P, const uint32_t* __restrict__ begin,
-                         const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
-                         uint32_t* __restrict__ JJ) {
+                         const uint32_t* __restrict__ end, const WalkNode* __restrict__ wn, WalkParams wp,
+                         const int64_t* __restrict__ jj_off, uint32_t* __restrict__ JJ, int64_t* __restrict__ jm,
+                         unsigned long long* n_far) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= ng) return;
     const int32_t g = groups[k];
     const uint32_t gb = begin[g], ge = end[g];
     const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
-    int64_t jo = jj_off[k];
-    for (int64_t e = e0; e < e1; e += 32) {
-        uint32_t b = 0, cnt = 0;
-        if (e + lane < e1) {
-            const int32_t leaf = P[e + lane];
+    int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+    long long rfar = 0, ext2 = 0;
+    int period = 0;
+    if (SPLIT) {
+        const WalkNode G = wn[g];
+        glo[0] = (int)G.a.x; glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
+        ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
+        const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
+        ext2 = ext * ext;
+        const int root = patch_of(wp, gb);
+        rfar = wp.rfar[root];
+        period = (int)wp.period[root];
+    }
+    // leaf entry e -> (first particle, count, far?)
+    auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt, bool& far) {
+        b = 0;
+        cnt = 0;
+        far = false;
+        if (e < e1) {
+            const int32_t leaf = P[e];
             b = begin[leaf];
             cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
+            if (SPLIT && cnt > 0) {
+                const long long d2 = box_gap2(wn[leaf], glo, ghi, period);
+                far = d2 > rfar && 16 * d2 >= ext2;
+            }
         }
-        uint32_t x = cnt;
+    };
+    int64_t jn = jj_off[k], jf = jn;
+    if (SPLIT) {  // far run starts after every near particle
+        uint32_t near = 0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            uint32_t b, cnt;
+            bool far;
+            entry(e, b, cnt, far);
+            near += far ? 0u : cnt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(0xffffffffu, near, o);
+        jf = jn + near;
+        if (lane == 0) {
+            jm[k] = jf;
+            const unsigned long long ni = ge - gb;
+            atomicAdd(n_far, ni * (unsigned long long)(jj_off[k + 1] - jf));
+        }
+    }
+    for (int64_t e = e0; e < e1; e += 32) {
+        uint32_t b, cnt;
+        bool far;
+        entry(e + lane, b, cnt, far);
+        const uint32_t cn = far ? 0u : cnt, cf = far ? cnt : 0u;
+        uint32_t xn = cn, xf = cf;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const uint32_t yn = __shfl_up_sync(0xffffffffu, xn, o);
+            const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
+            if (lane >= o) {
+                xn += yn;
+                xf += yf;
+            }
         }
-        const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
-        const int64_t pos = jo + (x - cnt);
+        const uint32_t tn = __shfl_sync(0xffffffffu, xn, 31), tf = __shfl_sync(0xffffffffu, xf, 31);
+        const int64_t pos = far ? jf + (xf - cf) : jn + (xn - cn);
         for (uint32_t t = 0; t < cnt; ++t) JJ[pos + t] = b + t;
-        jo += tot;
+        jn += tn;
+        jf += tf;
     }
 }
 
@@ -185,6 +259,7 @@ WalkParams walk_params(const Ctx* c) {
         w.D[l] = d;
     }
     w.rcq = c->d_rcq.p;
+    w.rfar = c->d_rfar.p;
     w.period = c->d_period.p;
     w.off = c->d_off.p;
     w.np = c->n_patches;
@@ -203,26 +278,33 @@ int stage_lists(Ctx* c) {
     // |dr|, |dz| <= r_coll and a phi difference of at most ~r_coll / r_min, so
     // (r_coll / r_min + 2e-8) S bounds their grid distance (2e-8 covers the
     // angle's approximation error); the phi axis wraps after floor(2 pi S) cells.
-    std::vector<long long> rcq(c->n_patches), period(c->n_patches, 0);
+    // The far threshold of the split expansion widens the contact reach by
+    // 1e-5 of itself plus two cells, so that no rounding of a coordinate into
+    // its cell can put a touching pair into a far leaf.
+    std::vector<long long> rcq(c->n_patches), rfar(c->n_patches), period(c->n_patches, 0);
     for (int q = 0; q < c->n_patches; ++q) {
         const double L = c->h_box[8 * q + 3];
         const double S = 2097152.0 / L;
-        double r2;
+        double a;
         if (c->prm.key_frame == 1) {
-            double a = c->prm.r_coll / c->h_box[8 * q + 1];
+            a = c->prm.r_coll / c->h_box[8 * q + 1];
             a = a + 2e-8;
             a = a * S;
-            r2 = a * a;
             period[q] = (long long)std::floor(6.283185307179586 * S);
         } else {
-            const double r = c->prm.r_coll * S;
-            r2 = r * r;
+            a = c->prm.r_coll * S;
         }
+        const double r2 = a * a;
         rcq[q] = (r2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(r2);
+        const double w = c->prm.r_coll > 0.0 ? a * (1.0 + 1e-5) + 2.0 : 0.0;
+        rfar[q] = (w * w >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(w * w);
     }
     BH_TRY(grow(c, c->d_rcq, rcq.size(), "walk contact thresholds"));
+    BH_TRY(grow(c, c->d_rfar, rfar.size(), "far thresholds"));
     BH_TRY(grow(c, c->d_period, period.size(), "walk periods"));
     BH_CUDA(c, cudaMemcpyAsync(c->d_rcq.p, rcq.data(), rcq.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                               c->stream));
+    BH_CUDA(c, cudaMemcpyAsync(c->d_rfar.p, rfar.data(), rfar.size() * sizeof(long long), cudaMemcpyHostToDevice,
                                c->stream));
     BH_CUDA(c, cudaMemcpyAsync(c->d_period.p, period.data(), period.size() * sizeof(long long),
                                cudaMemcpyHostToDevice, c->stream));
@@ -255,9 +337,24 @@ int stage_lists(Ctx* c) {
                                             c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
                                             c->n_nodes, c->d_status);
     BH_LAUNCH(c);
-    k_expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p,
-                                                             c->end.p, c->cnt_j.p, c->JJ.p);
+    const bool split = c->prm.precision == BH_PREC_FP32;
+    unsigned long long* n_far = c->d_small + 10;
+    if (split) {
+        BH_TRY(grow(c, c->cnt_jm, (size_t)ng + 1, "list split points"));
+        BH_CUDA(c, cudaMemsetAsync(n_far, 0, sizeof(unsigned long long), c->stream));
+    }
+    auto expand = split ? k_expand<true> : k_expand<false>;
+    expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p,
+                                                           c->end.p, c->wnode.p, wp, c->cnt_j.p, c->JJ.p,
+                                                           split ? c->cnt_jm.p : nullptr, n_far);
     BH_LAUNCH(c);
+    c->n_int_pp_far = 0;
+    if (split) {
+        unsigned long long hf = 0;
+        BH_CUDA(c, cudaMemcpyAsync(&hf, n_far, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->n_int_pp_far = (int64_t)hf;
+    }
     if (c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
     return BH_OK;
 }

@@ -15,8 +15,9 @@ def test_recorded_traffic_matches_only_its_configuration():
     tuning = dict(rec["tuning"])
     got = bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], tuning)
     assert got == rec["bytes_per_launch"]
-    for key, other in (("n_g", 128), ("chunk", 64), ("order_window", 8192), ("sched", 0), ("warps", 8)):
-        t = dict(tuning, **{key: other})
+    for key, alt in (("n_g", (128, 256)), ("chunk", (64, 96)), ("order_window", (8192, 0)), ("sched", (0, 2)),
+                     ("warps", (2, 8))):
+        t = dict(tuning, **{key: alt[0] if tuning[key] != alt[0] else alt[1]})
         assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], t) is None, key
     assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"] // 2, rec["key_frame"], tuning) is None
     assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], 1 - rec["key_frame"], tuning) is None
@@ -24,11 +25,13 @@ def test_recorded_traffic_matches_only_its_configuration():
 
 
 def test_traffic_record_follows_the_kernel_source():
-    """The committed record carries the hash of the force kernel's source as
-    it is now (a change to the kernel must retake or drop the number)."""
+    """The committed record carries the hash of the force kernel's source
+    and of the list expansion as they are now (a change to either must
+    retake or drop the number)."""
     import hashlib
+    assert {"force32.cu", "force_common.cuh", "walk.cu"} <= set(bench.TRAFFIC_SOURCES)
     h = hashlib.sha256()
-    for f in ("force32.cu", "force_common.cuh"):
+    for f in bench.TRAFFIC_SOURCES:
         with open(bench.os.path.join(bench.ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     assert _rec()["source_sha256"] == h.hexdigest()
