@@ -153,25 +153,28 @@ TRAFFIC_SOURCES = ("force32.cu", "force_common.cuh", "walk.cu")
 
 def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning: dict):
     """DRAM bytes per launch of the force kernel from the committed ncu
-    capture, if it was taken on this workload (size, frame, n_g and launch
-    settings) with the kernel source as it is now (else None)."""
+    captures (one record per launch setting captured), if one was taken on
+    this workload (size, frame, n_g and launch settings) with the kernel
+    source as it is now (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[kernel]
+        recs = json.load(open(path))[kernel]
     except (OSError, KeyError, ValueError):
         return None
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n
-            or rec.get("key_frame") != key_frame):
-        return None
-    if any(rec.get("tuning", {}).get(k) != tuning.get(k) for k in ("n_g", "chunk", "warps", "sched", "order_window",
-                                                                    "order_by_cost")):
-        return None
-    return rec["bytes_per_launch"]
+    for rec in recs if isinstance(recs, list) else [recs]:
+        if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload or rec.get("N") != n
+                or rec.get("key_frame") != key_frame):
+            continue
+        if any(rec.get("tuning", {}).get(k) != tuning.get(k) for k in ("n_g", "chunk", "warps", "sched",
+                                                                        "order_window", "order_by_cost")):
+            continue
+        return rec["bytes_per_launch"]
+    return None
 
 
 def oracle_sector(n_sector: int, full_n: int, prm: dict, seed: int = 77):

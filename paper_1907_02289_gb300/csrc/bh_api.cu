@@ -559,7 +559,7 @@ int bh_destroy(bh_ctx* ctx) {
     }
     release(c->sort_hist); release(c->digit_hist); release(c->pscratch); release(c->scan_tmp);
     release(c->level); release(c->nchild); release(c->begin); release(c->end); release(c->parent);
-    release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->split_cnt);
+    release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->skip); release(c->split_cnt);
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
     release(c->cz); release(c->Q); release(c->cell32); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);

@@ -114,6 +114,7 @@ struct Ctx {
     DBuf<int32_t> parent, first_child;
     DBuf<uint32_t> qlo, qhi;         // 3 per node
     DBuf<WalkNode> wnode;
+    DBuf<int32_t> skip;                 // depth-first successor of each node's subtree (-1: none)
     DBuf<uint32_t> split_cnt;        // per node of a level
     DBuf<uint32_t> split_off;
     DBuf<uint32_t> split_bnd;        // 9 per node of a level

@@ -139,6 +139,32 @@ __global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cn
     wnode[k] = w;
 }
 
+// Depth-first successor of node u's subtree: the node a pre-order walk
+// visits after u when it does not descend into u.  Children of a node are
+// consecutive ids, so that is u + 1 unless u is its parent's last child, in
+// which case it is the parent's successor; a root has none (-1), which ends
+// the walk of its patch.
+__global__ void k_skip(int64_t nn, const int32_t* __restrict__ parent, const int32_t* __restrict__ first_child,
+                       const uint8_t* __restrict__ nchild, int32_t* __restrict__ skip, int* status) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nn) return;
+    int64_t v = u;
+    for (int up = 0; up <= kLevels + 1; ++up) {
+        const int32_t p = parent[v];
+        if (p < 0) {
+            skip[u] = -1;
+            return;
+        }
+        if (v + 1 < (int64_t)first_child[p] + nchild[p]) {
+            skip[u] = (int32_t)(v + 1);
+            return;
+        }
+        v = p;
+    }
+    atomicOr(status, kStatBounds);  // deeper than the key grid: never for a valid tree
+    skip[u] = -1;
+}
+
 __device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);
     lo = __double2float_rn(__dsub_rn(v, (double)hi));
@@ -421,6 +447,10 @@ int stage_boxes(Ctx* c) {
                                                              c->nchild.p, c->qlo.p, c->qhi.p, c->wnode.p);
         BH_LAUNCH(c);
     }
+    BH_TRY(grow(c, c->skip, (size_t)nn, "walk successors"));
+    k_skip<<<blocks_for(nn, 256), 256, 0, c->stream>>>(nn, c->parent.p, c->first_child.p, c->nchild.p, c->skip.p,
+                                                       c->d_status);
+    BH_LAUNCH(c);
     return BH_OK;
 }
 

@@ -2,9 +2,10 @@
 // builds the group's interaction list (Barnes' group walk): opened leaves
 // become particle entries, accepted nodes become cell entries.  The walk is
 // depth first in octant order, so both lists come out ordered by first
-// particle.  A count pass sizes the lists, a fill pass writes them, and the
-// particle entries are then expanded into the particle indices the force
-// kernel reads.
+// particle; it needs no stack, since every node carries the successor of its
+// subtree.  A count pass sizes the lists, a fill pass writes them (16-byte
+// stores), and the particle entries are then expanded into the particle
+// indices the force kernel reads.
 //
 // Opening test (integer boxes on the key grid, exact): per axis the gap in
 // whole cells is delta = max(0, clo - ghi - 1, glo - chi - 1), d2 = sum of
@@ -65,9 +66,42 @@ __device__ __forceinline__ long long box_gap2(const WalkNode& R, const int (&glo
     return (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2 * d2;
 }
 
+// Per-thread list writer: entries are gathered in registers and written as
+// aligned 16-byte stores; the partial quads at the two ends of the thread's
+// run [base, base + count) are written entry by entry, so no store touches
+// another thread's run.  dst must be 16-byte aligned.
+struct ListOut {
+    int32_t* dst;
+    int64_t base, pos;
+    int32_t v0, v1, v2, v3;
+    __device__ __forceinline__ int32_t at(int s) const { return s == 0 ? v0 : s == 1 ? v1 : s == 2 ? v2 : v3; }
+    __device__ __forceinline__ void put_range(int64_t a, int64_t b) const {
+        for (int64_t q = a; q < b; ++q) dst[q] = at((int)(q & 3));
+    }
+    __device__ __forceinline__ void put(int32_t v) {
+        const int s = (int)(pos & 3);
+        v0 = s == 0 ? v : v0;
+        v1 = s == 1 ? v : v1;
+        v2 = s == 2 ? v : v2;
+        v3 = s == 3 ? v : v3;
+        if (s == 3) {
+            if (pos - 3 >= base)
+                *reinterpret_cast<int4*>(dst + (pos - 3)) = make_int4(v0, v1, v2, v3);
+            else
+                put_range(base, pos + 1);
+        }
+        ++pos;
+    }
+    __device__ __forceinline__ void flush() const { put_range(max(base, pos & ~(int64_t)3), pos); }
+};
+
+// The walk is stackless: a node that is not descended into is followed by
+// its subtree's successor (skip), an opened inner node by its first child,
+// which visits the nodes in the same depth-first octant order as a stack.
 template <bool FILL>
 __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
                                               const WalkNode* __restrict__ wn,
+                                              const int32_t* __restrict__ skip,
                                               const uint32_t* __restrict__ begin,
                                               const uint32_t* __restrict__ end, WalkParams wp,
                                               int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
@@ -84,25 +118,25 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
         const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
         const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
         ni = (int64_t)(end[g] - begin[g]);
-        int64_t pbase = 0, cbase = 0;
+        ListOut po{P, 0, 0, 0, 0, 0, 0}, co{C, 0, 0, 0, 0, 0, 0};
         if (FILL) {
-            pbase = np_io[k];
-            cbase = nc_io[k];
+            po.base = po.pos = np_io[k];
+            co.base = co.pos = nc_io[k];
         }
         const int root = patch_of(wp, gb);
         const long long rcq = wp.rcq[root];
         const int period = (int)wp.period[root];
-        int sn[kLevels + 3], se[kLevels + 3];
-        int sp = 0;
         int node = root;
-        for (;;) {
+        for (int64_t visits = 0;; ++visits) {
             const WalkNode R = wn[node];
+            const int after = skip[node];
             const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
             const long long d2 = box_gap2(R, glo, ghi, period);
             const bool open = d2 < wp.D[lev] || d2 <= rcq;
+            int next = after;
             if (open) {
                 if (nch == 0) {
-                    if (FILL) P[pbase + np] = node;
+                    if (FILL) po.put(node);
                     ++np;
                     const uint32_t lb = begin[node];
                     if (lb >= gb && lb < ge)
@@ -110,21 +144,22 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                     else
                         nj += (int64_t)(end[node] - lb);
                 } else {
-                    sn[sp] = (int)R.b.w;
-                    se[sp] = (int)R.b.w + nch;
-                    ++sp;
+                    next = (int)R.b.w;
                 }
             } else {
-                if (FILL) C[cbase + nc] = node;
+                if (FILL) co.put(node);
                 ++nc;
             }
-            if (sp == 0) break;
-            node = sn[sp - 1]++;
-            if (sn[sp - 1] == se[sp - 1]) --sp;
-            if (node < 0 || node >= nn || sp > kLevels + 1) {  // never taken for a valid tree
+            if (next < 0) break;
+            if (next >= nn || visits >= nn) {  // never taken for a valid tree
                 atomicOr(status, kStatBounds);
                 break;
             }
+            node = next;
+        }
+        if (FILL) {
+            po.flush();
+            co.flush();
         }
         if (!FILL) {
             np_io[k] = np;
@@ -177,28 +212,31 @@ __global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const i
         rfar = wp.rfar[root];
         period = (int)wp.period[root];
     }
-    // leaf entry e -> (first particle, count, far?)
-    auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt, bool& far) {
+    // leaf entry e -> (first particle, count); far? by the box test, or from
+    // the first pass's flags (bit c = the lane's entry of round c < 32)
+    auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt) {
         b = 0;
         cnt = 0;
-        far = false;
         if (e < e1) {
             const int32_t leaf = P[e];
             b = begin[leaf];
             cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
-            if (SPLIT && cnt > 0) {
-                const long long d2 = box_gap2(wn[leaf], glo, ghi, period);
-                far = d2 > rfar && 16 * d2 >= ext2;
-            }
         }
     };
+    auto far_of = [&](int64_t e) -> bool {
+        const long long d2 = box_gap2(wn[P[e]], glo, ghi, period);
+        return d2 > rfar && 16 * d2 >= ext2;
+    };
     int64_t jn = jj_off[k], jf = jn;
+    uint32_t flags = 0;
     if (SPLIT) {  // far run starts after every near particle
         uint32_t near = 0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
+        int c = 0;
+        for (int64_t e = e0 + lane; e < e1; e += 32, ++c) {
             uint32_t b, cnt;
-            bool far;
-            entry(e, b, cnt, far);
+            entry(e, b, cnt);
+            const bool far = cnt > 0 && far_of(e);
+            if (far && c < 32) flags |= 1u << c;
             near += far ? 0u : cnt;
         }
 #pragma unroll
@@ -210,10 +248,10 @@ __global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const i
             atomicAdd(n_far, ni * (unsigned long long)(jj_off[k + 1] - jf));
         }
     }
-    for (int64_t e = e0; e < e1; e += 32) {
+    for (int64_t e = e0, c = 0; e < e1; e += 32, ++c) {
         uint32_t b, cnt;
-        bool far;
-        entry(e + lane, b, cnt, far);
+        entry(e + lane, b, cnt);
+        const bool far = SPLIT && cnt > 0 && (c < 32 ? ((flags >> c) & 1u) != 0 : far_of(e + lane));
         const uint32_t cn = far ? 0u : cnt, cf = far ? cnt : 0u;
         uint32_t xn = cn, xf = cf;
 #pragma unroll
@@ -312,8 +350,8 @@ int stage_lists(Ctx* c) {
     unsigned long long* inter = c->d_small + 8;
     BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));
     const unsigned nb = blocks_for(ng, 128);
-    k_walk<false><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
-                                             c->cnt_c.p, c->cnt_j.p, nullptr, nullptr, inter,
+    k_walk<false><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp,
+                                             c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, nullptr, nullptr, inter,
                                              c->n_nodes, c->d_status);
     BH_LAUNCH(c);
     DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
@@ -333,8 +371,8 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->P, (size_t)c->n_pp + 1, "particle lists"));
     BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
     BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));
-    k_walk<true><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p,
-                                            c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
+    k_walk<true><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp,
+                                            c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
                                             c->n_nodes, c->d_status);
     BH_LAUNCH(c);
     const bool split = c->prm.precision == BH_PREC_FP32;

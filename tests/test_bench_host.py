@@ -6,22 +6,28 @@ import json
 import bench
 
 
-def _rec():
+def _recs():
     return json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_force32"]
 
 
 def test_recorded_traffic_matches_only_its_configuration():
-    rec = _rec()
-    tuning = dict(rec["tuning"])
-    got = bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], tuning)
-    assert got == rec["bytes_per_launch"]
-    for key, alt in (("n_g", (128, 256)), ("chunk", (64, 96)), ("order_window", (8192, 0)), ("sched", (0, 2)),
-                     ("warps", (2, 8))):
-        t = dict(tuning, **{key: alt[0] if tuning[key] != alt[0] else alt[1]})
-        assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], t) is None, key
-    assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"] // 2, rec["key_frame"], tuning) is None
-    assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], 1 - rec["key_frame"], tuning) is None
-    assert bench.recorded_traffic("k_force32", "patches64", rec["N"], rec["key_frame"], tuning) is None
+    recs = _recs()
+    assert isinstance(recs, list) and recs
+    captured = [r["tuning"] for r in recs]
+    for rec in recs:
+        tuning = dict(rec["tuning"])
+        got = bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], tuning)
+        assert got == rec["bytes_per_launch"]
+        for key, alts in (("n_g", (128, 256, 192)), ("chunk", (64, 96)), ("order_window", (8192, 0)),
+                          ("sched", (0, 2)), ("warps", (2, 8))):
+            for alt in alts:
+                t = dict(tuning, **{key: alt})
+                if t == tuning or any(all(t.get(k) == c.get(k) for k in c) for c in captured):
+                    continue
+                assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], rec["key_frame"], t) is None
+        assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"] // 2, rec["key_frame"], tuning) is None
+        assert bench.recorded_traffic("k_force32", rec["workload"], rec["N"], 1 - rec["key_frame"], tuning) is None
+        assert bench.recorded_traffic("k_force32", "patches64", rec["N"], rec["key_frame"], tuning) is None
 
 
 def test_traffic_record_follows_the_kernel_source():
@@ -34,7 +40,8 @@ def test_traffic_record_follows_the_kernel_source():
     for f in bench.TRAFFIC_SOURCES:
         with open(bench.os.path.join(bench.ROOT, "paper_1907_02289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    assert _rec()["source_sha256"] == h.hexdigest()
+    for rec in _recs():
+        assert rec["source_sha256"] == h.hexdigest()
 
 
 def test_fp32_peak_from_unit_counts():
