@@ -20,7 +20,10 @@ and updates.
            surface density
 
 --impl reference runs the oracle as the reference arm.  Under torchrun each
-rank runs an independent replica (weak scaling); rank 0 prints.
+rank runs an independent replica (weak scaling); with --shard the patches
+workload instead splits one set of 64 patches across the ranks by the LPT
+rule on estimated cost (strong scaling; no data-path collective).  Rank 0
+prints; value sums the ranks' interactions over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -76,6 +79,9 @@ def parse():
     ap.add_argument("--n-g", type=int, default=None, help="override the group size limit")
     ap.add_argument("--n-leaf", type=int, default=None, help="override the leaf size limit")
     ap.add_argument("--tune", default="", help="launch settings to apply, e.g. chunk=64,order_window=8192")
+    ap.add_argument("--shard", action="store_true",
+                    help="patches workload under torchrun: split one set of patches across the ranks (LPT on "
+                         "estimated cost, strong scaling) instead of one set per rank")
     return ap.parse_args()
 
 
@@ -93,6 +99,29 @@ def max_over_ranks(x: float, device="cpu") -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(x: float, device="cpu") -> float:
+    """The sum of x over all ranks (work done by the whole job); x itself
+    when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_patches(sizes, rank: int, world: int):
+    """Patch indices this rank steps when one set of patches is split across
+    the ranks, and the load imbalance (largest / mean estimated cost)."""
+    from paper_1907_02289_gb300 import shard
+    costs = [shard.patch_cost(int(s)) for s in sizes]
+    parts = shard.lpt_assign(costs, world)
+    if any(not p for p in parts):
+        raise SystemExit(f"--shard: {len(sizes)} patches cannot give every one of {world} ranks a patch")
+    return parts[rank], shard.imbalance(costs, parts)
 
 
 def replica_seed(base_seed: int, rank: int) -> int:
@@ -286,8 +315,19 @@ def run_ours(args):
     if args.n_leaf is not None:
         prm["n_leaf"] = args.n_leaf
     offsets = None
+    sharded = args.shard and pr["kind"] == "patches"
+    shard_info = None
+    if args.shard and not sharded:
+        raise SystemExit("--shard applies to the patches workload only")
     if pr["kind"] == "patches":
-        parts, sizes = synth.patches(seed=replica_seed(pr["seed"], rank))
+        if sharded:  # one set of patches for the whole job, LPT-split across the ranks
+            parts, sizes = synth.patches(seed=pr["seed"])
+            mine, imb = shard_patches(sizes, rank, world)
+            shard_info = {"patches_this_rank": len(mine), "patches_total": len(sizes),
+                          "estimated_cost_imbalance": imb}
+            parts, sizes = [parts[i] for i in mine], [sizes[i] for i in mine]
+        else:
+            parts, sizes = synth.patches(seed=replica_seed(pr["seed"], rank))
         P = {f: np.concatenate([q[f] for q in parts]) for f in synth.FIELDS}
         offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         n = int(offsets[-1])
@@ -353,7 +393,12 @@ def run_ours(args):
     launches = c1["n_launches"] - c0["n_launches"]
     inter = pp + pc
     elapsed = max_over_ranks(elapsed, "cuda")
-    value = world * inter / elapsed
+    # work of the whole job: every rank's own (sharded patches differ per
+    # rank; replicas are alike, so this is world x one rank's)
+    job_inter = sum_over_ranks(inter, "cuda")
+    job_n = sum_over_ranks(n, "cuda")
+    job_paper_flops = sum_over_ranks(pp * PAPER_PP + pc * PAPER_PC, "cuda")
+    value = job_inter / elapsed
     if prm["precision"] == 1:
         flops_pc = FLOPS_PC2 if prm["order"] >= 2 else FLOPS_PC1
         flops_pp = FLOPS_PP_NO_EPS if prm["eps"] == 0.0 else FLOPS_PP
@@ -450,9 +495,9 @@ def run_ours(args):
         barrier()
         te = time.perf_counter() - t0
         te = max_over_ranks(te, "cuda")
-        e2e = {"value": world * (ppe + pce) / te, "unit": "interactions/s",
+        e2e = {"value": sum_over_ranks(ppe + pce, "cuda") / te, "unit": "interactions/s",
                "h2d_bytes_per_step": n * (10 * 8 + 8), "d2h_bytes_per_step": n * (10 * 8 + 8),
-               "particle_steps_per_s": world * n * args.steps / te, "api": "bh_step_host (pinned host buffers)"}
+               "particle_steps_per_s": job_n * args.steps / te, "api": "bh_step_host (pinned host buffers)"}
         ctxh.close()
 
     cpu = None
@@ -490,7 +535,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prm["precision"] == 1 else "f64",
+                "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32" if prm["precision"] == 1 else "f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "N": n, "theta": prm["theta"], "n_g": prm["n_g"],
                            "n_leaf": prm["n_leaf"],
@@ -499,15 +544,17 @@ def run_ours(args):
                            "precision": "FP32 group-relative forces, FP64 positions/velocities/updates"
                            if prm["precision"] == 1 else "FP64",
                            "l2": "inputs larger than L2 (particle arrays %.1f GB)" % (n * 88 / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "parallelism": ("patches split across ranks (LPT)" if sharded and world > 1
+                                           else "replicas" if world > 1 else "single GPU"),
+                           **({"shard_rank0": shard_info} if shard_info else {}),
                            **({"patches": len(offsets) - 1} if offsets is not None else {}),
                            **({"tuning": tuning} if tuning else {})},
-                "particle_steps_per_s": world * n * args.steps / elapsed,
+                "particle_steps_per_s": job_n * args.steps / elapsed,
                 "interactions_per_step": inter / args.steps,
                 "pp_pc_per_step": [pp / args.steps, pc / args.steps],
                 "pp_far_per_step": pp_far / args.steps,
                 ("pct_fp32_peak" if f32 else "pct_fp64_peak"): 100 * roofline["frac"] if roofline["frac"] else None,
-                "flops_per_s_paper_convention": world * (pp * PAPER_PP + pc * PAPER_PC) / elapsed,
+                "flops_per_s_paper_convention": job_paper_flops / elapsed,
                 "force_error": err, "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "device_memory_used_gb": mem_used_gb,
                 **({"load_balance_busy_fraction": balance} if balance is not None else {})}
