@@ -44,8 +44,10 @@ sys.path.insert(0, ROOT)
 # separation 24 (23 without softening, where the + eps^2 is not issued),
 # particle-particle with a far list particle (single-float separation) 18
 # (17 without softening: its r^2 chain adds eps^2 = 0, not counted),
-# particle-cell with quadrupole 49, monopole only 18.
-FLOPS_PP, FLOPS_PP_NO_EPS, FLOPS_PC2, FLOPS_PC1 = 24, 23, 49, 18
+# particle-cell with quadrupole 48 (a = (M R^2 - 5/2 (d.q) / R^2) d / R^5
+# + q / R^5: 3 FADD, 3 FFMA for R^2, FMUL R^-2, 9 for q, 3 for d.q, 2 FMUL
+# for R^-5, FMUL + FMUL + FFMA for the coefficient, 6 FFMA), monopole only 18.
+FLOPS_PP, FLOPS_PP_NO_EPS, FLOPS_PC2, FLOPS_PC1 = 24, 23, 48, 18
 FLOPS_PP_FAR, FLOPS_PP_FAR_NO_EPS = 18, 17
 # The plain FP64 kernel (absolute coordinates, rsqrt not counted): pp 18
 # (3 sub, r^2 5, + eps^2 1, 3 mul, 3 FMA), pc with quadrupole 53, monopole 21.

@@ -306,17 +306,17 @@ __device__ __forceinline__ void pc_body(const CPair& Cp, const float2 (&nh)[3], 
     const float2 ri2 = __fmul2_rn(ri, ri);
     const float2 ri3 = __fmul2_rn(ri, ri2);
     if (ORDER >= 2) {
-        // q = -Q d, dqd = d.(-Q d); a += (M/R^3 + 5/2 (dQd)/R^7) d - Q d / R^5
+        // q = -Q d, dqd = d.(-Q d); a += (M R^2 - 5/2 dqd / R^2) d / R^5 + q / R^5
         const float2 qx = __ffma2_rn(Cp.qxx, dx, __ffma2_rn(Cp.qxy, dy, __fmul2_rn(Cp.qxz, dz)));
         const float2 qy = __ffma2_rn(Cp.qxy, dx, __ffma2_rn(Cp.qyy, dy, __fmul2_rn(Cp.qyz, dz)));
         const float2 qz = __ffma2_rn(Cp.qxz, dx, __ffma2_rn(Cp.qyz, dy, __fmul2_rn(Cp.qzz, dz)));
         const float2 dqd = __ffma2_rn(dx, qx, __ffma2_rn(dy, qy, __fmul2_rn(dz, qz)));
-        const float2 ri5 = __fmul2_rn(ri3, ri2);
-        const float2 ri7 = __fmul2_rn(ri5, ri2);
-        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri7), f2(-2.5f), __fmul2_rn(Cp.m, ri3));
-        g[0] = __ffma2_rn(ri5, qx, __ffma2_rn(s, dx, g[0]));
-        g[1] = __ffma2_rn(ri5, qy, __ffma2_rn(s, dy, g[1]));
-        g[2] = __ffma2_rn(ri5, qz, __ffma2_rn(s, dz, g[2]));
+        const float2 ri4 = __fmul2_rn(ri2, ri2);
+        const float2 ri5 = __fmul2_rn(ri4, ri);
+        const float2 s = __ffma2_rn(__fmul2_rn(dqd, ri2), f2(-2.5f), __fmul2_rn(Cp.m, R2));
+        g[0] = __ffma2_rn(ri5, __ffma2_rn(s, dx, qx), g[0]);
+        g[1] = __ffma2_rn(ri5, __ffma2_rn(s, dy, qy), g[1]);
+        g[2] = __ffma2_rn(ri5, __ffma2_rn(s, dz, qz), g[2]);
     } else {
         const float2 s = __fmul2_rn(Cp.m, ri3);
         g[0] = __ffma2_rn(s, dx, g[0]);
