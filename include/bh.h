@@ -313,6 +313,22 @@ int bh_get_balance(bh_ctx* ctx, double* busy_fraction);
 int bh_sort_keys_static(uint64_t* keys, uint32_t* idx, uint64_t* keys_tmp, uint32_t* idx_tmp, int64_t n,
                         void* stream, char* err, size_t err_len);
 
+/* The FP64 -> FP32 hi/lo split the FP32 path applies to every particle
+ * coordinate and node centre (Sec. 4.7: the single-precision kernel works on
+ * coordinates relative to a group origin, formed from these pairs), on its
+ * own: hi[i] = v[i] rounded to the nearest float (ties to even), lo[i] =
+ * v[i] - hi[i] (exact in FP64) rounded the same way.  Every finite or
+ * non-finite input gives the bits of those two conversions.
+ *
+ *  v       [n] double, device, in.
+ *  hi, lo  [n] float, device, out; caller-owned, distinct, not overlapping v.
+ *  n       >= 0.
+ *  stream  cudaStream_t (NULL = legacy default stream); enqueues one kernel
+ *          and returns without synchronising.
+ * No context is needed and nothing is allocated.  Errors: BH_E_INVAL (n < 0,
+ * a NULL pointer with n > 0, hi == lo), BH_E_CUDA (launch failure). */
+int bh_split_f32(const double* v, float* hi, float* lo, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

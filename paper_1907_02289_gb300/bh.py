@@ -22,7 +22,7 @@ SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_se
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
            "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_set_tuning", "bh_get_tuning", "bh_autotune",
-           "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static")
+           "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static", "bh_split_f32")
 BH_SCHED_GRID, BH_SCHED_STATIC, BH_SCHED_DYNAMIC = 0, 1, 2
 BH_SORT_STATIC_MAX_N = 4194304
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.bh_get_balance.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.bh_get_diagnostics.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.POINTER(bh_diagnostics)]
     lib.bh_sort_keys_static.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.bh_split_f32.argtypes = [P, P, P, ctypes.c_int64, P]
     _lib = lib
     return lib
 
@@ -136,6 +137,21 @@ def bh_sort_keys_static(keys, idx, keys_tmp, idx_tmp, stream=None):
                                  ctypes.c_void_p(stream), buf, len(buf))
     if rc != BH_OK:
         raise BHError(rc, buf.value.decode())
+    return rc
+
+
+def bh_split_f32(v, hi, lo, stream=None):
+    """FP32 hi/lo split of the float64 device tensor v into the float32
+    device tensors hi and lo (same length) on the given stream (default:
+    torch's current stream)."""
+    import torch
+    lib = load()
+    n = v.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.bh_split_f32(v.data_ptr(), hi.data_ptr(), lo.data_ptr(), n, ctypes.c_void_p(stream))
+    if rc != BH_OK:
+        raise BHError(rc, "bh_split_f32 failed")
     return rc
 
 

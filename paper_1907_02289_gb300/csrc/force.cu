@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "force_common.cuh"
+#include "split32.cuh"
 
 namespace bh {
 namespace {
@@ -151,14 +152,23 @@ __global__ void k_split_particles(const double* __restrict__ x, const double* __
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v[3] = {x[i], y[i], z[i]};
-    float h[3], l[3];
+    float h[3], l[3], mh, ml;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        h[a] = __double2float_rn(v[a]);
-        l[a] = __double2float_rn(__dsub_rn(v[a], (double)h[a]));
-    }
-    phi[i] = make_float4(h[0], h[1], h[2], __double2float_rn(m[i]));
+    for (int a = 0; a < 3; ++a) split_f32(v[a], h[a], l[a]);
+    split_f32(m[i], mh, ml);
+    phi[i] = make_float4(h[0], h[1], h[2], mh);
     plo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// The split alone, for callers and tests of it (bh_split_f32).
+__global__ void k_split_values(const double* __restrict__ v, int64_t n, float* __restrict__ hi,
+                               float* __restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h, l;
+    split_f32(v[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
 }
 
 }  // namespace
@@ -213,3 +223,10 @@ int stage_force(Ctx* c, bh_particles* p, bool add_central) {
 }
 
 }  // namespace bh
+
+extern "C" int bh_split_f32(const double* v, float* hi, float* lo, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!v || !hi || !lo)) || (n > 0 && hi == lo)) return BH_E_INVAL;
+    if (n == 0) return BH_OK;
+    bh::k_split_values<<<bh::blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, n, hi, lo);
+    return cudaGetLastError() == cudaSuccess ? BH_OK : BH_E_CUDA;
+}

@@ -11,6 +11,7 @@
 // internal nodes: children in octant order) with _rn intrinsics, so they do
 // not depend on thread scheduling or on multiply-add contraction.
 #include "bh_internal.cuh"
+#include "split32.cuh"
 
 namespace bh {
 namespace {
@@ -165,10 +166,6 @@ __global__ void k_skip(int64_t nn, const int32_t* __restrict__ parent, const int
     skip[u] = -1;
 }
 
-__device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
-    hi = __double2float_rn(v);
-    lo = __double2float_rn(__dsub_rn(v, (double)hi));
-}
 
 // Moments of the nodes of one level (children already done).
 template <int ORDER, bool CELL32>
