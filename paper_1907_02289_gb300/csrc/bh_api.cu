@@ -189,9 +189,21 @@ int evaluate(Ctx* c, bh_particles* p) {
     } else {
         BH_TRY(stage_moments(c, p));
     }
-    if (c->want_pos_event) {  // x..id are final for this step from here on
+    if (c->want_pos_event && c->early_now) {  // x..id are final for this step from here on
         BH_CUDA(c, cudaEventRecord(c->pos_event, c->stream));
         c->pos_event_recorded = true;
+        if (c->early_dst) {  // copy them back while the force kernel runs
+            const bh_particles& h = *c->early_dst;
+            const bh_particles& d = *c->early_src;
+            const size_t nb = (size_t)d.n * sizeof(double);
+            BH_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->pos_event, 0));
+            BH_CUDA(c, cudaMemcpyAsync(h.x, d.x, nb, cudaMemcpyDeviceToHost, c->copy_stream));
+            BH_CUDA(c, cudaMemcpyAsync(h.y, d.y, nb, cudaMemcpyDeviceToHost, c->copy_stream));
+            BH_CUDA(c, cudaMemcpyAsync(h.z, d.z, nb, cudaMemcpyDeviceToHost, c->copy_stream));
+            BH_CUDA(c, cudaMemcpyAsync(h.m, d.m, nb, cudaMemcpyDeviceToHost, c->copy_stream));
+            BH_CUDA(c, cudaMemcpyAsync(h.id, d.id, (size_t)d.n * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                       c->copy_stream));
+        }
     }
     BH_TRY(stage_force(c, p, true));
     c->k_eval++;
@@ -617,12 +629,13 @@ int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps) {
     BH_TRY(bh::check_particles(c, p, true));
     if (c->have_tree && p->n != c->n) return bh::fail(c, BH_E_INVAL, "particle count changed");
     const double dt = c->prm.dt;
+    c->early_now = false;  // the initial evaluation is never the step's last
     if (!c->have_acc) {
         BH_TRY(bh::evaluate(c, p));
         c->have_acc = true;
     }
     for (int s = 0; s < nsteps; ++s) {
-        c->pos_event_recorded = false;  // only the last step's evaluation counts
+        c->early_now = s == nsteps - 1;  // only the last step's evaluation counts
         if (c->tune.graph && c->have_lists && c->k_eval % c->prm.rebuild_every != 0) {
             BH_TRY(bh::graph_reuse_step(c, p));
             continue;
@@ -724,21 +737,19 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     if (!c->pos_event) BH_CUDA(c, cudaEventCreateWithFlags(&c->pos_event, cudaEventDisableTiming));
     c->want_pos_event = true;
     c->pos_event_recorded = false;
+    c->early_dst = h;
+    c->early_src = &d;
     const int rc = bh_step(ctx, &d, nsteps);
     c->want_pos_event = false;
+    c->early_now = false;
+    c->early_dst = c->early_src = nullptr;
     BH_TRY(rc);
-    // positions, masses and ids: copied back on the second stream as soon as
-    // the last evaluation has fixed them (while its force kernel runs);
-    // velocities and accelerations after the final kick
+    // positions, masses and ids: their copy back was enqueued on the second
+    // stream by the last evaluation as soon as they were final (so it ran
+    // with the force kernel); velocities and accelerations follow the final
+    // kick.  A step run as a graph has no such point: everything after it.
     const bool early = c->pos_event_recorded;
     const int late_from = early ? 3 : 0;
-    if (early) {
-        BH_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->pos_event, 0));
-        const int pos[4] = {0, 1, 2, 6};
-        for (int a : pos)
-            BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream));
-        BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->copy_stream));
-    }
     for (int a = late_from; a < 10; ++a) {
         if (early && a == 6) continue;
         BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -148,11 +148,15 @@ struct Ctx {
     cudaGraphExec_t graph_exec = nullptr;  // the captured list-reusing step
     cudaStream_t cap_stream = nullptr;   // private stream the step is captured on
     // host-buffer stepping: positions, masses and ids are final once the last
-    // evaluation's tree/moments stage is enqueued; their copy back overlaps
-    // the force kernel on a second stream
+    // evaluation's tree/moments stage is enqueued; their copy back is
+    // enqueued right there, on a second stream, so that it overlaps the force
+    // kernel (the host waits after that kernel to size the contact pass)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t pos_event = nullptr;
     bool want_pos_event = false, pos_event_recorded = false;
+    bool early_now = false;              // the evaluation being run is the call's last
+    const bh_particles* early_dst = nullptr;  // host arrays of the early copy
+    const bh_particles* early_src = nullptr;  // device arrays it copies from
     bool graph_ok = false;               // graph_exec matches the current lists and arrays
     bh_particles graph_p{};              // particle arrays the graph was captured with
     int64_t graph_launches = 0;          // kernels in the graph
