@@ -314,11 +314,11 @@ int bh_sort_keys_static(uint64_t* keys, uint32_t* idx, uint64_t* keys_tmp, uint3
                         void* stream, char* err, size_t err_len);
 
 /* The FP64 -> FP32 hi/lo split the FP32 path applies to every particle
- * coordinate and node centre (Sec. 4.7: the single-precision kernel works on
- * coordinates relative to a group origin, formed from these pairs), on its
- * own: hi[i] = v[i] rounded to the nearest float (ties to even), lo[i] =
- * v[i] - hi[i] (exact in FP64) rounded the same way.  Every finite or
- * non-finite input gives the bits of those two conversions.
+ * coordinate and mass each evaluation (Sec. 4.7: the single-precision
+ * kernel works on coordinates relative to a group origin, formed from these
+ * pairs), on its own: hi[i] = v[i] rounded to the nearest float (ties to
+ * even), lo[i] = v[i] - hi[i] (exact in FP64) rounded the same way.  Every
+ * finite or non-finite input gives the bits of those two conversions.
  *
  *  v       [n] double, device, in.
  *  hi, lo  [n] float, device, out; caller-owned, distinct, not overlapping v.

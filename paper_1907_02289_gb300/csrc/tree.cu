@@ -11,7 +11,6 @@
 // internal nodes: children in octant order) with _rn intrinsics, so they do
 // not depend on thread scheduling or on multiply-add contraction.
 #include "bh_internal.cuh"
-#include "split32.cuh"
 
 namespace bh {
 namespace {
@@ -168,13 +167,13 @@ __global__ void k_skip(int64_t nn, const int32_t* __restrict__ parent, const int
 
 
 // Moments of the nodes of one level (children already done).
-template <int ORDER, bool CELL32>
+template <int ORDER>
 __global__ void k_moments(int64_t ls, int64_t cnt, const uint32_t* __restrict__ begin,
                           const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
                           const uint8_t* __restrict__ nchild, const double* __restrict__ x,
                           const double* __restrict__ y, const double* __restrict__ z,
                           const double* __restrict__ m, double* M, double* cx, double* cy,
-                          double* cz, double* Q, float4* cell32) {
+                          double* cz, double* Q) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     const int64_t k = ls + t;
@@ -252,16 +251,6 @@ __global__ void k_moments(int64_t ls, int64_t cnt, const uint32_t* __restrict__ 
     cz[k] = c2;
 #pragma unroll
     for (int a = 0; a < 6; ++a) Q[6 * k + a] = q[a];
-    if (CELL32) {
-        float h0, h1, h2, l0, l1, l2;
-        split_f32(c0, h0, l0);
-        split_f32(c1, h1, l1);
-        split_f32(c2, h2, l2);
-        cell32[3 * k + 0] = make_float4(h0, h1, h2, __double2float_rn(Mk));
-        cell32[3 * k + 1] = make_float4(l0, l1, l2, __double2float_rn(q[0]));
-        cell32[3 * k + 2] = make_float4(__double2float_rn(q[3]), __double2float_rn(q[4]),
-                                        __double2float_rn(q[1]), __double2float_rn(q[5]));
-    }
 }
 
 // Moments for the FP32 force path, all in FP32: offsets from a reference
@@ -482,15 +471,13 @@ int stage_moments(Ctx* c, const bh_particles* p) {
     for (int lev = depth - 1; lev >= 0; --lev) {
         const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
         const unsigned nb = blocks_for(cnt, 128);
-#define BH_MOM(O, F)                                                                               \
-    k_moments<O, F><<<nb, 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p, c->first_child.p,     \
-                                               c->nchild.p, p->x, p->y, p->z, p->m, c->M.p, c->cx.p, \
-                                               c->cy.p, c->cz.p, c->Q.p, c->cell32.p)
-        if (c->prm.order >= 2) {
-            if (f32) BH_MOM(2, true); else BH_MOM(2, false);
-        } else {
-            if (f32) BH_MOM(1, true); else BH_MOM(1, false);
-        }
+#define BH_MOM(O)                                                                                  \
+    k_moments<O><<<nb, 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p, c->first_child.p, c->nchild.p, \
+                                            p->x, p->y, p->z, p->m, c->M.p, c->cx.p, c->cy.p, c->cz.p, c->Q.p)
+        if (c->prm.order >= 2)
+            BH_MOM(2);
+        else
+            BH_MOM(1);
 #undef BH_MOM
         BH_LAUNCH(c);
     }
