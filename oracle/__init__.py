@@ -1,8 +1,8 @@
 """CPU FP64 oracle for the group-shared Barnes-Hut force evaluation
 (Iwasawa et al., arXiv:1907.02289).
 
-TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
-leg of the benchmark may import this package.  It shares no code with the CUDA
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg and reference arm may import this package.  It shares no code with the CUDA
 library and never imports it; the only thing both sides use is the seeded input
 generator, which holds none of the method's arithmetic.
 
