@@ -115,6 +115,10 @@ typedef struct {
                          * group's largest side away), evaluated with a single
                          * FP32 separation relative to the group origin; 0 on
                          * the FP64 path                                       */
+    int64_t n_one_walk_builds; /* list builds whose lists came from a single tree
+                         * walk into per-group slots (sized from the previous
+                         * build's longest lists) instead of a count walk and a
+                         * fill walk; results are the same either way          */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).

@@ -575,7 +575,7 @@ int bh_destroy(bh_ctx* ctx) {
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
     release(c->cz); release(c->Q); release(c->cell32); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
-    release(c->cnt_c); release(c->cnt_j); release(c->cnt_jm); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
+    release(c->cnt_c); release(c->cnt_j); release(c->cnt_jm); release(c->stash_p); release(c->stash_c); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
     release(c->hbuf); release(c->hid);
     for (auto& pr : c->ev_force) {
         cudaEventDestroy(pr.first);
@@ -888,6 +888,7 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_launches = c->n_launches;
     out->n_contacts = c->n_contacts;
     out->n_pp_far = c->n_int_pp_far;
+    out->n_one_walk_builds = c->n_one_walk_builds;
     return BH_OK;
 }
 

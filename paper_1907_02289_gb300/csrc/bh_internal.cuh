@@ -167,6 +167,9 @@ struct Ctx {
     int64_t n_int_pp_far = 0;            // FP32 path: pp interactions with far list particles
     DBuf<int64_t> cnt_p, cnt_c, cnt_j;   // per group counts, then offsets (ng + 1)
     DBuf<int64_t> cnt_jm;                // FP32 path: per group index of the first far list particle
+    DBuf<int32_t> stash_p, stash_c;      // per group list slots of the one-walk build
+    int64_t walk_cap_p = 0, walk_cap_c = 0;  // their sizes (0: count and fill walks)
+    int64_t n_one_walk_builds = 0;       // list builds whose lists came from one walk
     DBuf<int32_t> P, C;
     DBuf<uint32_t> JJ;
     DBuf<int64_t> ipp;                   // per group interaction counts (scratch)

@@ -72,13 +72,17 @@ __device__ __forceinline__ long long box_gap2(const WalkNode& R, const int (&glo
 // another thread's run.  dst must be 16-byte aligned.
 struct ListOut {
     int32_t* dst;
-    int64_t base, pos;
+    int64_t base, pos, cap;  // entries at or past cap are counted, not written
     int32_t v0, v1, v2, v3;
     __device__ __forceinline__ int32_t at(int s) const { return s == 0 ? v0 : s == 1 ? v1 : s == 2 ? v2 : v3; }
     __device__ __forceinline__ void put_range(int64_t a, int64_t b) const {
         for (int64_t q = a; q < b; ++q) dst[q] = at((int)(q & 3));
     }
     __device__ __forceinline__ void put(int32_t v) {
+        if (pos >= cap) {
+            ++pos;
+            return;
+        }
         const int s = (int)(pos & 3);
         v0 = s == 0 ? v : v0;
         v1 = s == 1 ? v : v1;
@@ -92,13 +96,20 @@ struct ListOut {
         }
         ++pos;
     }
-    __device__ __forceinline__ void flush() const { put_range(max(base, pos & ~(int64_t)3), pos); }
+    __device__ __forceinline__ void flush() const { put_range(max(base, min(pos, cap) & ~(int64_t)3), min(pos, cap)); }
 };
 
 // The walk is stackless: a node that is not descended into is followed by
 // its subtree's successor (skip), an opened inner node by its first child,
 // which visits the nodes in the same depth-first octant order as a stack.
-template <bool FILL>
+// Modes: count (list sizes and interaction counts); fill (the lists, at the
+// scanned offsets); stash (count, and write each group's lists into a slot
+// of capP / capC entries at k * cap, flagging a group that does not fit).
+// Count and stash also record the longest lists, which size the next
+// build's slots.
+constexpr int kWalkCount = 0, kWalkFill = 1, kWalkStash = 2;
+
+template <int MODE>
 __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
                                               const WalkNode* __restrict__ wn,
                                               const int32_t* __restrict__ skip,
@@ -107,7 +118,9 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                                               int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
                                               int64_t* __restrict__ nj_io, int32_t* __restrict__ P,
                                               int32_t* __restrict__ C, unsigned long long* inter,
-                                              int64_t nn, int* status) {
+                                              int64_t nn, int* status, int64_t capP, int64_t capC,
+                                              unsigned long long* longest, unsigned long long* overflow) {
+    constexpr bool WRITE = MODE != kWalkCount, COUNT = MODE != kWalkFill;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < ng;
     int64_t np = 0, nc = 0, nj = 0, ni = 0, nown = 0;
@@ -118,10 +131,15 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
         const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
         const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
         ni = (int64_t)(end[g] - begin[g]);
-        ListOut po{P, 0, 0, 0, 0, 0, 0}, co{C, 0, 0, 0, 0, 0, 0};
-        if (FILL) {
+        ListOut po{P, 0, 0, INT64_MAX, 0, 0, 0, 0}, co{C, 0, 0, INT64_MAX, 0, 0, 0, 0};
+        if (MODE == kWalkFill) {
             po.base = po.pos = np_io[k];
             co.base = co.pos = nc_io[k];
+        } else if (MODE == kWalkStash) {
+            po.dst = P + k * capP;
+            po.cap = capP;
+            co.dst = C + k * capC;
+            co.cap = capC;
         }
         const int root = patch_of(wp, gb);
         const long long rcq = wp.rcq[root];
@@ -136,7 +154,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
             int next = after;
             if (open) {
                 if (nch == 0) {
-                    if (FILL) po.put(node);
+                    if (WRITE) po.put(node);
                     ++np;
                     const uint32_t lb = begin[node];
                     if (lb >= gb && lb < ge)
@@ -147,7 +165,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                     next = (int)R.b.w;
                 }
             } else {
-                if (FILL) co.put(node);
+                if (WRITE) co.put(node);
                 ++nc;
             }
             if (next < 0) break;
@@ -157,27 +175,34 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
             }
             node = next;
         }
-        if (FILL) {
+        if (WRITE) {
             po.flush();
             co.flush();
         }
-        if (!FILL) {
+        if (MODE == kWalkStash && (np > capP || nc > capC)) atomicOr(overflow, 1ull);
+        if (COUNT) {
             np_io[k] = np;
             nc_io[k] = nc;
             nj_io[k] = nj;
         }
     }
-    if (!FILL) {
-        // interaction counts: n_i * (list particles) and n_i * (list cells)
+    if (COUNT) {
+        // interaction counts: n_i * (list particles) and n_i * (list cells);
+        // longest particle and cell lists
         unsigned long long ipp = (unsigned long long)(ni * (nj + nown)), ipc = (unsigned long long)(ni * nc);
+        unsigned long long lp = (unsigned long long)np, lc = (unsigned long long)nc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
             ipc += __shfl_xor_sync(0xffffffffu, ipc, o);
+            lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o));
+            lc = max(lc, __shfl_xor_sync(0xffffffffu, lc, o));
         }
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&inter[0], ipp);
             atomicAdd(&inter[1], ipc);
+            atomicMax(&longest[0], lp);
+            atomicMax(&longest[1], lc);
         }
     }
 }
@@ -271,6 +296,19 @@ __global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const i
     }
 }
 
+// One warp per group: the group's stashed lists (slots of capP / capC
+// entries) to their places in the packed lists.
+__global__ void k_unstash(int64_t ng, const int64_t* __restrict__ pp_off, const int64_t* __restrict__ pc_off,
+                          const int32_t* __restrict__ sP, const int32_t* __restrict__ sC, int64_t capP,
+                          int64_t capC, int32_t* __restrict__ P, int32_t* __restrict__ C) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= ng) return;
+    const int64_t p0 = pp_off[k], np = pp_off[k + 1] - p0, c0 = pc_off[k], nc = pc_off[k + 1] - c0;
+    for (int64_t t = lane; t < np; t += 32) P[p0 + t] = sP[k * capP + t];
+    for (int64_t t = lane; t < nc; t += 32) C[c0 + t] = sC[k * capC + t];
+}
+
 __global__ void k_set_last(int64_t* off, int64_t ng, const unsigned long long* total) {
     off[ng] = (int64_t)*total;
 }
@@ -348,11 +386,28 @@ int stage_lists(Ctx* c) {
                                cudaMemcpyHostToDevice, c->stream));
     const WalkParams wp = walk_params(c);
     unsigned long long* inter = c->d_small + 8;
-    BH_CUDA(c, cudaMemsetAsync(inter, 0, 2 * sizeof(unsigned long long), c->stream));
+    unsigned long long* overflow = c->d_small + 11;
+    unsigned long long* longest = c->d_small + 12;  // two words
+    // One walk when the previous build gave slot sizes and the slots take
+    // at most 4x the previous lists' storage; else (and after an overflow)
+    // a count walk and a fill walk.
+    const int64_t capP = c->walk_cap_p, capC = c->walk_cap_c;
+    bool stash = capP > 0 && capC > 0 &&
+                 (double)ng * (double)(capP + capC) <= 4.0 * (double)(c->n_pp + c->n_pc) + 1.0e6;
+    if (stash) {
+        BH_TRY(grow(c, c->stash_p, (size_t)(ng * capP), "stashed particle lists"));
+        BH_TRY(grow(c, c->stash_c, (size_t)(ng * capC), "stashed cell lists"));
+    }
+    BH_CUDA(c, cudaMemsetAsync(inter, 0, 6 * sizeof(unsigned long long), c->stream));  // words 8..13
     const unsigned nb = blocks_for(ng, 128);
-    k_walk<false><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp,
-                                             c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, nullptr, nullptr, inter,
-                                             c->n_nodes, c->d_status);
+    if (stash)
+        k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(
+            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
+            c->stash_p.p, c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest, overflow);
+    else
+        k_walk<kWalkCount><<<nb, 128, 0, c->stream>>>(
+            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
+            nullptr, nullptr, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
     BH_LAUNCH(c);
     DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
     for (int a = 0; a < 3; ++a) {
@@ -371,10 +426,20 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->P, (size_t)c->n_pp + 1, "particle lists"));
     BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
     BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));
-    k_walk<true><<<nb, 128, 0, c->stream>>>(ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp,
-                                            c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, c->P.p, c->C.p, inter,
-                                            c->n_nodes, c->d_status);
+    if (stash && h[11] == 0) {
+        k_unstash<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->cnt_p.p, c->cnt_c.p, c->stash_p.p,
+                                                                   c->stash_c.p, capP, capC, c->P.p, c->C.p);
+        ++c->n_one_walk_builds;
+    } else {
+        k_walk<kWalkFill><<<nb, 128, 0, c->stream>>>(
+            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
+            c->P.p, c->C.p, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
+    }
     BH_LAUNCH(c);
+    // slots of the next build: the longest lists of this one plus a quarter,
+    // in whole 16-byte units
+    c->walk_cap_p = (int64_t)(((h[12] + h[12] / 4 + 4) + 3) & ~3ull);
+    c->walk_cap_c = (int64_t)(((h[13] + h[13] / 4 + 4) + 3) & ~3ull);
     const bool split = c->prm.precision == BH_PREC_FP32;
     unsigned long long* n_far = c->d_small + 10;
     if (split) {
