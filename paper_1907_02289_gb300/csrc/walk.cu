@@ -3,8 +3,11 @@
 // become particle entries, accepted nodes become cell entries.  The walk is
 // depth first in octant order, so both lists come out ordered by first
 // particle; it needs no stack, since every node carries the successor of its
-// subtree.  A count pass sizes the lists, a fill pass writes them (16-byte
-// stores), and the particle entries are then expanded into the particle
+// subtree.  A count pass sizes the lists and a fill pass writes them (16-byte
+// stores); from the second build on, one pass both counts and writes each
+// group's lists into a slot sized from the previous build, and a copy packs
+// the slots (a group that outgrows its slot sends the build back to count
+// and fill).  The particle entries are then expanded into the particle
 // indices the force kernel reads.
 //
 // Opening test (integer boxes on the key grid, exact): per axis the gap in
