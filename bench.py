@@ -487,6 +487,7 @@ def run_ours(args):
         ctxh.bh_step_host(H, args.warmup)
         ctxh.bh_set_timing(False)
         ppe = pce = 0
+        cb0 = ctxh.bh_get_counters()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -497,8 +498,12 @@ def run_ours(args):
         barrier()
         te = time.perf_counter() - t0
         te = max_over_ranks(te, "cuda")
+        cb1 = ctxh.bh_get_counters()
+        # bytes the library copied per step (ids, and masses on the way back,
+        # only on list-constructing steps: the others leave them unchanged)
         e2e = {"value": sum_over_ranks(ppe + pce, "cuda") / te, "unit": "interactions/s",
-               "h2d_bytes_per_step": n * (10 * 8 + 8), "d2h_bytes_per_step": n * (10 * 8 + 8),
+               "h2d_bytes_per_step": (cb1["n_h2d_bytes"] - cb0["n_h2d_bytes"]) / args.steps,
+               "d2h_bytes_per_step": (cb1["n_d2h_bytes"] - cb0["n_d2h_bytes"]) / args.steps,
                "particle_steps_per_s": job_n * args.steps / te, "api": "bh_step_host (pinned host buffers)"}
         ctxh.close()
 

@@ -119,6 +119,10 @@ typedef struct {
                          * walk into per-group slots (sized from the previous
                          * build's longest lists) instead of a count walk and a
                          * fill walk; results are the same either way          */
+    int64_t n_h2d_bytes; /* bytes bh_step_host has copied host -> device so far  */
+    int64_t n_d2h_bytes; /* ... and device -> host (ids, and masses on the way
+                          * back, only for calls with a list-constructing
+                          * evaluation: other steps leave them unchanged)        */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
@@ -176,7 +180,12 @@ int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps);
 
 /* Same as bh_step with HOST particle arrays: each call copies the arrays to
  * library-owned device buffers, steps, and copies x..id and ax..az back.
- * Synchronises. */
+ * Only list-constructing evaluations reorder the particles, so a call with
+ * none of them copies neither ids (either way) nor masses (back): they are
+ * unchanged and the host arrays stay current; a later list-constructing
+ * call copies the host ids in before reordering them.  Positions, masses
+ * and ids are copied back on a second stream while the last evaluation's
+ * force kernel runs.  Synchronises. */
 int bh_step_host(bh_ctx* ctx, bh_particles* host, int nsteps);
 
 /* Wait for the stream and report device-side errors. */

@@ -43,7 +43,8 @@ class bh_particles(ctypes.Structure):
 
 class bh_counters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
-                                               "n_contacts", "n_pp_far", "n_one_walk_builds")]
+                                               "n_contacts", "n_pp_far", "n_one_walk_builds",
+                                               "n_h2d_bytes", "n_d2h_bytes")]
 
 
 class bh_diagnostics(ctypes.Structure):

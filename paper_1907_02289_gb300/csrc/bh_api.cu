@@ -200,9 +200,11 @@ int evaluate(Ctx* c, bh_particles* p) {
             BH_CUDA(c, cudaMemcpyAsync(h.x, d.x, nb, cudaMemcpyDeviceToHost, c->copy_stream));
             BH_CUDA(c, cudaMemcpyAsync(h.y, d.y, nb, cudaMemcpyDeviceToHost, c->copy_stream));
             BH_CUDA(c, cudaMemcpyAsync(h.z, d.z, nb, cudaMemcpyDeviceToHost, c->copy_stream));
-            BH_CUDA(c, cudaMemcpyAsync(h.m, d.m, nb, cudaMemcpyDeviceToHost, c->copy_stream));
-            BH_CUDA(c, cudaMemcpyAsync(h.id, d.id, (size_t)d.n * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                       c->copy_stream));
+            if (c->early_ids) {  // masses and ids change only when the evaluations reorder
+                BH_CUDA(c, cudaMemcpyAsync(h.m, d.m, nb, cudaMemcpyDeviceToHost, c->copy_stream));
+                BH_CUDA(c, cudaMemcpyAsync(h.id, d.id, (size_t)d.n * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                           c->copy_stream));
+            }
         }
     }
     BH_TRY(stage_force(c, p, true));
@@ -729,16 +731,27 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     d.m = b + 6 * n; d.ax = b + 7 * n; d.ay = b + 8 * n; d.az = b + 9 * n; d.id = c->hid.p; d.n = n;
     double* hs[10] = {h->x, h->y, h->z, h->vx, h->vy, h->vz, h->m, h->ax, h->ay, h->az};
     double* ds[10] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.ax, d.ay, d.az};
+    // Only list-constructing evaluations reorder the particles.  When this
+    // call has none, the ids are not needed on the device and neither ids
+    // nor masses change, so they are not copied (the caller's copies stay
+    // current; a later list build copies the ids in before reordering them).
+    bool reorder = !c->have_lists || !c->have_acc;
+    for (int64_t k = c->k_eval; !reorder && k < c->k_eval + nsteps; ++k) reorder = k % c->prm.rebuild_every == 0;
     const int ncopy = c->have_acc ? 10 : 7;
     for (int a = 0; a < ncopy; ++a)
         BH_CUDA(c, cudaMemcpyAsync(ds[a], hs[a], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    BH_CUDA(c, cudaMemcpyAsync(d.id, h->id, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    c->h2d_bytes += (int64_t)ncopy * n * (int64_t)sizeof(double);
+    if (reorder) {
+        BH_CUDA(c, cudaMemcpyAsync(d.id, h->id, n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+        c->h2d_bytes += n * (int64_t)sizeof(int64_t);
+    }
     if (!c->copy_stream) BH_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     if (!c->pos_event) BH_CUDA(c, cudaEventCreateWithFlags(&c->pos_event, cudaEventDisableTiming));
     c->want_pos_event = true;
     c->pos_event_recorded = false;
     c->early_dst = h;
     c->early_src = &d;
+    c->early_ids = reorder;
     const int rc = bh_step(ctx, &d, nsteps);
     c->want_pos_event = false;
     c->early_now = false;
@@ -750,11 +763,19 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     // kick.  A step run as a graph has no such point: everything after it.
     const bool early = c->pos_event_recorded;
     const int late_from = early ? 3 : 0;
+    int64_t out_bytes = early ? (reorder ? 4 : 3) * n * (int64_t)sizeof(double) +
+                                    (reorder ? n * (int64_t)sizeof(int64_t) : 0)
+                              : 0;
     for (int a = late_from; a < 10; ++a) {
-        if (early && a == 6) continue;
+        if ((early || !reorder) && a == 6) continue;  // masses: copied early, or unchanged
         BH_CUDA(c, cudaMemcpyAsync(hs[a], ds[a], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        out_bytes += n * (int64_t)sizeof(double);
     }
-    if (!early) BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    if (!early && reorder) {
+        BH_CUDA(c, cudaMemcpyAsync(h->id, d.id, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+        out_bytes += n * (int64_t)sizeof(int64_t);
+    }
+    c->d2h_bytes += out_bytes;
     if (early) BH_CUDA(c, cudaStreamSynchronize(c->copy_stream));
     return bh_sync(ctx);
 }
@@ -889,6 +910,8 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_contacts = c->n_contacts;
     out->n_pp_far = c->n_int_pp_far;
     out->n_one_walk_builds = c->n_one_walk_builds;
+    out->n_h2d_bytes = c->h2d_bytes;
+    out->n_d2h_bytes = c->d2h_bytes;
     return BH_OK;
 }
 

@@ -157,6 +157,8 @@ struct Ctx {
     bool early_now = false;              // the evaluation being run is the call's last
     const bh_particles* early_dst = nullptr;  // host arrays of the early copy
     const bh_particles* early_src = nullptr;  // device arrays it copies from
+    bool early_ids = true;               // the early copy includes masses and ids
+    int64_t h2d_bytes = 0, d2h_bytes = 0;  // copied by bh_step_host so far
     bool graph_ok = false;               // graph_exec matches the current lists and arrays
     bh_particles graph_p{};              // particle arrays the graph was captured with
     int64_t graph_launches = 0;          // kernels in the graph

@@ -210,3 +210,33 @@ def test_host_steps_equal_device_steps_cylindrical(graph):
             outs.append(D.numpy())
     for f in bh.Particles.FIELDS:
         assert np.array_equal(outs[0][f], outs[1][f]), f
+
+
+def test_host_steps_copy_ids_only_when_reordering():
+    """bh_step_host copies ids (and masses back) only for calls with a
+    list-constructing evaluation; the byte counters say so, and the host
+    arrays end equal to the device path's."""
+    from paper_1907_02289_gb300 import bh
+    n = 20000
+    P = synth.ring(n, 25)
+    prm = _prm()  # lists rebuilt every 4 evaluations
+    ctx = bh.Context(**prm)
+    H = bh.HostParticles(P, pinned=True)
+    deltas = []
+    for _ in range(6):
+        c0 = ctx.bh_get_counters()
+        ctx.bh_step_host(H, 1)
+        c1 = ctx.bh_get_counters()
+        deltas.append((c1["n_h2d_bytes"] - c0["n_h2d_bytes"], c1["n_d2h_bytes"] - c0["n_d2h_bytes"]))
+    full_in, full_out = 10 * 8 * n + 8 * n, 10 * 8 * n + 8 * n
+    # evaluations: call 1 = initial (0) + 1, then 2, 3, 4 (list build), 5, 6
+    assert deltas[0] == (7 * 8 * n + 8 * n, full_out)  # no accelerations to copy in yet
+    assert deltas[1] == deltas[2] == deltas[4] == deltas[5] == (10 * 8 * n, 9 * 8 * n)
+    assert deltas[3] == (full_in, full_out)
+    D = bh.Particles(P)
+    cd = bh.Context(**prm)
+    cd.bh_step(D, 6)
+    cd.bh_sync()
+    out = D.numpy()
+    for f in bh.Particles.FIELDS:
+        assert np.array_equal(H.a[f], out[f]), f
