@@ -23,7 +23,11 @@ int fail(Ctx* c, int code, const char* fmt, ...) {
 int grow_raw(Ctx* c, void** p, size_t* cap, size_t need, const char* what, bool keep) {
     if (need <= *cap && *p) return BH_OK;
     void* q = nullptr;
-    size_t bytes = need < 256 ? 256 : need;
+    // A buffer that has to grow again (list sizes vary a little from one
+    // build to the next) gets a quarter of headroom: each regrowth costs a
+    // stream synchronisation, an allocation and a free in the middle of a step.
+    size_t bytes = *p ? need + need / 4 : need;
+    if (bytes < 256) bytes = 256;
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
