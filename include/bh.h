@@ -306,8 +306,9 @@ int bh_get_balance(bh_ctx* ctx, double* busy_fraction);
  *  keys      [n] uint64 device, in: keys; out: keys in ascending order.
  *  idx       [n] uint32 device, out: idx[i] = input position of the key now
  *            at i; equal keys keep their input order (stable).
- *  keys_tmp, idx_tmp  [n] caller-owned device scratch, contents clobbered;
- *            must not alias keys or idx.
+ *  keys_tmp, idx_tmp  [n] caller-owned device scratch, contents clobbered.
+ *            The four buffers must be pairwise disjoint byte ranges
+ *            (any overlap is rejected with BH_E_INVAL).
  *  n         0 <= n <= BH_SORT_STATIC_MAX_N; larger n is rejected with
  *            BH_E_INVAL before anything runs.
  *  stream    cudaStream_t for all work (NULL = legacy default stream).  The
@@ -317,10 +318,13 @@ int bh_get_balance(bh_ctx* ctx, double* busy_fraction);
  * The first call on each device does set-up with that device current: it
  * looks up the scratch array's address (cudaGetSymbolAddress) and sets the
  * sort kernel's shared-memory limit; make that first call before capturing
- * any stream on that device.  Every call on one device uses the same scratch
+ * any stream on that device.  The looked-up address belongs to the device's
+ * primary context: after cudaDeviceReset (or anything else that destroys
+ * that context) this entry point must not be called again in the process.
+ * Every call on one device uses the same scratch
  * array, so calls that can overlap in time (different streams or host
  * threads) race and give wrong results: order them, e.g. on one stream.
- * Errors: BH_E_INVAL (n out of range, NULL or aliased buffers, device
+ * Errors: BH_E_INVAL (n out of range, NULL or overlapping buffers, device
  * ordinal >= 64), BH_E_CUDA (set-up or launch failure). */
 #define BH_SORT_STATIC_MAX_N 4194304
 int bh_sort_keys_static(uint64_t* keys, uint32_t* idx, uint64_t* keys_tmp, uint32_t* idx_tmp, int64_t n,

@@ -123,19 +123,50 @@ def make_params(**kw) -> bh_params:
     return p
 
 
+def _check_buffers(what: str, n: int, bufs):
+    """Reject, before anything is launched, buffers the C side cannot check:
+    bufs is a list of (name, tensor, torch dtype); each must have that dtype,
+    exactly n elements, be contiguous and live on one CUDA device.  Returns
+    that device."""
+    import torch
+    for name, t, dt in bufs:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{what}: {name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{what}: {name} must have dtype {dt}, not {t.dtype}")
+        if t.numel() != n:
+            raise ValueError(f"{what}: {name} has {t.numel()} elements, {n} expected")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: {name} must be contiguous")
+    dev = bufs[0][1].device
+    for name, t, _ in bufs:
+        if not t.is_cuda:
+            raise ValueError(f"{what}: {name} must be a CUDA tensor (got device {t.device})")
+        if t.device != dev:
+            raise ValueError(f"{what}: {name} is on {t.device}, {bufs[0][0]} on {dev}: all must share one device")
+    return dev
+
+
 def bh_sort_keys_static(keys, idx, keys_tmp, idx_tmp, stream=None):
     """Stable sort of the uint64 keys (device tensors, int64 dtype holding the
     bits) with idx (int32 dtype holding uint32) the input position of each
     sorted key; keys_tmp / idx_tmp are device scratch of the same sizes.
-    Nothing is allocated by the library; see bh.h for the limits."""
+    All four tensors must be contiguous, on one CUDA device, with keys.numel()
+    elements each.  The call runs with that device current, on the given
+    stream (default: that device's current stream).  Nothing is allocated by
+    the library; see bh.h for the limits."""
     import torch
+    n = keys.numel() if isinstance(keys, torch.Tensor) else -1
+    dev = _check_buffers("bh_sort_keys_static", n, [("keys", keys, torch.int64), ("idx", idx, torch.int32),
+                                                     ("keys_tmp", keys_tmp, torch.int64),
+                                                     ("idx_tmp", idx_tmp, torch.int32)])
     lib = load()
-    n = keys.numel()
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    buf = ctypes.create_string_buffer(256)
-    rc = lib.bh_sort_keys_static(keys.data_ptr(), idx.data_ptr(), keys_tmp.data_ptr(), idx_tmp.data_ptr(), n,
-                                 ctypes.c_void_p(stream), buf, len(buf))
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        buf = ctypes.create_string_buffer(256)
+        rc = lib.bh_sort_keys_static(keys.data_ptr(), idx.data_ptr(), keys_tmp.data_ptr(), idx_tmp.data_ptr(), n,
+                                     ctypes.c_void_p(stream), buf, len(buf))
     if rc != BH_OK:
         raise BHError(rc, buf.value.decode())
     return rc
@@ -143,14 +174,18 @@ def bh_sort_keys_static(keys, idx, keys_tmp, idx_tmp, stream=None):
 
 def bh_split_f32(v, hi, lo, stream=None):
     """FP32 hi/lo split of the float64 device tensor v into the float32
-    device tensors hi and lo (same length) on the given stream (default:
-    torch's current stream)."""
+    device tensors hi and lo (same length, contiguous, one CUDA device) on the
+    given stream (default: that device's current stream), with that device
+    current."""
     import torch
+    n = v.numel() if isinstance(v, torch.Tensor) else -1
+    dev = _check_buffers("bh_split_f32", n, [("v", v, torch.float64), ("hi", hi, torch.float32),
+                                             ("lo", lo, torch.float32)])
     lib = load()
-    n = v.numel()
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    rc = lib.bh_split_f32(v.data_ptr(), hi.data_ptr(), lo.data_ptr(), n, ctypes.c_void_p(stream))
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        rc = lib.bh_split_f32(v.data_ptr(), hi.data_ptr(), lo.data_ptr(), n, ctypes.c_void_p(stream))
     if rc != BH_OK:
         raise BHError(rc, "bh_split_f32 failed")
     return rc

@@ -756,6 +756,15 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     c->early_dst = h;
     c->early_src = &d;
     c->early_ids = reorder;
+    // From here on the copy stream may hold copies into the caller's host
+    // arrays: every return waits for them, so none is still writing after
+    // the call has returned (with an error or not).
+    struct CopyStreamGuard {
+        cudaStream_t s;
+        ~CopyStreamGuard() {
+            if (s) cudaStreamSynchronize(s);
+        }
+    } guard{c->copy_stream};
     const int rc = bh_step(ctx, &d, nsteps);
     c->want_pos_event = false;
     c->early_now = false;
@@ -781,6 +790,7 @@ int bh_step_host(bh_ctx* ctx, bh_particles* h, int nsteps) {
     }
     c->d2h_bytes += out_bytes;
     if (early) BH_CUDA(c, cudaStreamSynchronize(c->copy_stream));
+    guard.s = nullptr;  // waited for above
     return bh_sync(ctx);
 }
 

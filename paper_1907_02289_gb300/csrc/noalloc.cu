@@ -41,6 +41,9 @@ int report(char* err, size_t err_len, int code, const char* fmt, ...) {
 // Per-device set-up, done once with the caller's device current: look up the
 // address of g_sort_scratch on that device and raise the downsweep kernel's
 // shared-memory limit there.  A failure is reported and retried next call.
+// The cached address belongs to the device's primary context: it is not valid
+// after that context is destroyed (cudaDeviceReset), after which this entry
+// point must not be called again in the process.
 int device_scratch(uint32_t** out, char* err, size_t err_len) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -81,8 +84,16 @@ extern "C" int bh_sort_keys_static(uint64_t* keys, uint32_t* idx, uint64_t* keys
     if (n == 0) return BH_OK;
     if (!keys || !idx || !keys_tmp || !idx_tmp)
         return report(err, err_len, BH_E_INVAL, "null buffer pointer");
-    if ((void*)keys == (void*)keys_tmp || (void*)idx == (void*)idx_tmp)
-        return report(err, err_len, BH_E_INVAL, "keys_tmp/idx_tmp must not alias keys/idx");
+    {  // the four buffers must be pairwise disjoint byte ranges
+        const uintptr_t lo[4] = {(uintptr_t)keys, (uintptr_t)idx, (uintptr_t)keys_tmp, (uintptr_t)idx_tmp};
+        const uintptr_t len[4] = {(uintptr_t)n * 8u, (uintptr_t)n * 4u, (uintptr_t)n * 8u, (uintptr_t)n * 4u};
+        static const char* const name[4] = {"keys", "idx", "keys_tmp", "idx_tmp"};
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (lo[a] < lo[b] + len[b] && lo[b] < lo[a] + len[a])
+                    return report(err, err_len, BH_E_INVAL, "%s and %s overlap (the four buffers must be disjoint)",
+                                  name[a], name[b]);
+    }
     if (sort_scratch_words(n) > kStaticWords)
         return report(err, err_len, BH_E_INVAL, "sort of n = %lld needs %lld scratch words, %lld available",
                       (long long)n, (long long)sort_scratch_words(n), (long long)kStaticWords);

@@ -111,6 +111,13 @@ def test_rejects_size_over_max_and_bad_buffers():
     with pytest.raises(bh.BHError) as e:
         bh.bh_sort_keys_static(k1, i1, k1, i1.clone())
     assert e.value.code == bh.BH_E_INVAL
+    # partial overlaps: keys_tmp starting inside keys, idx sharing keys' bytes
+    big = torch.zeros(20, dtype=torch.int64, device="cuda")
+    for args in ((big[0:10], i1, big[5:15], i1.clone()),
+                 (big[0:10], big[0:10].view(torch.int32)[0:10], big[10:20], i1.clone())):
+        with pytest.raises(bh.BHError) as e:
+            bh.bh_sort_keys_static(*args)
+        assert e.value.code == bh.BH_E_INVAL and "overlap" in str(e.value)
     k0 = torch.zeros(0, dtype=torch.int64, device="cuda")
     i0 = torch.zeros(0, dtype=torch.int32, device="cuda")
     assert bh.bh_sort_keys_static(k0, i0, k0.clone(), i0.clone()) == bh.BH_OK
