@@ -182,13 +182,13 @@ class Clocks:
 TRAFFIC_SOURCES = ("force32.cu", "force_common.cuh", "walk.cu")
 
 
-def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning: dict):
+def recorded_traffic(kernel: str, workload: str, n: int, key_frame: int, tuning: dict, path: str | None = None):
     """DRAM bytes per launch of the force kernel from the committed ncu
     captures (one record per launch setting captured), if one was taken on
     this workload (size, frame, n_g and launch settings) with the kernel
     source as it is now (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     try:
         recs = json.load(open(path))[kernel]
     except (OSError, KeyError, ValueError):

@@ -48,7 +48,9 @@ extern "C" {
 #define BH_E_CUDA 3          /* a CUDA call failed                           */
 #define BH_E_LIST_OVERFLOW 4 /* list or node buffer too small (needed size   */
                              /* is reported by bh_get_sizes)                 */
-#define BH_E_TIMEOUT 5       /* a bounded device wait gave up                */
+#define BH_E_TIMEOUT 5       /* reserved: no kernel of this library waits on */
+                             /* the device (no spin on a flag, a barrier or  */
+                             /* another kernel), so it is never returned     */
 #define BH_E_STATE 6         /* call out of order (e.g. forces before lists) */
 
 #define BH_PREC_FP64 0 /* plain FP64 force kernel                              */
@@ -85,7 +87,14 @@ typedef struct bh_ctx bh_ctx;
  *             r_coll / r_min (r_min: the smallest particle radius of the
  *             patch), so no contact pair is missed.  Needs r > 0 for every
  *             particle (BH_E_INVAL otherwise, at the list build).
- *  list_capacity  reserved, 0. */
+ *  list_capacity  most interaction-list entries one list build may hold:
+ *             particle-list entries (opened leaves) + cell-list entries
+ *             (accepted nodes) + list particles (the leaves' particles, the
+ *             form the force kernels read); 0 = no limit (buffers grow on
+ *             demand).  A build that needs more fails with
+ *             BH_E_LIST_OVERFLOW before writing any list; bh_get_sizes then
+ *             reports the sizes it needs, and bh_set_list_capacity changes
+ *             the limit. */
 typedef struct {
     double theta, eps, G, M_central, r_coll, kappa, eta, dt;
     int n_g, n_leaf, order, precision;
@@ -100,6 +109,31 @@ typedef struct {
     double *ax, *ay, *az;
     int64_t n;
 } bh_particles;
+
+/* Stages of the path timed by bh_set_timing (indices of bh_counters.stage_ms):
+ *  KEYS      cylindrical coordinates (key_frame 1), root box, Morton keys   (a1)
+ *  SORT      stable radix sort of (key, index)                              (a2)
+ *  PERMUTE   gather of the particle arrays into key order                   (a2)
+ *  TREE      octree levels, integer node boxes and walk records             (a3)
+ *  MOMENTS   node moments (every evaluation)                                (a4)
+ *  GROUPS    groups                                                         (a5)
+ *  LISTS     tree walk, list expansion and the FP32 kernel's group order (a6, a7)
+ *  SPLIT     FP32 path: hi/lo split of the particles (every evaluation)
+ *  FORCE     force kernel                                                   (a8)
+ *  CONTACTS  FP32 path: the FP64 contact pass after the force kernel        (a8)
+ *  UPDATE    leapfrog kicks and drift                                       (a9) */
+#define BH_STAGE_KEYS 0
+#define BH_STAGE_SORT 1
+#define BH_STAGE_PERMUTE 2
+#define BH_STAGE_TREE 3
+#define BH_STAGE_MOMENTS 4
+#define BH_STAGE_GROUPS 5
+#define BH_STAGE_LISTS 6
+#define BH_STAGE_SPLIT 7
+#define BH_STAGE_FORCE 8
+#define BH_STAGE_CONTACTS 9
+#define BH_STAGE_UPDATE 10
+#define BH_N_STAGES 11
 
 /* Interaction and timing counters of the last force evaluation. */
 typedef struct {
@@ -123,6 +157,12 @@ typedef struct {
     int64_t n_d2h_bytes; /* ... and device -> host (ids, and masses on the way
                           * back, only for calls with a list-constructing
                           * evaluation: other steps leave them unchanged)        */
+    double stage_ms[BH_N_STAGES];     /* device time of each stage (CUDA events on the
+                                       * context's stream) summed over the calls made
+                                       * with timing on since the last reset
+                                       * (bh_get_timing); steps run as a captured
+                                       * graph are not timed                     */
+    int64_t stage_calls[BH_N_STAGES]; /* timed calls of each stage                */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
@@ -191,7 +231,9 @@ int bh_step_host(bh_ctx* ctx, bh_particles* host, int nsteps);
 /* Wait for the stream and report device-side errors. */
 int bh_sync(bh_ctx* ctx);
 
-/* Sizes of the current structures (any pointer may be NULL). */
+/* Sizes of the current structures (any pointer may be NULL).  After a list
+ * build that failed with BH_E_LIST_OVERFLOW the three list sizes are the ones
+ * that build needed (their sum is the capacity it asked for). */
 int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp_entries,
                  int64_t* n_pc_entries, int64_t* n_list_particles);
 
@@ -210,13 +252,20 @@ int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int
 int bh_get_moments(bh_ctx* ctx, double* M, double* c3, double* Q6);
 int bh_get_groups(bh_ctx* ctx, int32_t* group_nodes);
 int bh_get_lists(bh_ctx* ctx, int64_t* pp_off, int32_t* pp_ids, int64_t* pc_off, int32_t* pc_ids);
+/* Counters; when timing is on this synchronises the stream to read the
+ * stage events. */
 int bh_get_counters(bh_ctx* ctx, bh_counters* out);
 
-/* Measurement hooks.  bh_set_timing(ctx, 1) makes every force-kernel launch
- * record a pair of CUDA events on the context's stream (launches inside a
- * captured graph step are not timed); bh_get_timing synchronises the stream
- * and returns the summed kernel time (ms) and the number of timed launches,
- * clearing them when reset != 0. */
+/* Change list_capacity (see bh_params) for later list builds; entries >= 0.
+ * Errors: BH_E_INVAL for entries < 0. */
+int bh_set_list_capacity(bh_ctx* ctx, int64_t entries);
+
+/* Measurement hooks.  bh_set_timing(ctx, 1) makes every force-kernel launch,
+ * and every stage of the path (BH_STAGE_*), record a pair of CUDA events on
+ * the context's stream (work inside a captured graph step is not timed);
+ * bh_get_timing synchronises the stream and returns the summed force-kernel
+ * time (ms) and the number of timed launches, clearing them and the stage
+ * times of bh_counters when reset != 0. */
 int bh_set_timing(bh_ctx* ctx, int enable);
 int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int reset);
 
@@ -250,6 +299,13 @@ typedef struct {
                           order is applied within windows of w consecutive
                           groups (list order = Morton order), so the warps in
                           flight work on nearby groups whose list data share L2 */
+    int graph_contact_room; /* contact candidates a graph step may hold: 0 = twice
+                          the last eager evaluation's count + 65536; n > 0 = n.
+                          More candidates than that in a graph step are
+                          dropped and reported as BH_E_LIST_OVERFLOW at the
+                          next synchronising call (that step's contact terms
+                          are then incomplete); eager evaluations always grow
+                          the buffer instead */
 } bh_tuning;
 /* Errors: BH_E_INVAL for a value out of range (n_g < n_leaf included). */
 int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t);
@@ -291,6 +347,16 @@ int bh_get_diagnostics(bh_ctx* ctx, const bh_particles* p, bh_diagnostics* out);
  * (bh_set_timing): busy fraction = sum over warps of (finish - start) /
  * (warps x (last finish - first start)).  BH_E_STATE if there is none. */
 int bh_get_balance(bh_ctx* ctx, double* busy_fraction);
+
+/* Peak arithmetic rate of this device, measured: a kernel of independent
+ * fused multiply-add chains on every SM (FP32 for kind BH_PEAK_FP32, FP64 for
+ * BH_PEAK_FP64), timed with CUDA events after a warm-up launch (2 flops per
+ * FMA).  Runs on the legacy default stream of the current device and
+ * synchronises.  Allocates a small output buffer (freed before returning).
+ * Errors: BH_E_INVAL for an unknown kind or NULL tflops, BH_E_CUDA. */
+#define BH_PEAK_FP32 0
+#define BH_PEAK_FP64 1
+int bh_measure_peak(int kind, double* tflops);
 
 /* Stable radix sort that allocates nothing.  The paper has no counterpart:
  * this is the sort of bh_build_tree (Sec. 4.2 step 3a, same kernels, same

@@ -22,9 +22,13 @@ SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_se
            "bh_compute_forces", "bh_step", "bh_step_host", "bh_sync", "bh_get_sizes", "bh_get_keys",
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
            "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_set_tuning", "bh_get_tuning", "bh_autotune",
-           "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static", "bh_split_f32")
+           "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static", "bh_split_f32",
+           "bh_set_list_capacity", "bh_measure_peak")
 BH_SCHED_GRID, BH_SCHED_STATIC, BH_SCHED_DYNAMIC = 0, 1, 2
 BH_SORT_STATIC_MAX_N = 4194304
+STAGES = ("keys", "sort", "permute", "tree", "moments", "groups", "lists", "split", "force", "contacts", "update")
+BH_N_STAGES = len(STAGES)
+BH_PEAK_FP32, BH_PEAK_FP64 = 0, 1
 
 
 class bh_params(ctypes.Structure):
@@ -44,7 +48,8 @@ class bh_particles(ctypes.Structure):
 class bh_counters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
                                                "n_contacts", "n_pp_far", "n_one_walk_builds",
-                                               "n_h2d_bytes", "n_d2h_bytes")]
+                                               "n_h2d_bytes", "n_d2h_bytes")] + [
+        ("stage_ms", ctypes.c_double * BH_N_STAGES), ("stage_calls", ctypes.c_int64 * BH_N_STAGES)]
 
 
 class bh_diagnostics(ctypes.Structure):
@@ -55,7 +60,8 @@ class bh_diagnostics(ctypes.Structure):
 
 
 class bh_tuning(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph", "order_window")]
+    _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph", "order_window",
+                                            "graph_contact_room")]
 
 
 _lib = None
@@ -106,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.bh_get_diagnostics.argtypes = [P, ctypes.POINTER(bh_particles), ctypes.POINTER(bh_diagnostics)]
     lib.bh_sort_keys_static.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_char_p, ctypes.c_size_t]
     lib.bh_split_f32.argtypes = [P, P, P, ctypes.c_int64, P]
+    lib.bh_set_list_capacity.argtypes = [P, ctypes.c_int64]
+    lib.bh_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     _lib = lib
     return lib
 
@@ -189,6 +197,17 @@ def bh_split_f32(v, hi, lo, stream=None):
     if rc != BH_OK:
         raise BHError(rc, "bh_split_f32 failed")
     return rc
+
+
+def bh_measure_peak(kind: int) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (kind BH_PEAK_FP32
+    or BH_PEAK_FP64)."""
+    lib = load()
+    v = ctypes.c_double()
+    rc = lib.bh_measure_peak(int(kind), ctypes.byref(v))
+    if rc != BH_OK:
+        raise BHError(rc, "bh_measure_peak failed")
+    return v.value
 
 
 class Particles:
@@ -349,9 +368,16 @@ class Context:
         return L
 
     def bh_get_counters(self):
+        """Counters; stage_ms / stage_calls are dicts keyed by stage name."""
         c = bh_counters()
         self._chk(self.lib.bh_get_counters(self.h, ctypes.byref(c)))
-        return {f: getattr(c, f) for f, _ in bh_counters._fields_}
+        out = {f: getattr(c, f) for f, _ in bh_counters._fields_ if not f.startswith("stage_")}
+        out["stage_ms"] = dict(zip(STAGES, c.stage_ms[:]))
+        out["stage_calls"] = dict(zip(STAGES, c.stage_calls[:]))
+        return out
+
+    def bh_set_list_capacity(self, entries: int):
+        return self._chk(self.lib.bh_set_list_capacity(self.h, int(entries)))
 
     def bh_set_timing(self, enable: bool = True):
         return self._chk(self.lib.bh_set_timing(self.h, 1 if enable else 0))

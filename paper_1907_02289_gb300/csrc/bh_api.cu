@@ -77,6 +77,50 @@ int timing_end(Ctx* c) {
     return BH_OK;
 }
 
+int stage_begin(Ctx* c, int stage) {
+    if (!c->timing || c->capturing) return BH_OK;
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    if (!a || !b) return fail(c, BH_E_CUDA, "cudaEventCreate failed");
+    BH_CUDA(c, cudaEventRecord(a, c->stream));
+    c->stage_open.push_back((int)c->ev_stage.size());
+    c->ev_stage.push_back({stage, a, b});
+    return BH_OK;
+}
+
+int stage_end(Ctx* c) {
+    if (!c->timing || c->capturing || c->stage_open.empty()) return BH_OK;
+    const int k = c->stage_open.back();
+    c->stage_open.pop_back();
+    BH_CUDA(c, cudaEventRecord(c->ev_stage[k].b, c->stream));
+    return BH_OK;
+}
+
+// Read the recorded stage events into the sums (synchronises the stream).
+static int read_stage_events(Ctx* c) {
+    if (c->ev_stage.empty()) return BH_OK;
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t keep = c->stage_open.empty() ? c->ev_stage.size() : (size_t)c->stage_open.front();
+    for (size_t k = 0; k < keep; ++k) {
+        float ms = 0.f;
+        BH_CUDA(c, cudaEventElapsedTime(&ms, c->ev_stage[k].a, c->ev_stage[k].b));
+        c->stage_ms[c->ev_stage[k].stage] += ms;
+        c->stage_calls[c->ev_stage[k].stage]++;
+        c->ev_pool.push_back(c->ev_stage[k].a);
+        c->ev_pool.push_back(c->ev_stage[k].b);
+    }
+    c->ev_stage.erase(c->ev_stage.begin(), c->ev_stage.begin() + keep);
+    for (int& k : c->stage_open) k -= (int)keep;
+    return BH_OK;
+}
+
+// Run a stage under its timing events.
+#define BH_STAGE(c, id, expr)              \
+    do {                                   \
+        BH_TRY(stage_begin((c), (id)));    \
+        BH_TRY(expr);                      \
+        BH_TRY(stage_end(c));              \
+    } while (0)
+
 // Patch layout: offsets on host and device, per-patch root boxes, sort tiles.
 int setup_patches(Ctx* c, int n_patches, const int64_t* off) {
     c->n_patches = n_patches;
@@ -117,6 +161,7 @@ int check_params(Ctx* c, const bh_params* p) {
         return fail(c, BH_E_INVAL, "key_frame must be 0 (Cartesian) or 1 (cylindrical)");
     if (!(p->eps >= 0.0) || !(p->r_coll >= 0.0) || !(p->dt >= 0.0))
         return fail(c, BH_E_INVAL, "eps, r_coll and dt must be >= 0");
+    if (p->list_capacity < 0) return fail(c, BH_E_INVAL, "list_capacity must be >= 0");
     return BH_OK;
 }
 
@@ -154,7 +199,7 @@ int build_tree(Ctx* c, bh_particles* p) {
         const int64_t off[2] = {0, p->n};
         BH_TRY(setup_patches(c, 1, off));
     }
-    BH_TRY(stage_keys(c, p));
+    BH_STAGE(c, BH_STAGE_KEYS, stage_keys(c, p));
     BH_TRY(read_status(c));
     c->h_box.resize(8 * (size_t)c->n_patches);
     BH_CUDA(c, cudaMemcpyAsync(c->h_box.data(), c->d_box, c->h_box.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -164,19 +209,21 @@ int build_tree(Ctx* c, bh_particles* p) {
         for (int q = 0; q < c->n_patches; ++q)
             if (!(c->h_box[8 * q + 1] > 0.0))
                 return fail(c, BH_E_INVAL, "the cylindrical key frame needs every particle off the axis (r > 0)");
-    BH_TRY(stage_sort(c));
-    BH_TRY(stage_permute(c, p));
+    BH_STAGE(c, BH_STAGE_SORT, stage_sort(c));
+    BH_STAGE(c, BH_STAGE_PERMUTE, stage_permute(c, p));
+    BH_TRY(stage_begin(c, BH_STAGE_TREE));
     BH_TRY(stage_octree(c));
     BH_TRY(stage_boxes(c));
+    BH_TRY(stage_end(c));
     BH_TRY(stage_moments(c, p));
-    BH_TRY(stage_groups(c));
+    BH_STAGE(c, BH_STAGE_GROUPS, stage_groups(c));
     c->have_tree = true;
     return BH_OK;
 }
 
 int make_lists(Ctx* c) {
     if (!c->have_tree) return fail(c, BH_E_STATE, "bh_make_lists needs a tree (call bh_build_tree)");
-    BH_TRY(stage_lists(c));
+    BH_STAGE(c, BH_STAGE_LISTS, stage_lists(c));
     c->have_lists = true;
     c->graph_ok = false;
     c->evals_since_build = 0;
@@ -231,7 +278,8 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
         // inside the graph the contact pass cannot grow its buffer: leave room
         // for twice the candidates of the last eager evaluation
         if (c->prm.precision == BH_PREC_FP32 && c->prm.r_coll > 0.0) {
-            const size_t want = (size_t)(2 * c->n_contacts + 65536);
+            const size_t want = c->tune.graph_contact_room > 0 ? (size_t)c->tune.graph_contact_room
+                                                               : (size_t)(2 * c->n_contacts + 65536);
             if (c->contacts.cap < want) BH_TRY(grow(c, c->contacts, want, "contact pairs"));
         }
         // capture on a private stream (the legacy default stream cannot be
@@ -299,6 +347,7 @@ int check_tuning(Ctx* c, const bh_tuning* t) {
     if ((t->order_by_cost != 0 && t->order_by_cost != 1) || (t->graph != 0 && t->graph != 1))
         return fail(c, BH_E_INVAL, "order_by_cost and graph must be 0 or 1");
     if (t->order_window < 0) return fail(c, BH_E_INVAL, "order_window must be >= 0");
+    if (t->graph_contact_room < 0) return fail(c, BH_E_INVAL, "graph_contact_room must be >= 0");
     return BH_OK;
 }
 
@@ -312,6 +361,7 @@ void apply_tuning(Ctx* c, const bh_tuning* t) {
     c->tune.order_by_cost = t->order_by_cost;
     c->tune.graph = t->graph;
     c->tune.order_window = t->order_window;
+    c->tune.graph_contact_room = t->graph_contact_room;
     c->graph_ok = false;
     (void)relist;
 }
@@ -324,6 +374,7 @@ void read_tuning(const Ctx* c, bh_tuning* t) {
     t->order_by_cost = c->tune.order_by_cost;
     t->graph = c->tune.graph;
     t->order_window = c->tune.order_window;
+    t->graph_contact_room = c->tune.graph_contact_room;
 }
 
 // Elapsed device time of fn() on the context's stream (ms).
@@ -805,9 +856,9 @@ int bh_get_sizes(bh_ctx* ctx, int64_t* n_nodes, int64_t* n_groups, int64_t* n_pp
     if (!c) return BH_E_INVAL;
     if (n_nodes) *n_nodes = c->have_tree ? c->n_nodes : 0;
     if (n_groups) *n_groups = c->have_tree ? c->n_groups : 0;
-    if (n_pp) *n_pp = c->have_lists ? c->n_pp : 0;
-    if (n_pc) *n_pc = c->have_lists ? c->n_pc : 0;
-    if (n_jj) *n_jj = c->have_lists ? c->n_jj : 0;
+    if (n_pp) *n_pp = c->have_lists ? c->n_pp : c->list_overflowed ? c->need_pp : 0;
+    if (n_pc) *n_pc = c->have_lists ? c->n_pc : c->list_overflowed ? c->need_pc : 0;
+    if (n_jj) *n_jj = c->have_lists ? c->n_jj : c->list_overflowed ? c->need_jj : 0;
     return BH_OK;
 }
 
@@ -926,6 +977,19 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_one_walk_builds = c->n_one_walk_builds;
     out->n_h2d_bytes = c->h2d_bytes;
     out->n_d2h_bytes = c->d2h_bytes;
+    BH_TRY(bh::read_stage_events(c));
+    for (int s = 0; s < BH_N_STAGES; ++s) {
+        out->stage_ms[s] = c->stage_ms[s];
+        out->stage_calls[s] = c->stage_calls[s];
+    }
+    return BH_OK;
+}
+
+int bh_set_list_capacity(bh_ctx* ctx, int64_t entries) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (entries < 0) return bh::fail(c, BH_E_INVAL, "list capacity must be >= 0");
+    c->prm.list_capacity = entries;
     return BH_OK;
 }
 
@@ -954,6 +1018,11 @@ int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int re
             c->ev_pool.push_back(pr.second);
         }
         c->ev_force.clear();
+        BH_TRY(bh::read_stage_events(c));
+        for (int s = 0; s < BH_N_STAGES; ++s) {
+            c->stage_ms[s] = 0.0;
+            c->stage_calls[s] = 0;
+        }
     }
     return BH_OK;
 }

@@ -57,6 +57,7 @@ struct Tuning {
     int order_by_cost = 1;   // within a size class, largest estimated cost first
     int graph = 0;           // capture list-reusing steps of bh_step in a CUDA graph
     int order_window = 0;    // > 0: size-class order within windows of this many groups
+    int graph_contact_room = 0;  // > 0: contact candidates a graph step may hold (0: automatic)
 };
 
 struct Ctx {
@@ -74,9 +75,23 @@ struct Ctx {
     int64_t n_launches = 0;    // kernels launched by this context
 
     // optional CUDA-event timing of the force kernel (one event pair per launch)
+    // and of every stage (BH_STAGE_*)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_force;
+    struct StageEv {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<StageEv> ev_stage;       // recorded, not yet read
+    std::vector<int> stage_open;         // indices into ev_stage of stages begun, not ended
+    double stage_ms[BH_N_STAGES] = {};   // read stage times, summed since the last reset
+    int64_t stage_calls[BH_N_STAGES] = {};
+
+    // list capacity (bh_params.list_capacity; 0 = none) and the sizes a build
+    // that exceeded it needed
+    bool list_overflowed = false;
+    int64_t need_pp = 0, need_pc = 0, need_jj = 0;
 
     // patches: independent particle sets, each with its own root box and
     // tree (a forest whose roots are nodes 0..n_patches-1); 1 for one set
@@ -241,9 +256,12 @@ int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of partic
 int build_order32(Ctx* c);                         // FP32 kernel's group order (per list build)
 int stage_force(Ctx* c, bh_particles* p, bool add_central);
 
-// bh_api.cu: force-kernel timing (no-ops unless enabled)
+// bh_api.cu: force-kernel and stage timing (no-ops unless enabled, or while
+// capturing a graph); stage_end closes the innermost stage begun
 int timing_begin(Ctx* c);
 int timing_end(Ctx* c);
+int stage_begin(Ctx* c, int stage);
+int stage_end(Ctx* c);
 
 // update.cu
 int stage_kick(Ctx* c, bh_particles* p, double h);

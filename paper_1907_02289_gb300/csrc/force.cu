@@ -210,12 +210,14 @@ int stage_force(Ctx* c, bh_particles* p, bool add_central) {
     if (c->prm.precision == BH_PREC_FP64) {
         const unsigned nb = blocks_for(ng, kWarps);
         BH_TRY(timing_begin(c));
+        BH_TRY(stage_begin(c, BH_STAGE_FORCE));
         k_force64<<<nb, 32 * kWarps, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p, c->JJ.p,
                                                      c->cnt_c.p, c->C.p, p->x, p->y, p->z, p->vx, p->vy, p->vz,
                                                      p->m, c->M.p, c->cx.p, c->cy.p, c->cz.p, c->Q.p, fp,
                                                      add_central, p->ax, p->ay, p->az, (uint32_t)c->n,
                                                      c->n_nodes, c->d_status);
         BH_LAUNCH(c);
+        BH_TRY(stage_end(c));
         return timing_end(c);
     }
     // the hi/lo split and the FP32 records were made by stage_moments

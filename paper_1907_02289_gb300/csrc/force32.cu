@@ -1013,6 +1013,7 @@ int build_order32(Ctx* c) {
 
 namespace {
 int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, unsigned nb) {
+    BH_TRY(stage_begin(c, BH_STAGE_CONTACTS));
     unsigned long long* acc = c->contact_acc.p;
     k_contacts_clear<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, c->d_status);
     BH_LAUNCH(c);
@@ -1022,7 +1023,7 @@ int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, 
     k_contacts_apply<<<nb, 128, 0, c->stream>>>(A.contacts, A.ncontact, A.contact_cap, acc, p->ax, p->ay, p->az,
                                                 c->d_status);
     BH_LAUNCH(c);
-    return BH_OK;
+    return stage_end(c);
 }
 }  // namespace
 
@@ -1099,8 +1100,10 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     c->f32_blocks = nb;
     for (int attempt = 0; attempt < 2; ++attempt) {
         BH_TRY(timing_begin(c));
+        BH_TRY(stage_begin(c, BH_STAGE_FORCE));
         kern<<<nb, 32 * W, smem, c->stream>>>(A);
         BH_LAUNCH(c);
+        BH_TRY(stage_end(c));
         BH_TRY(timing_end(c));
         if (!contact) break;
         if (c->capturing) {

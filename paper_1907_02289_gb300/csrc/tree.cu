@@ -448,7 +448,10 @@ int stage_moments(Ctx* c, const bh_particles* p) {
         // FP32 path: hi/lo split of the particles, then FP32 moments with a
         // hi/lo centre (no FP64 arithmetic per node)
         BH_TRY(grow(c, c->cell32, (size_t)nn * 3, "FP32 cell records"));
+        BH_TRY(stage_begin(c, BH_STAGE_SPLIT));
         BH_TRY(stage_split(c, p));
+        BH_TRY(stage_end(c));
+        BH_TRY(stage_begin(c, BH_STAGE_MOMENTS));
         for (int lev = depth - 1; lev >= 0; --lev) {
             const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
             if (c->prm.order >= 2)
@@ -461,13 +464,14 @@ int stage_moments(Ctx* c, const bh_particles* p) {
                                                                             c->phi.p, c->plo.p, c->cell32.p);
             BH_LAUNCH(c);
         }
-        return BH_OK;
+        return stage_end(c);
     }
     BH_TRY(grow(c, c->M, (size_t)nn, "moments M"));
     BH_TRY(grow(c, c->cx, (size_t)nn, "moments cx"));
     BH_TRY(grow(c, c->cy, (size_t)nn, "moments cy"));
     BH_TRY(grow(c, c->cz, (size_t)nn, "moments cz"));
     BH_TRY(grow(c, c->Q, (size_t)nn * 6, "moments Q"));
+    BH_TRY(stage_begin(c, BH_STAGE_MOMENTS));
     for (int lev = depth - 1; lev >= 0; --lev) {
         const int64_t ls = c->lvl_start[lev], cnt = c->lvl_start[lev + 1] - ls;
         const unsigned nb = blocks_for(cnt, 128);
@@ -481,7 +485,7 @@ int stage_moments(Ctx* c, const bh_particles* p) {
 #undef BH_MOM
         BH_LAUNCH(c);
     }
-    return BH_OK;
+    return stage_end(c);
 }
 
 int stage_groups(Ctx* c) {

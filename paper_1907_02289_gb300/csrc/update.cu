@@ -95,16 +95,18 @@ int stage_diagnostics(Ctx* c, const bh_particles* p, double* host_out) {
 }
 
 int stage_kick(Ctx* c, bh_particles* p, double h) {
+    BH_TRY(stage_begin(c, BH_STAGE_UPDATE));
     k_kick<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, p->ax, p->ay, p->az, p->vx, p->vy, p->vz);
     BH_LAUNCH(c);
-    return BH_OK;
+    return stage_end(c);
 }
 
 int stage_kick_drift(Ctx* c, bh_particles* p, double h, double dt) {
+    BH_TRY(stage_begin(c, BH_STAGE_UPDATE));
     k_kick_drift<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, dt, p->ax, p->ay, p->az, p->vx, p->vy,
                                                                p->vz, p->x, p->y, p->z);
     BH_LAUNCH(c);
-    return BH_OK;
+    return stage_end(c);
 }
 
 }  // namespace bh

@@ -395,7 +395,8 @@ int stage_lists(Ctx* c) {
     // at most 4x the previous lists' storage; else (and after an overflow)
     // a count walk and a fill walk.
     const int64_t capP = c->walk_cap_p, capC = c->walk_cap_c;
-    bool stash = capP > 0 && capC > 0 &&
+    // (a list capacity bounds the entries held, so it rules out the slots)
+    bool stash = capP > 0 && capC > 0 && c->prm.list_capacity == 0 &&
                  (double)ng * (double)(capP + capC) <= 4.0 * (double)(c->n_pp + c->n_pc) + 1.0e6;
     if (stash) {
         BH_TRY(grow(c, c->stash_p, (size_t)(ng * capP), "stashed particle lists"));
@@ -426,6 +427,17 @@ int stage_lists(Ctx* c) {
     c->n_jj = (int64_t)h[2];
     c->n_int_pp = (int64_t)h[8];
     c->n_int_pc = (int64_t)h[9];
+    c->list_overflowed = false;
+    if (c->prm.list_capacity > 0 && c->n_pp + c->n_pc + c->n_jj > c->prm.list_capacity) {
+        c->list_overflowed = true;
+        c->need_pp = c->n_pp;
+        c->need_pc = c->n_pc;
+        c->need_jj = c->n_jj;
+        return fail(c, BH_E_LIST_OVERFLOW,
+                    "the lists need %lld entries (%lld leaf, %lld cell, %lld list-particle), list_capacity is %lld",
+                    (long long)(c->n_pp + c->n_pc + c->n_jj), (long long)c->n_pp, (long long)c->n_pc,
+                    (long long)c->n_jj, (long long)c->prm.list_capacity);
+    }
     BH_TRY(grow(c, c->P, (size_t)c->n_pp + 1, "particle lists"));
     BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
     BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));

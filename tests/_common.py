@@ -20,23 +20,38 @@ def force_errors(a, ref):
     return rel, rmsn, r
 
 
+# The FP64 path is held to its tolerance everywhere; the FP32 path's gate has
+# the near-cancelling provision of the error metric (tree part only): every
+# particle with |a_ref| >= NEAR_CANCEL x median|a_ref| must meet the relative
+# tolerance, and the few below that cut (whose FP32 sums of terms far larger
+# than the total carry a large relative error) meet it in the rms-normalised
+# form |da_i| / rms|a_ref| instead.
+NEAR_CANCEL = 1e-2
+FP64_TOL_MAX = 1e-9  # tolerances at or below this are FP64 gates: no provision
+
+
 def assert_force_close(a, ref, tol, what=""):
-    """Gate: max relative error <= tol.  Where particles whose acceleration
-    nearly cancels (|a_ref| < 0.1 x median: an FP32 sum of terms ~100x larger
-    than the total carries a relative error ~1e-7 x median / |a|) are the only
-    ones above tol, the gate is the rms-normalised max |da_i| / rms|a_ref|
-    <= tol instead, and every particle at |a_ref| >= 1e-2 x median must still
-    be within 2 tol."""
+    """Gate of the force error.  FP64 tolerances (<= FP64_TOL_MAX): max
+    relative error <= tol over every particle.  FP32 tolerances: max relative
+    error <= tol over every particle with |a_ref| >= NEAR_CANCEL x median, and
+    rms-normalised error <= tol for the particles below that cut.  Returns
+    (the form used for the particles below the cut or "rel", max relative
+    error over the gated particles)."""
     rel, rmsn, r = force_errors(a, ref)
-    if rel.max() <= tol:
-        return "rel", float(rel.max())
+    if tol <= FP64_TOL_MAX:
+        i = int(np.argmax(rel))
+        assert rel[i] <= tol, f"{what}: max rel err {rel[i]:.3e} > {tol} (particle {i})"
+        return "rel", float(rel[i])
     med = np.median(r)
-    above = rel > tol
-    assert r[above].max() < 0.1 * med, (
-        f"{what}: max rel err {rel.max():.3e} > {tol} at |a| = {r[above].max() / med:.3f} x median")
-    assert rel[r >= 1e-2 * med].max() <= 2 * tol, f"{what}: rel err {rel[r >= 1e-2 * med].max():.3e} > 2 x {tol}"
-    assert rmsn.max() <= tol, f"{what}: max rms-normalised err {rmsn.max():.3e} > {tol}"
-    return "rms", float(rmsn.max())
+    ok = r >= NEAR_CANCEL * med
+    worst = float(rel[ok].max()) if ok.any() else 0.0
+    assert worst <= tol, (
+        f"{what}: max rel err {worst:.3e} > {tol} over particles with |a| >= {NEAR_CANCEL} x median "
+        f"({int((rel[ok] > tol).sum())} above)")
+    if (~ok).any():
+        assert rmsn[~ok].max() <= tol, f"{what}: rms-normalised err {rmsn[~ok].max():.3e} > {tol} (near-cancelling)"
+        return "rms", worst
+    return "rel", worst
 
 
 def gpu_build(P, prm, precision=None, forces=True, flags=None):

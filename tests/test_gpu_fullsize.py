@@ -108,6 +108,33 @@ def test_ring_2p20_fp64_forces_and_ten_steps():
     assert dx <= 200 * prm["dt"] ** 2 * 1e-12 * a_tree + 1e-14
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_ring_2p20_list_reusing_evaluation(precision, tol):
+    """2^20 ring: after two leapfrog steps on the lists of the first build
+    (evaluations 1 and 2 reuse them), one more list-reusing evaluation on the
+    GPU's own state (positions and velocities as the steps left them) against
+    the oracle's list-reusing evaluation (Sec. 4.2: moments refreshed, the
+    first build's order, groups and lists kept) on that same state."""
+    from paper_1907_02289_gb300 import bh
+    P, prm = synth.make("ring1m_fp64")
+    op = orc_params(prm)
+    ctx = bh.Context(**dict(prm, precision=precision))
+    D = bh.Particles(P)
+    ctx.bh_step(D, 2)
+    ctx.bh_sync()
+    assert ctx.bh_get_counters()["n_rebuilds"] == 1
+    ctx.bh_compute_forces(D, bh.BH_FORCE_TREE_ONLY)
+    ctx.bh_sync()
+    S = orc.rebuild(P, op)
+    now = D.numpy()
+    assert np.array_equal(now["id"], S.P["id"])
+    L = ctx.bh_get_lists()
+    assert np.array_equal(L["P"], S.lists["P"]) and np.array_equal(L["C"], S.lists["C"])
+    S.P = {f: np.ascontiguousarray(now[f]) for f in orc.FIELDS}
+    orc.refresh(S, op)
+    assert_force_close(accel_of(D), orc.tree_forces(S, op), tol, f"2^20 list-reusing evaluation, precision {precision}")
+
+
 def test_ring_2p24_fp32_vs_fp64_sample(capsys):
     """2^24 ring, theta 0.5: FP64 and FP32 forces on a 65,536-particle sample
     (rng(2)) against the oracle on the same lists."""

@@ -420,6 +420,53 @@ def test_tree_error_decreases_with_theta_and_order():
     assert errs[(2, 0.4)] < errs[(1, 0.4)] and errs[(2, 0.4)] < 1e-3
 
 
+# ---------------------------------------------------- list reuse (refresh) ----
+def test_refresh_keeps_lists_and_recomputes_moments_of_moved_particles():
+    """The list-reusing evaluation (Sec. 4.2): after the particles move, the
+    order, tree, groups and lists stay as built, and every node's moments are
+    those of its (moved) particles, summed directly."""
+    P, prm, S = _ring_state(5000)
+    lists0 = {k: v.copy() for k, v in S.lists.items()}
+    groups0, begin0 = S.groups.copy(), S.tree["begin"].copy()
+    rng = np.random.default_rng(9)
+    for c in "xyz":
+        S.P[c] = S.P[c] + rng.normal(0.0, 3e-5, len(S.P[c]))
+    orc.refresh(S, prm)
+    assert all(np.array_equal(S.lists[k], lists0[k]) for k in lists0)
+    assert np.array_equal(S.groups, groups0) and np.array_equal(S.tree["begin"], begin0)
+    t, mo, Q = S.tree, S.mom, S.P
+    x = np.stack([Q["x"], Q["y"], Q["z"]], 1); m = Q["m"]
+    for k in list(range(0, len(t["level"]), 37)) + [0]:
+        b, e = t["begin"][k], t["end"][k]
+        Mk = m[b:e].sum(); c = (m[b:e, None] * x[b:e]).sum(0) / Mk
+        assert math.isclose(mo["M"][k], Mk, rel_tol=1e-13)
+        assert np.allclose([mo["cx"][k], mo["cy"][k], mo["cz"][k]], c, rtol=0, atol=1e-14)
+        d = x[b:e] - c; d2 = (d * d).sum(1)
+        assert math.isclose(mo["Q"][k][3], (3 * m[b:e] * d[:, 0] * d[:, 1]).sum(), rel_tol=1e-9,
+                            abs_tol=1e-10 * Mk * (d2.max() + 1e-300))
+
+
+def test_reused_lists_at_theta_zero_still_cover_every_pair():
+    """At theta = 0 every list holds every leaf, so an evaluation on reused
+    lists after the particles moved is still the direct sum in the current
+    order (bit for bit), and a 4-step run with rebuilds every 4 evaluations
+    stays within rounding of one that rebuilds at every evaluation."""
+    P = synth.ring(1500, 12, r_in=0.999, r_out=1.001, phi_max=0.01)
+    kappa, eta = synth.contact_params(1e-3)
+    prm = orc.Params(theta=0.0, n_g=32, n_leaf=4, order=2, r_coll=2e-5, kappa=kappa, eta=eta, M_central=1.0,
+                     dt=1e-3, rebuild_every=4)
+    S = orc.rebuild(P, prm)
+    for c in "xyz":
+        S.P[c] = S.P[c] + 1e-3 * S.P["v" + c]
+    orc.refresh(S, prm)
+    assert np.array_equal(orc.tree_forces(S, prm), orc.direct(S.P, prm))
+    S4, a4, _ = orc.step(P, prm, 3)
+    S1, a1, _ = orc.step(P, orc.Params(**{**prm.__dict__, "rebuild_every": 1}), 3)
+    o4, o1 = np.argsort(S4.P["id"]), np.argsort(S1.P["id"])
+    assert np.allclose(a4[o4], a1[o1], rtol=1e-10, atol=0)
+    assert np.max(np.abs(S4.P["x"][o4] - S1.P["x"][o1])) < 1e-15
+
+
 # ----------------------------------------------------------------- step ----
 def test_step_circular_orbit():
     """One particle about M_c = 1: KDK keeps a circular orbit's radius to
