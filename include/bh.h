@@ -94,12 +94,23 @@ typedef struct bh_ctx bh_ctx;
  *             demand).  A build that needs more fails with
  *             BH_E_LIST_OVERFLOW before writing any list; bh_get_sizes then
  *             reports the sizes it needs, and bh_set_list_capacity changes
- *             the limit. */
+ *             the limit.
+ *  omega      rotation rate of the frame the particle arrays are kept in
+ *             (Sec. 4.4: coordinates rotating at the Kepler rate of the ring
+ *             centre, so that particles there barely move): 0 = inertial.
+ *             With omega != 0 every step's drift is followed by the rotation
+ *             of x, y and vx, vy by -omega dt about the z axis (x' = c x + s y,
+ *             y' = -s x + c y, c = cos(omega dt), s = sin(omega dt)), so the
+ *             arrays hold positions and inertial velocities in axes that turn
+ *             with the frame; keys, trees and lists are built there.  The
+ *             forces are rotation-invariant (the central mass sits on the axis),
+ *             so this is the inertial integration seen from the turning axes. */
 typedef struct {
     double theta, eps, G, M_central, r_coll, kappa, eta, dt;
     int n_g, n_leaf, order, precision;
     int rebuild_every, key_frame;
     int64_t list_capacity;
+    double omega;
 } bh_params;
 
 /* Caller-owned device arrays (see Conventions). */
@@ -121,7 +132,8 @@ typedef struct {
  *  SPLIT     FP32 path: hi/lo split of the particles (every evaluation)
  *  FORCE     force kernel                                                   (a8)
  *  CONTACTS  FP32 path: the FP64 contact pass after the force kernel        (a8)
- *  UPDATE    leapfrog kicks and drift                                       (a9) */
+ *  UPDATE    leapfrog kicks and drift                                       (a9)
+ *  REFINE    FP32 path: re-evaluation of ill-conditioned particles         (a8) */
 #define BH_STAGE_KEYS 0
 #define BH_STAGE_SORT 1
 #define BH_STAGE_PERMUTE 2
@@ -133,7 +145,8 @@ typedef struct {
 #define BH_STAGE_FORCE 8
 #define BH_STAGE_CONTACTS 9
 #define BH_STAGE_UPDATE 10
-#define BH_N_STAGES 11
+#define BH_STAGE_REFINE 11
+#define BH_N_STAGES 12
 
 /* Interaction and timing counters of the last force evaluation. */
 typedef struct {
@@ -157,6 +170,13 @@ typedef struct {
     int64_t n_d2h_bytes; /* ... and device -> host (ids, and masses on the way
                           * back, only for calls with a list-constructing
                           * evaluation: other steps leave them unchanged)        */
+    int64_t n_refined;   /* FP32 path: particles of the last force evaluation whose
+                          * FP32 sum was ill-conditioned, |a_i| < 0.12 G x the
+                          * root of the sum of the squares of its FP32 tile
+                          * partial sums (a particle whose neighbours' pulls
+                          * nearly cancel), and which the refinement pass
+                          * evaluated again over the same lists in df (pairs
+                          * of FP32 numbers) arithmetic; 0 on the FP64 path    */
     double stage_ms[BH_N_STAGES];     /* device time of each stage (CUDA events on the
                                        * context's stream) summed over the calls made
                                        * with timing on since the last reset
@@ -342,6 +362,24 @@ typedef struct {
     int64_t contact_candidates, contacts;
 } bh_diagnostics;
 int bh_get_diagnostics(bh_ctx* ctx, const bh_particles* p, bh_diagnostics* out);
+
+/* Self-gravity potential over the current lists (the energy the ring's
+ * diagnostics need besides bh_get_diagnostics' kinetic and central terms;
+ * Sec. 5.1 times steps with their diagnostics), in FP64 whatever the
+ * precision: node moments are recomputed in FP64 from the current positions,
+ * then for every particle phi_i = sum over its group's own particles and list
+ * particles (j != i) of the potential of Eq. (1)'s gravity,
+ *   -G m_j / sqrt(r^2 + eps^2) for r > r_coll, and inside r_coll (where the
+ *   gravity is held at its r_coll value) -G m_j / s - G m_j (r_coll^2 - r^2)
+ *   / (2 s^3), s^2 = r_coll^2 + eps^2 (continuous at r_coll),
+ * plus over its list cells -G M / R - G/2 R.Q.R / R^5 (R = x_i - centre,
+ * R^2 including eps^2; quadrupole term for order 2).
+ *  phi  [n] caller-owned device array for phi_i, or NULL.
+ *  W    host double for W = 1/2 sum m_i phi_i (fixed-order FP64 reduction,
+ *       bit-reproducible), or NULL; when given, the call synchronises.
+ * Particles must be in the order of the last list build.  The contact
+ * spring and dashpot have no potential here.  BH_E_STATE without lists. */
+int bh_compute_potential(bh_ctx* ctx, const bh_particles* p, double* phi, double* W);
 
 /* Load balance of the last persistent force launch made with timing on
  * (bh_set_timing): busy fraction = sum over warps of (finish - start) /

@@ -18,6 +18,7 @@ force error).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -57,6 +58,8 @@ def lib():
         _lib.orc_tree.restype = _i64
         _lib.orc_groups.restype = _i64
         _lib.orc_root_box.restype = _int
+        _lib.orc_pair_potential.restype = _dbl
+        _lib.orc_cell_potential.restype = _dbl
     return _lib
 
 
@@ -88,6 +91,7 @@ class Params:
     dt: float = 1e-3
     rebuild_every: int = 4
     key_frame: int = 0          # 0 Cartesian, 1 cylindrical (phi, r, z) tree (Sec. 4.3)
+    omega: float = 0.0          # rotation rate of the coordinate frame (Sec. 4.4); 0 = inertial
 
 
 # --------------------------------------------------------------------------
@@ -241,6 +245,45 @@ def central(x, y, z, G, Mc):
     return np.stack([ax, ay, az], axis=1)
 
 
+def pair_potential(prm: Params, xi, xj, mj) -> float:
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib().orc_pair_potential(_dbl(prm.G), _dbl(prm.eps), _dbl(prm.r_coll), _p(f(xi)), _p(f(xj)),
+                                          _dbl(mj)))
+
+
+def cell_potential(G, eps, order, xi, M, c, Q) -> float:
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib().orc_cell_potential(_dbl(G), _dbl(eps), _int(order), _p(f(xi)), _dbl(M), _p(f(c)), _p(f(Q))))
+
+
+def direct_potential(P: dict, prm: Params) -> np.ndarray:
+    """phi_i = sum over j != i of the pair potential (direct summation)."""
+    n = len(P["x"])
+    phi = np.empty(n)
+    lib().orc_direct_potential(_i64(n), _p(P["x"]), _p(P["y"]), _p(P["z"]), _p(P["m"]), _dbl(prm.G),
+                               _dbl(prm.eps), _dbl(prm.r_coll), _p(phi))
+    return phi
+
+
+def tree_potential(S: "State", prm: Params) -> np.ndarray:
+    """Per-particle self-gravity potential over the lists of S (the same
+    leaves, cells and order as tree_forces)."""
+    n = len(S.P["x"])
+    phi = np.full(n, np.nan)
+    t, L, mo, P = S.tree, S.lists, S.mom, S.P
+    lib().orc_tree_potential(_i64(0), _i64(len(S.groups)), _p(S.groups), _p(t["begin"]), _p(t["end"]),
+                             _p(L["pp_off"]), _p(L["P"] if len(L["P"]) else np.zeros(1, np.int32)), _p(L["pc_off"]),
+                             _p(L["C"] if len(L["C"]) else np.zeros(1, np.int32)), _p(mo["M"]), _p(mo["cx"]),
+                             _p(mo["cy"]), _p(mo["cz"]), _p(mo["Q"]), _int(prm.order), _p(P["x"]), _p(P["y"]),
+                             _p(P["z"]), _p(P["m"]), _dbl(prm.G), _dbl(prm.eps), _dbl(prm.r_coll), _p(phi))
+    return phi
+
+
+def self_energy(m, phi) -> float:
+    """Self-gravity potential energy W = 1/2 sum m_i phi_i."""
+    return float(0.5 * np.sum(m * phi))
+
+
 def tree_forces(S: "State", prm: Params, k0: int = 0, k1: int | None = None, out=None):
     """Tree acceleration (tree part only, no central mass) for groups [k0, k1).
     Entries of particles outside those groups are left as in ``out`` (NaN)."""
@@ -329,11 +372,32 @@ def accel(S: State, prm: Params) -> np.ndarray:
     return a
 
 
+def rotate_frame(Q: dict, omega_dt: float) -> None:
+    """The coordinate frame turns by omega dt about the z axis (Sec. 4.4):
+    positions and velocities, expressed in the frame, rotate by -omega dt."""
+    c, s = math.cos(omega_dt), math.sin(omega_dt)
+    x, y, vx, vy = Q["x"], Q["y"], Q["vx"], Q["vy"]
+    Q["x"], Q["y"] = c * x + s * y, c * y - s * x
+    Q["vx"], Q["vy"] = c * vx + s * vy, c * vy - s * vx
+
+
+def to_inertial(Q: dict, angle: float) -> dict:
+    """Arrays of a frame that has turned by angle, expressed in the inertial
+    axes (the rotation undone)."""
+    c, s = math.cos(angle), math.sin(angle)
+    out = dict(Q)
+    out["x"], out["y"] = c * Q["x"] - s * Q["y"], s * Q["x"] + c * Q["y"]
+    out["vx"], out["vy"] = c * Q["vx"] - s * Q["vy"], s * Q["vx"] + c * Q["vy"]
+    return out
+
+
 def step(P: dict, prm: Params, nsteps: int):
     """Kick-drift-kick leapfrog with the persistent-list schedule of Sec. 4.2.
     Force evaluation k (k = 0 initial) rebuilds iff k % rebuild_every == 0,
     otherwise refreshes moments only.  The contact term at evaluation k+1 sees
-    the half-step velocity.  Returns (final State, acceleration, #evaluations)."""
+    the half-step velocity.  With prm.omega != 0 the arrays live in a frame
+    turning at omega (Sec. 4.4): after every drift the frame turns by
+    omega dt.  Returns (final State, acceleration, #evaluations)."""
     dt = prm.dt
     S = rebuild({f: np.array(P[f]) for f in FIELDS}, prm)
     a = accel(S, prm)
@@ -344,6 +408,8 @@ def step(P: dict, prm: Params, nsteps: int):
             Q["v" + c] = Q["v" + c] + (0.5 * dt) * a[:, "xyz".index(c)]
         for c in "xyz":
             Q[c] = Q[c] + dt * Q["v" + c]
+        if prm.omega != 0.0:
+            rotate_frame(Q, prm.omega * dt)
         if k % prm.rebuild_every == 0:
             S = rebuild(Q, prm)
         else:

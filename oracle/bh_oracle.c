@@ -711,3 +711,105 @@ void orc_central(int64_t n, const double* x, const double* y, const double* z, d
         az[i] = f * z[i];
     }
 }
+
+/* ---- Self-gravity potential (the energy diagnostic of a ring simulation,
+ * Sec. 5.1 times steps with their diagnostics) ------------------------------
+ * The potential of the gravity Eq. (1) applies (the contact spring and
+ * dashpot are not gravity and have none here):
+ *   r > r_coll:   phi_ij = -G m_j / sqrt(r^2 + eps^2)
+ *   r <= r_coll:  gravity is held at its r_coll value, a = G m_j r / s^3 with
+ *                 s^2 = r_coll^2 + eps^2, whose potential (continuous at r_coll)
+ *                 is phi_ij = -G m_j / s - G m_j (r_coll^2 - r^2) / (2 s^3);
+ *   coincident (r = 0) pairs contribute nothing, like their force.
+ * A list cell (R = x_i - c, R2 = R.R + eps^2) contributes
+ *   phi = -G M / sqrt(R2) - G/2 R.Q.R / R2^(5/2)
+ * whose negative gradient is the cell term of orc_cell. */
+static double orc_pair_pot(double G, double eps2, double r_coll, double xi, double yi, double zi, double xj,
+                           double yj, double zj, double mj)
+{
+    double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return 0.0;
+    double rc2 = r_coll * r_coll;
+    if (r2 > rc2) {
+        double s2 = r2 + eps2;
+        return -G * mj / sqrt(s2);
+    }
+    double s2 = rc2 + eps2;
+    double s = sqrt(s2);
+    return -G * mj / s - G * mj * (rc2 - r2) / (2.0 * s2 * s);
+}
+
+static double orc_cell_pot(double G, double eps2, int order, double xi, double yi, double zi, double M, double cx,
+                           double cy, double cz, const double* Q)
+{
+    double Rx = xi - cx, Ry = yi - cy, Rz = zi - cz;
+    double R2 = Rx * Rx + Ry * Ry + Rz * Rz + eps2;
+    double R = sqrt(R2);
+    double phi = -G * M / R;
+    if (order >= 2) {
+        double QRx = Q[0] * Rx + Q[3] * Ry + Q[4] * Rz;
+        double QRy = Q[3] * Rx + Q[1] * Ry + Q[5] * Rz;
+        double QRz = Q[4] * Rx + Q[5] * Ry + Q[2] * Rz;
+        double RQR = Rx * QRx + Ry * QRy + Rz * QRz;
+        phi -= 0.5 * G * RQR / (R2 * R2 * R);
+    }
+    return phi;
+}
+
+/* Single pair and single cell, exported for closed-form tests. */
+double orc_pair_potential(double G, double eps, double r_coll, const double* xi, const double* xj, double mj)
+{
+    return orc_pair_pot(G, eps * eps, r_coll, xi[0], xi[1], xi[2], xj[0], xj[1], xj[2], mj);
+}
+
+double orc_cell_potential(double G, double eps, int order, const double* xi, double M, const double* c,
+                          const double* Q)
+{
+    return orc_cell_pot(G, eps * eps, order, xi[0], xi[1], xi[2], M, c[0], c[1], c[2], Q);
+}
+
+/* Direct summation: phi_i = sum over j != i, ascending j, of phi_ij. */
+void orc_direct_potential(int64_t n, const double* x, const double* y, const double* z, const double* m, double G,
+                          double eps, double r_coll, double* phi)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            s += orc_pair_pot(G, eps * eps, r_coll, x[i], y[i], z[i], x[j], y[j], z[j], m[j]);
+        }
+        phi[i] = s;
+    }
+}
+
+/* Tree potential over the same lists and in the same order as
+ * orc_tree_forces: the particles of the P leaves (j != i), then the cells. */
+void orc_tree_potential(int64_t k0, int64_t k1, const int32_t* groups, const uint32_t* begin, const uint32_t* end,
+                        const int64_t* pp_off, const int32_t* P, const int64_t* pc_off, const int32_t* C,
+                        const double* M, const double* cx, const double* cy, const double* cz, const double* Q,
+                        int order, const double* x, const double* y, const double* z, const double* m, double G,
+                        double eps, double r_coll, double* phi)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = k0; k < k1; ++k) {
+        int32_t g = groups[k];
+        for (uint32_t i = begin[g]; i < end[g]; ++i) {
+            double s = 0.0;
+            for (int64_t e = pp_off[k]; e < pp_off[k + 1]; ++e) {
+                int32_t leaf = P[e];
+                for (uint32_t j = begin[leaf]; j < end[leaf]; ++j) {
+                    if (j == i) continue;
+                    s += orc_pair_pot(G, eps * eps, r_coll, x[i], y[i], z[i], x[j], y[j], z[j], m[j]);
+                }
+            }
+            for (int64_t e = pc_off[k]; e < pc_off[k + 1]; ++e) {
+                int32_t c = C[e];
+                s += orc_cell_pot(G, eps * eps, order, x[i], y[i], z[i], M[c], cx[c], cy[c], cz[c],
+                                  Q + 6 * (int64_t)c);
+            }
+            phi[i] = s;
+        }
+    }
+}

@@ -23,10 +23,11 @@ SYMBOLS = ("bh_create", "bh_batch_create", "bh_destroy", "bh_last_error", "bh_se
            "bh_get_root", "bh_get_tree", "bh_get_moments", "bh_get_groups", "bh_get_lists",
            "bh_get_counters", "bh_set_timing", "bh_get_timing", "bh_set_tuning", "bh_get_tuning", "bh_autotune",
            "bh_get_balance", "bh_get_diagnostics", "bh_sort_keys_static", "bh_split_f32",
-           "bh_set_list_capacity", "bh_measure_peak")
+           "bh_set_list_capacity", "bh_measure_peak", "bh_compute_potential")
 BH_SCHED_GRID, BH_SCHED_STATIC, BH_SCHED_DYNAMIC = 0, 1, 2
 BH_SORT_STATIC_MAX_N = 4194304
-STAGES = ("keys", "sort", "permute", "tree", "moments", "groups", "lists", "split", "force", "contacts", "update")
+STAGES = ("keys", "sort", "permute", "tree", "moments", "groups", "lists", "split", "force", "contacts", "update",
+          "refine")
 BH_N_STAGES = len(STAGES)
 BH_PEAK_FP32, BH_PEAK_FP64 = 0, 1
 
@@ -37,7 +38,7 @@ class bh_params(ctypes.Structure):
                 ("eta", ctypes.c_double), ("dt", ctypes.c_double), ("n_g", ctypes.c_int),
                 ("n_leaf", ctypes.c_int), ("order", ctypes.c_int), ("precision", ctypes.c_int),
                 ("rebuild_every", ctypes.c_int), ("key_frame", ctypes.c_int),
-                ("list_capacity", ctypes.c_int64)]
+                ("list_capacity", ctypes.c_int64), ("omega", ctypes.c_double)]
 
 
 class bh_particles(ctypes.Structure):
@@ -48,7 +49,7 @@ class bh_particles(ctypes.Structure):
 class bh_counters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
                                                "n_contacts", "n_pp_far", "n_one_walk_builds",
-                                               "n_h2d_bytes", "n_d2h_bytes")] + [
+                                               "n_h2d_bytes", "n_d2h_bytes", "n_refined")] + [
         ("stage_ms", ctypes.c_double * BH_N_STAGES), ("stage_calls", ctypes.c_int64 * BH_N_STAGES)]
 
 
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH):
     lib.bh_split_f32.argtypes = [P, P, P, ctypes.c_int64, P]
     lib.bh_set_list_capacity.argtypes = [P, ctypes.c_int64]
     lib.bh_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.bh_compute_potential.argtypes = [P, ctypes.POINTER(bh_particles), P, ctypes.POINTER(ctypes.c_double)]
     _lib = lib
     return lib
 
@@ -125,7 +127,8 @@ def _np(a):
 def make_params(**kw) -> bh_params:
     p = bh_params()
     defaults = dict(theta=0.5, eps=0.0, G=1.0, M_central=0.0, r_coll=0.0, kappa=0.0, eta=0.0, dt=1e-3, n_g=64,
-                    n_leaf=8, order=1, precision=BH_PREC_FP64, rebuild_every=4, key_frame=0, list_capacity=0)
+                    n_leaf=8, order=1, precision=BH_PREC_FP64, rebuild_every=4, key_frame=0, list_capacity=0,
+                    omega=0.0)
     for k, v in {**defaults, **{k: v for k, v in kw.items() if k in defaults}}.items():
         setattr(p, k, v)
     return p
@@ -405,6 +408,20 @@ class Context:
         return {"mass": d.mass, "momentum": np.array(d.momentum[:]), "angular_momentum": np.array(d.angular_momentum[:]),
                 "kinetic": d.kinetic, "potential_central": d.potential_central,
                 "contact_candidates": d.contact_candidates, "contacts": d.contacts}
+
+    def bh_compute_potential(self, P: "Particles", phi=None):
+        """Self-gravity potential energy W (and phi_i into the float64 device
+        tensor phi of n elements when given)."""
+        import torch
+        ptr = None
+        if phi is not None:
+            if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float64
+                    and phi.is_contiguous() and phi.numel() == P.n):
+                raise ValueError("phi must be a contiguous float64 CUDA tensor of n elements")
+            ptr = phi.data_ptr()
+        W = ctypes.c_double()
+        self._chk(self.lib.bh_compute_potential(self.h, ctypes.byref(P.struct), ptr, ctypes.byref(W)))
+        return W.value
 
     def bh_get_balance(self):
         b = ctypes.c_double()

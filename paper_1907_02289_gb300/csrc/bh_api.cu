@@ -162,6 +162,7 @@ int check_params(Ctx* c, const bh_params* p) {
     if (!(p->eps >= 0.0) || !(p->r_coll >= 0.0) || !(p->dt >= 0.0))
         return fail(c, BH_E_INVAL, "eps, r_coll and dt must be >= 0");
     if (p->list_capacity < 0) return fail(c, BH_E_INVAL, "list_capacity must be >= 0");
+    if (!std::isfinite(p->omega)) return fail(c, BH_E_INVAL, "omega must be finite");
     return BH_OK;
 }
 
@@ -616,7 +617,7 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_box);
     cudaFree(c->d_small);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag);
+    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag); release(c->pot);
     for (int b = 0; b < 2; ++b) {
         release(c->ord_key[b]);
         release(c->ord_idx[b]);
@@ -630,7 +631,7 @@ int bh_destroy(bh_ctx* ctx) {
     release(c->level); release(c->nchild); release(c->begin); release(c->end); release(c->parent);
     release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->skip); release(c->split_cnt);
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
-    release(c->cz); release(c->Q); release(c->cell32); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
+    release(c->cz); release(c->Q); release(c->cell32); release(c->cell32lo); release(c->refine); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
     release(c->cnt_c); release(c->cnt_j); release(c->cnt_jm); release(c->stash_p); release(c->stash_c); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
     release(c->hbuf); release(c->hid);
@@ -751,6 +752,16 @@ int bh_get_diagnostics(bh_ctx* ctx, const bh_particles* p, bh_diagnostics* out) 
         out->contacts = (int64_t)(h[2] / 2);
     }
     return bh::read_status(c);
+}
+
+int bh_compute_potential(bh_ctx* ctx, const bh_particles* p, double* phi, double* W) {
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BH_E_INVAL;
+    if (!c->have_lists) return bh::fail(c, BH_E_STATE, "bh_compute_potential needs lists (call bh_make_lists)");
+    BH_TRY(bh::check_particles(c, p, false));
+    if (p->n != c->n) return bh::fail(c, BH_E_INVAL, "particle count changed since the tree was built");
+    BH_TRY(bh::stage_potential(c, p, phi, W));
+    return W ? bh::read_status(c) : BH_OK;
 }
 
 int bh_get_balance(bh_ctx* ctx, double* busy_fraction) {
@@ -977,6 +988,13 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_one_walk_builds = c->n_one_walk_builds;
     out->n_h2d_bytes = c->h2d_bytes;
     out->n_d2h_bytes = c->d2h_bytes;
+    out->n_refined = 0;
+    if (c->prm.precision == BH_PREC_FP32 && c->refine.p) {
+        unsigned long long nr = 0;
+        BH_CUDA(c, cudaMemcpyAsync(&nr, c->d_small + 20, sizeof(nr), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        out->n_refined = (int64_t)nr;
+    }
     BH_TRY(bh::read_stage_events(c));
     for (int s = 0; s < BH_N_STAGES; ++s) {
         out->stage_ms[s] = c->stage_ms[s];

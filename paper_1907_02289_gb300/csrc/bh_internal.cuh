@@ -137,9 +137,12 @@ struct Ctx {
     // moments
     DBuf<double> M, cx, cy, cz, Q;   // Q: 6 per node
     DBuf<float4> cell32;             // 3 per node: (c_hi, M), (c_lo, Qxx), (Qxy, Qxz, Qyy, Qyz)
+    DBuf<float> cell32lo;            // per node: exact mass - M of the record (FP32)
     DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
+    DBuf<uint2> refine;                 // (particle, list slot) queued for the refinement pass
     DBuf<unsigned long long> contacts;  // (i, j) contact candidates for the FP64 pass
     DBuf<double> diag;                   // diagnostic partial sums
+    DBuf<double> pot;                    // per-particle potential when the caller passes none
     DBuf<unsigned long long> contact_acc;  // per particle fixed-point contact sums (3 per particle)
     int64_t n_contacts = 0;
     bool contact_stats = false;         // the device contact counters hold an FP32 evaluation's counts
@@ -246,6 +249,7 @@ cudaError_t sort_pairs_with(cudaStream_t s, uint64_t* keys, uint32_t* idx, uint6
 int stage_octree(Ctx* c);                          // level-by-level split; sets n_nodes
 int stage_boxes(Ctx* c);                           // integer boxes + walk records
 int stage_moments(Ctx* c, const bh_particles* p);  // M, c, Q (+ FP32 cell records)
+int stage_moments64(Ctx* c, const bh_particles* p);  // FP64 M, c, Q whatever the precision
 int stage_groups(Ctx* c);                          // groups ordered by begin
 
 // walk.cu
@@ -255,6 +259,7 @@ int stage_lists(Ctx* c);                           // walk (count, fill) + parti
 int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of particles
 int build_order32(Ctx* c);                         // FP32 kernel's group order (per list build)
 int stage_force(Ctx* c, bh_particles* p, bool add_central);
+int stage_potential(Ctx* c, const bh_particles* p, double* phi, double* W);  // self-gravity potential (FP64)
 
 // bh_api.cu: force-kernel and stage timing (no-ops unless enabled, or while
 // capturing a graph); stage_end closes the innermost stage begun

@@ -29,6 +29,16 @@
 // folded after every tile into a compensated (TwoSum) hi/lo accumulator in
 // shared memory.
 //
+// Conditioning and refinement: the fold also sums the squares of the tile
+// partial sums.  The FP32 error of a_i (rounding of each term and of the
+// partial sums, both random in sign) grows with the root of that sum, not
+// with |a_i|, so where the pulls on a particle nearly cancel its relative
+// error grows without bound.  A particle with |a_i| below 0.12 G times that
+// root (about 0.3% of a ring's particles, measured) is queued, and a second
+// kernel evaluates it again over the same lists in df arithmetic (pairs of
+// FP32 numbers, dfloat.cuh), from the hi/lo coordinates and masses, and
+// replaces a_i.
+//
 // Mapping: one warp per group.  A group of n_i = 32 R + t particles gives
 // every lane R i-slots; the t remaining particles go to a "tail" slot shared
 // by J = 32 / T lanes (T = t rounded up to a power of two) that split the
@@ -52,6 +62,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "force_common.cuh"
 
 namespace bh {
@@ -71,6 +82,12 @@ namespace {
 #endif
 #ifndef BH_F32_TILE
 #define BH_F32_TILE 1  // list particles per tile = 64 x this, list cells = 32 x this
+#endif
+#ifndef BH_REFINE_K
+// refinement threshold: |a_i| < K G sqrt(sum of squared tile partial sums);
+// measured on the 2^24 and 2^26 rings and the 64 patches, it sends about 0.3%
+// of the particles to the refinement and leaves the others below 6e-6
+#define BH_REFINE_K 0.12
 #endif
 constexpr int kTileJ = 64 * BH_F32_TILE;  // list particles per tile (2 per lane per 64)
 constexpr int kTileC = 32 * BH_F32_TILE;  // list cells per tile (1 per lane per 32)
@@ -113,6 +130,7 @@ struct Smem32 {
     uint32_t q_j[kQueueCap];
     float ahi[32 * kSlots][3];  // compensated sums (G-free), hi part
     float alo[32 * kSlots][3];  // low part
+    float abnd[32 * kSlots];    // sum over folds of squared tile partial sums (conditioning of the sum)
 };
 
 struct Args {
@@ -146,6 +164,11 @@ struct Args {
     int chunk;                     // largest i-chunk (32, 64 or 96 particles)
     unsigned long long* ticket;    // NULL: static
     unsigned long long* warp_time; // optional: per warp (start, end) %globaltimer
+    // refinement: particle i of list slot k is queued as (i, k) when
+    // |a_i| < kref * G * sqrt(sum over tiles of the squared tile partial sums)
+    uint2* refine;
+    unsigned long long* nrefine;
+    double kref;
 };
 
 __device__ __forceinline__ float rel(float hi, float lo, float ohi, float olo) {
@@ -326,9 +349,11 @@ __device__ __forceinline__ void pc_body(const CPair& Cp, const float2 (&nh)[3], 
 }
 
 __device__ __forceinline__ void fold(Smem32& S, int s, float2 (&g)[3]) {
+    float bnd = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float t = __fadd_rn(g[c].x, g[c].y);
+        bnd = __fmaf_rn(t, t, bnd);
         const float hi = S.ahi[s][c];
         const float s1 = __fadd_rn(hi, t);
         const float bp = __fsub_rn(s1, hi);
@@ -337,6 +362,7 @@ __device__ __forceinline__ void fold(Smem32& S, int s, float2 (&g)[3]) {
         S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
         g[c] = make_float2(0.f, 0.f);
     }
+    S.abnd[s] += bnd;
 }
 
 template <int R, bool TAIL>
@@ -564,6 +590,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
             K.g[r][c] = make_float2(0.f, 0.f);
             S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
         }
+        S.abnd[32 * r + lane] = 0.f;
     }
     int qn = 0;
     __syncwarp();
@@ -689,12 +716,22 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
         double a[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
+        float bnd = S.abnd[s];
         if (tail)
-            for (int o = T; o < 32; o <<= 1)
+            for (int o = T; o < 32; o <<= 1) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+                bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+            }
         if (K.vl[r] && (!tail || tj == 0)) {
             const uint32_t i = K.iv[r];
+            // an ill-conditioned sum (terms far larger than the total) goes to
+            // the refinement pass, which rewrites a_i
+            const double kg = A.kref * A.fp.G;
+            if (A.refine && a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < kg * kg * (double)bnd) {
+                const unsigned long long q = atomicAdd(A.nrefine, 1ull);
+                A.refine[q] = make_uint2(i, (uint32_t)k);
+            }
             if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
             A.ax[i] = a[0];
             A.ay[i] = a[1];
@@ -938,6 +975,128 @@ __global__ void k_contacts_apply(const uint2* __restrict__ pairs, const unsigned
     }
 }
 
+// ---- refinement of ill-conditioned particles ------------------------------
+// A particle whose FP32 sum is ill-conditioned (|a_i| small against the sum
+// of |tile partial sums|, e.g. where the pull of its neighbours nearly
+// cancels) is evaluated again, over the same group lists and in the same
+// terms (Eq. (1)'s gravity with the r_coll floor; monopole + quadrupole),
+// in df arithmetic (hi + lo pairs of FP32 numbers, about 44 bits; see
+// dfloat.cuh) from the hi/lo particle coordinates and masses and the cell
+// records with their mass corrections.  One warp per queued particle; the
+// lanes split the entries and the partial sums are reduced in df.  The
+// result replaces a_i (the FP64 contact pass adds its term afterwards).
+struct RefineConsts {
+    df rc2, eps2, rc2eps2;  // r_coll^2, eps^2, r_coll^2 + eps^2
+};
+
+__device__ __forceinline__ df df_of(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+
+__device__ __forceinline__ void ref_pp(const Args& A, const RefineConsts& K, float xh, float xl, float yh, float yl,
+                                       float zh, float zl, uint32_t j, df (&acc)[3]) {
+    const float4 h = A.phi[j], l = A.plo[j];
+    const df d[3] = {df_diff(h.x, l.x, xh, xl), df_diff(h.y, l.y, yh, yl), df_diff(h.z, l.z, zh, zl)};
+    const df r2 = df_dot3(d[0], d[1], d[2]);
+    if (r2.hi == 0.f) return;  // coincident pair: no term
+    const df s2 = df_gt(r2, K.rc2) ? df_add(r2, K.eps2) : K.rc2eps2;
+    const df y = df_rsqrt(s2);
+    const df f = df_mul(df_mul(fast_two_sum(h.w, l.w), y), df_mul(y, y));  // m / s^3
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = df_add(acc[c], df_mul(f, d[c]));
+}
+
+__device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, const float* __restrict__ mlo,
+                                       float xh, float xl, float yh, float yl, float zh, float zl, int32_t cc,
+                                       df (&acc)[3]) {
+    const float4 r0 = A.cell32[3 * (int64_t)cc], r1 = A.cell32[3 * (int64_t)cc + 1];
+    // R = x_i - c (the oracle's sign); a = -M R / R^3 + Q R / R^5 - 5/2 (R.Q.R) R / R^7 (G-free)
+    const df R[3] = {df_diff(xh, xl, r0.x, r1.x), df_diff(yh, yl, r0.y, r1.y), df_diff(zh, zl, r0.z, r1.z)};
+    const df R2 = df_add(df_dot3(R[0], R[1], R[2]), K.eps2);
+    const df y = df_rsqrt(R2);
+    const df y2 = df_mul(y, y);
+    const df y3 = df_mul(y2, y);
+    const df M = fast_two_sum(r0.w, mlo[cc]);
+    const df mono = df_neg(df_mul(M, y3));
+    df t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = df_mul(mono, R[c]);
+    if (A.fp.order >= 2) {
+        const float4 r2v = A.cell32[3 * (int64_t)cc + 2];
+        const float qxx = r1.w, qxy = r2v.x, qxz = r2v.y, qyy = r2v.z, qyz = r2v.w;
+        const df qzz = df_neg(two_sum(qxx, qyy));
+        const df q[3] = {df_add(df_add(df_mul_f(R[0], qxx), df_mul_f(R[1], qxy)), df_mul_f(R[2], qxz)),
+                         df_add(df_add(df_mul_f(R[0], qxy), df_mul_f(R[1], qyy)), df_mul_f(R[2], qyz)),
+                         df_add(df_add(df_mul_f(R[0], qxz), df_mul_f(R[1], qyz)), df_mul(R[2], qzz))};
+        const df rqr = df_add(df_add(df_mul(R[0], q[0]), df_mul(R[1], q[1])), df_mul(R[2], q[2]));
+        const df y5 = df_mul(y3, y2);
+        const df w = df_mul_f(df_mul(rqr, df_mul(y5, y2)), -2.5f);  // -5/2 (R.Q.R) / R^7
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t[c] = df_add(t[c], df_add(df_mul(y5, q[c]), df_mul(w, R[c])));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = df_add(acc[c], t[c]);
+}
+
+__global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineConsts K, const float* __restrict__ mlo,
+                                                  int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t cnt = (int64_t)*A.nrefine;
+    if (cnt > cap) cnt = cap;  // cannot happen: one entry per particle at most
+    for (int64_t q = wid; q < cnt; q += nw) {
+        const uint2 e = A.refine[q];
+        const uint32_t i = e.x;
+        const int64_t k = e.y;
+        if (i >= A.n || k >= A.ng) {
+            if (lane == 0) atomicOr(A.status, kStatBounds);
+            continue;
+        }
+        const int32_t g = A.groups[k];
+        const uint32_t b = A.begin[g], en = A.end[g];
+        const float4 hi = A.phi[i], lo = A.plo[i];
+        df acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (uint32_t j = b + lane; j < en; j += 32)
+            if (j != i) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, j, acc);
+        const int64_t j1 = A.jj_off[k + 1];
+        for (int64_t p = A.jj_off[k] + lane; p < j1; p += 32) {
+            const uint32_t j = A.JJ[p];
+            if (j >= A.n) {
+                atomicOr(A.status, kStatBounds);
+                continue;
+            }
+            ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, j, acc);
+        }
+        const int64_t c1 = A.pc_off[k + 1];
+        for (int64_t p = A.pc_off[k] + lane; p < c1; p += 32) {
+            const int32_t cc = A.C[p];
+            if (cc < 0 || cc >= A.nn) {
+                atomicOr(A.status, kStatBounds);
+                continue;
+            }
+            ref_pc(A, K, mlo, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, cc, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const df v = {__shfl_xor_sync(0xffffffffu, acc[c].hi, o), __shfl_xor_sync(0xffffffffu, acc[c].lo, o)};
+                acc[c] = df_add(acc[c], v);
+            }
+        if (lane == 0) {
+            double a[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[c] = A.fp.G * df_to_double(acc[c]);
+            if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
+            A.ax[i] = a[0];
+            A.ay[i] = a[1];
+            A.az[i] = a[2];
+        }
+    }
+}
+
 using Force32Fn = void (*)(const Args);
 
 Force32Fn force32_kernel(int order, int mode) {
@@ -1012,6 +1171,25 @@ int build_order32(Ctx* c) {
 }
 
 namespace {
+RefineConsts refine_consts(const ForceParams& fp) {
+    auto split = [](double v) {
+        const float h = (float)v;
+        return df{h, (float)(v - (double)h)};
+    };
+    return RefineConsts{split(fp.rc2), split(fp.eps2), split(fp.rc2 + fp.eps2)};
+}
+
+// The refinement pass over the particles the force kernel queued (count
+// read on the device, so it can run inside a captured graph).
+int refine_pass(Ctx* c, const Args& A, const ForceParams& fp) {
+    if (!A.refine) return BH_OK;
+    BH_TRY(stage_begin(c, BH_STAGE_REFINE));
+    k_refine32<<<(unsigned)(c->num_sms * 4), 256, 0, c->stream>>>(A, refine_consts(fp), c->cell32lo.p,
+                                                                   (int64_t)c->refine.cap);
+    BH_LAUNCH(c);
+    return stage_end(c);
+}
+
 int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, unsigned nb) {
     BH_TRY(stage_begin(c, BH_STAGE_CONTACTS));
     unsigned long long* acc = c->contact_acc.p;
@@ -1054,6 +1232,8 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     if (contact) BH_TRY(grow(c, c->contact_acc, 3 * (size_t)c->n, "contact sums"));
     A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
     A.contact_cap = (int64_t)c->contacts.cap;
+    if (c->capturing && c->tune.graph_contact_room > 0)  // the room a graph step may use
+        A.contact_cap = std::min(A.contact_cap, (int64_t)c->tune.graph_contact_room);
     A.ncontact = c->d_small + 16;
     c->contact_stats = contact;
     BH_CUDA(c, cudaMemsetAsync(A.ncontact, 0, sizeof(unsigned long long), c->stream));
@@ -1080,6 +1260,13 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.chunk = std::min(c->tune.chunk, 32 * BH_F32_MAXR);
     A.ticket = nullptr;
     A.warp_time = nullptr;
+    A.kref = BH_REFINE_K;
+    A.nrefine = c->d_small + 20;
+    A.refine = nullptr;
+    if (A.kref > 0.0) {
+        BH_TRY(grow(c, c->refine, (size_t)c->n, "refinement queue"));
+        A.refine = c->refine.p;
+    }
     unsigned nb;
     if (c->tune.sched == BH_SCHED_GRID) {
         nb = blocks_for(A.ng, W);
@@ -1099,12 +1286,14 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     }
     c->f32_blocks = nb;
     for (int attempt = 0; attempt < 2; ++attempt) {
+        BH_CUDA(c, cudaMemsetAsync(A.nrefine, 0, sizeof(unsigned long long), c->stream));
         BH_TRY(timing_begin(c));
         BH_TRY(stage_begin(c, BH_STAGE_FORCE));
         kern<<<nb, 32 * W, smem, c->stream>>>(A);
         BH_LAUNCH(c);
         BH_TRY(stage_end(c));
         BH_TRY(timing_end(c));
+        BH_TRY(refine_pass(c, A, fp));
         if (!contact) break;
         if (c->capturing) {
             // inside a captured graph: no read-back; the pass takes the count

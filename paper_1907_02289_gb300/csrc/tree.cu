@@ -11,6 +11,7 @@
 // internal nodes: children in octant order) with _rn intrinsics, so they do
 // not depend on thread scheduling or on multiply-add contraction.
 #include "bh_internal.cuh"
+#include "dfloat.cuh"
 
 namespace bh {
 namespace {
@@ -266,13 +267,16 @@ template <int ORDER>
 __global__ void k_moments32(int64_t ls, int64_t cnt, const uint32_t* __restrict__ begin,
                             const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
                             const uint8_t* __restrict__ nchild, const float4* __restrict__ phi,
-                            const float4* __restrict__ plo, float4* cell32) {
+                            const float4* __restrict__ plo, float4* cell32, float* __restrict__ mlo) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     const int64_t k = ls + t;
     const int nc = nchild[k];
     float rh[3], rl[3];  // reference point (hi/lo)
     float Mk = 0.f, s[3] = {0.f, 0.f, 0.f}, q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // the mass also as a compensated sum of the (hi + lo) masses: the record
+    // keeps Mk, mlo[k] the difference (for the refinement of the FP32 kernel)
+    df Md = {0.f, 0.f};
     if (nc == 0) {
         const uint32_t b = begin[k], e = end[k];
         const float4 h0 = phi[b], l0 = plo[b];
@@ -282,6 +286,7 @@ __global__ void k_moments32(int64_t ls, int64_t cnt, const uint32_t* __restrict_
             const float4 h = phi[i], l = plo[i];
             const float d[3] = {dsub(h.x, l.x, rh[0], rl[0]), dsub(h.y, l.y, rh[1], rl[1]), dsub(h.z, l.z, rh[2], rl[2])};
             Mk += h.w;
+            Md = df_add(Md, {h.w, l.w});
 #pragma unroll
             for (int a = 0; a < 3; ++a) s[a] = fmaf(h.w, d[a], s[a]);
         }
@@ -312,6 +317,7 @@ __global__ void k_moments32(int64_t ls, int64_t cnt, const uint32_t* __restrict_
             const float4 h = cell32[3 * (f + cc)], l = cell32[3 * (f + cc) + 1];
             const float d[3] = {dsub(h.x, l.x, rh[0], rl[0]), dsub(h.y, l.y, rh[1], rl[1]), dsub(h.z, l.z, rh[2], rl[2])};
             Mk += h.w;
+            Md = df_add(Md, {h.w, mlo[f + cc]});
 #pragma unroll
             for (int a = 0; a < 3; ++a) s[a] = fmaf(h.w, d[a], s[a]);
         }
@@ -343,6 +349,7 @@ __global__ void k_moments32(int64_t ls, int64_t cnt, const uint32_t* __restrict_
         ch[a] = hi;
         cl[a] = __fsub_rn(lo, __fsub_rn(hi, rh[a]));
     }
+    mlo[k] = __fadd_rn(__fsub_rn(Md.hi, Mk), Md.lo);
     cell32[3 * k + 0] = make_float4(ch[0], ch[1], ch[2], Mk);
     cell32[3 * k + 1] = make_float4(cl[0], cl[1], cl[2], q[0]);
     cell32[3 * k + 2] = make_float4(q[3], q[4], q[1], q[5]);
@@ -448,6 +455,7 @@ int stage_moments(Ctx* c, const bh_particles* p) {
         // FP32 path: hi/lo split of the particles, then FP32 moments with a
         // hi/lo centre (no FP64 arithmetic per node)
         BH_TRY(grow(c, c->cell32, (size_t)nn * 3, "FP32 cell records"));
+        BH_TRY(grow(c, c->cell32lo, (size_t)nn, "FP32 cell mass corrections"));
         BH_TRY(stage_begin(c, BH_STAGE_SPLIT));
         BH_TRY(stage_split(c, p));
         BH_TRY(stage_end(c));
@@ -457,15 +465,23 @@ int stage_moments(Ctx* c, const bh_particles* p) {
             if (c->prm.order >= 2)
                 k_moments32<2><<<blocks_for(cnt, 128), 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p,
                                                                             c->first_child.p, c->nchild.p,
-                                                                            c->phi.p, c->plo.p, c->cell32.p);
+                                                                            c->phi.p, c->plo.p, c->cell32.p, c->cell32lo.p);
             else
                 k_moments32<1><<<blocks_for(cnt, 128), 128, 0, c->stream>>>(ls, cnt, c->begin.p, c->end.p,
                                                                             c->first_child.p, c->nchild.p,
-                                                                            c->phi.p, c->plo.p, c->cell32.p);
+                                                                            c->phi.p, c->plo.p, c->cell32.p, c->cell32lo.p);
             BH_LAUNCH(c);
         }
         return stage_end(c);
     }
+    return stage_moments64(c, p);
+}
+
+// FP64 node moments (the FP64 path's records; the FP32 path's potential
+// diagnostic also uses them).
+int stage_moments64(Ctx* c, const bh_particles* p) {
+    const int64_t nn = c->n_nodes;
+    const int depth = (int)c->lvl_start.size() - 1;
     BH_TRY(grow(c, c->M, (size_t)nn, "moments M"));
     BH_TRY(grow(c, c->cx, (size_t)nn, "moments cx"));
     BH_TRY(grow(c, c->cy, (size_t)nn, "moments cy"));

@@ -1,6 +1,8 @@
 // update.cu -- Sec. 4.2 step 4 ("integrate the orbits"): the FP64
 // kick-drift-kick leapfrog.  The acceleration arrays already hold the tree
 // part plus the central mass (added by the force kernel's epilogue).
+#include <cmath>
+
 #include "bh_internal.cuh"
 
 namespace bh {
@@ -16,19 +18,32 @@ __global__ void k_kick(int64_t n, double h, const double* __restrict__ ax, const
     vz[i] += h * az[i];
 }
 
+// Kick and drift; with ROT the frame then turns by omega dt (Sec. 4.4): x, y
+// and vx, vy are rotated by -omega dt about z (c = cos, s = sin of omega dt),
+// each product rounded on its own, as the oracle's step does.
+template <bool ROT>
 __global__ void k_kick_drift(int64_t n, double h, double dt, const double* __restrict__ ax,
                              const double* __restrict__ ay, const double* __restrict__ az,
                              double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz,
-                             double* __restrict__ x, double* __restrict__ y, double* __restrict__ z) {
+                             double* __restrict__ x, double* __restrict__ y, double* __restrict__ z, double c,
+                             double s) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double ux = vx[i] + h * ax[i], uy = vy[i] + h * ay[i], uz = vz[i] + h * az[i];
-    vx[i] = ux;
-    vy[i] = uy;
-    vz[i] = uz;
-    x[i] += dt * ux;
-    y[i] += dt * uy;
+    const double X = x[i] + dt * ux, Y = y[i] + dt * uy;
     z[i] += dt * uz;
+    vz[i] = uz;
+    if (ROT) {
+        x[i] = __dadd_rn(__dmul_rn(c, X), __dmul_rn(s, Y));
+        y[i] = __dsub_rn(__dmul_rn(c, Y), __dmul_rn(s, X));
+        vx[i] = __dadd_rn(__dmul_rn(c, ux), __dmul_rn(s, uy));
+        vy[i] = __dsub_rn(__dmul_rn(c, uy), __dmul_rn(s, ux));
+    } else {
+        x[i] = X;
+        y[i] = Y;
+        vx[i] = ux;
+        vy[i] = uy;
+    }
 }
 
 // Diagnostics: 11 FP64 sums per particle set (mass, momentum, angular
@@ -103,8 +118,10 @@ int stage_kick(Ctx* c, bh_particles* p, double h) {
 
 int stage_kick_drift(Ctx* c, bh_particles* p, double h, double dt) {
     BH_TRY(stage_begin(c, BH_STAGE_UPDATE));
-    k_kick_drift<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, dt, p->ax, p->ay, p->az, p->vx, p->vy,
-                                                               p->vz, p->x, p->y, p->z);
+    const double om = c->prm.omega * dt;
+    auto kern = om != 0.0 ? k_kick_drift<true> : k_kick_drift<false>;
+    kern<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, dt, p->ax, p->ay, p->az, p->vx, p->vy, p->vz, p->x,
+                                                       p->y, p->z, std::cos(om), std::sin(om));
     BH_LAUNCH(c);
     return stage_end(c);
 }

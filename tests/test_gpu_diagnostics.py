@@ -45,21 +45,61 @@ def test_sums_match_definition_and_repeat_bitwise():
 
 
 def test_energy_and_angular_momentum_nearly_conserved_by_steps():
-    """Over 20 steps the central potential dominates; KDK keeps the total
-    within O(dt^2) and L_z (the central force exerts no torque; self-gravity
-    and contacts are internal) to rounding."""
+    """Over 20 steps the total energy (kinetic + central + self-gravity
+    potential) stays within O(dt^2) and L_z (the central force exerts no
+    torque; self-gravity and contacts are internal) to rounding."""
     from paper_1907_02289_gb300 import bh
     P = synth.ring(30000, 32)
     prm = _prm()
     ctx = bh.Context(**prm)
     D = bh.Particles(P)
     d0 = ctx.bh_get_diagnostics(D)
+    ctx.bh_build_tree(D)
+    ctx.bh_make_lists()
+    w0 = ctx.bh_compute_potential(D)
     ctx.bh_step(D, 20)
     d1 = ctx.bh_get_diagnostics(D)
-    e0 = d0["kinetic"] + d0["potential_central"]
-    e1 = d1["kinetic"] + d1["potential_central"]
+    ctx.bh_build_tree(D)
+    ctx.bh_make_lists()
+    w1 = ctx.bh_compute_potential(D)
+    assert w0 < 0.0 and w1 < 0.0
+    e0 = d0["kinetic"] + d0["potential_central"] + w0
+    e1 = d1["kinetic"] + d1["potential_central"] + w1
     assert abs(e1 - e0) <= 1e-6 * abs(e0)
     assert abs(d1["angular_momentum"][2] - d0["angular_momentum"][2]) <= 1e-9 * abs(d0["angular_momentum"][2])
+
+
+@pytest.mark.parametrize("precision,frame", [(0, 0), (1, 0), (1, 1)])
+def test_potential_matches_oracle(precision, frame):
+    """Per-particle self-gravity potential over the GPU's lists against the
+    oracle's tree potential on the same lists (FP64 either way: 1e-12), and
+    W = 1/2 sum m phi against the oracle's, repeated bit for bit."""
+    import torch
+    from paper_1907_02289_gb300 import bh
+    P = synth.ring(40000, 33, phi_max=0.05)
+    prm = _prm(precision=precision, key_frame=frame)
+    ctx = bh.Context(**prm)
+    D = bh.Particles(P)
+    ctx.bh_build_tree(D)
+    ctx.bh_make_lists()
+    phi = torch.empty(len(P["x"]), dtype=torch.float64, device="cuda")
+    W1 = ctx.bh_compute_potential(D, phi)
+    W2 = ctx.bh_compute_potential(D)
+    assert W1 == W2
+    ref = orc.rebuild(P, orc.Params(**{k: v for k, v in prm.items() if k in orc.Params.__dataclass_fields__}))
+    pref = orc.tree_potential(ref, orc.Params(**{k: v for k, v in prm.items() if k in orc.Params.__dataclass_fields__}))
+    got = phi.cpu().numpy()
+    assert np.max(np.abs(got - pref) / np.abs(pref)) <= 1e-12
+    assert np.isclose(W1, orc.self_energy(ref.P["m"], pref), rtol=1e-13, atol=0)
+
+
+def test_potential_needs_lists():
+    from paper_1907_02289_gb300 import bh
+    ctx = bh.Context(**_prm())
+    D = bh.Particles(synth.ring(1000, 34))
+    with pytest.raises(bh.BHError) as e:
+        ctx.bh_compute_potential(D)
+    assert e.value.code == bh.BH_E_STATE
 
 
 def test_contact_count_matches_brute_force():

@@ -497,6 +497,170 @@ def test_step_time_reversible_and_schedule():
     assert np.max(np.abs(x1 - x0)) < 1e-12
 
 
+# ---- self-gravity potential --------------------------------------------------
+def test_pair_potential_closed_forms_and_its_gradient_is_the_gravity():
+    """-G m / r outside r_coll (softened: -G m / sqrt(r^2 + eps^2)); inside,
+    the potential of the held gravity, continuous at r_coll; its negative
+    derivative equals the gravity of Eq. (1) on either side (central
+    differences), and coincident pairs contribute nothing."""
+    kappa, eta = synth.contact_params(1e-3)
+    for eps in (0.0, 1e-3):
+        prm = orc.Params(G=2.0, eps=eps, r_coll=2e-5, kappa=0.0, eta=0.0)
+        xi = np.zeros(3)
+        for r in (1e-5, 1.9e-5, 3e-5, 0.7):
+            xj = np.array([r, 0.0, 0.0])
+            phi = orc.pair_potential(prm, xi, xj, 3e-12)
+            if r > 2e-5:
+                assert math.isclose(phi, -2.0 * 3e-12 / math.sqrt(r * r + eps * eps), rel_tol=1e-15)
+            h = 1e-4 * r
+            dphi = (orc.pair_potential(prm, xi, xj + [h, 0, 0], 3e-12) -
+                    orc.pair_potential(prm, xi, xj - [h, 0, 0], 3e-12)) / (2 * h)
+            # a_i = -grad_{x_i} phi = +d phi / d x_j along the axis
+            a = orc.pair_accel(prm, xi, np.zeros(3), 1.0, xj, np.zeros(3), 3e-12)
+            assert math.isclose(a[0], dphi, rel_tol=1e-6)
+        rc = 2e-5
+        below = orc.pair_potential(prm, xi, np.array([rc * (1 - 1e-12), 0, 0]), 3e-12)
+        above = orc.pair_potential(prm, xi, np.array([rc * (1 + 1e-12), 0, 0]), 3e-12)
+        assert math.isclose(below, above, rel_tol=1e-10)
+        assert orc.pair_potential(prm, xi, xi, 3e-12) == 0.0
+    del kappa, eta
+
+
+def test_cell_potential_far_field_orders_and_gradient():
+    """A cell's potential against the direct sum over its particles: the
+    monopole error falls as (s/d)^2 (the dipole vanishes about the centre of
+    mass), the quadrupole's as (s/d)^3; its negative gradient is orc_cell."""
+    rng = np.random.default_rng(4)
+    xs = rng.uniform(-0.5, 0.5, (40, 3)); ms = rng.uniform(0.5, 1.5, 40)
+    M = ms.sum(); c = (ms[:, None] * xs).sum(0) / M
+    d = xs - c; d2 = (d * d).sum(1)
+    Q = np.array([(ms * (3 * d[:, 0] ** 2 - d2)).sum(), (ms * (3 * d[:, 1] ** 2 - d2)).sum(),
+                  (ms * (3 * d[:, 2] ** 2 - d2)).sum(), (3 * ms * d[:, 0] * d[:, 1]).sum(),
+                  (3 * ms * d[:, 0] * d[:, 2]).sum(), (3 * ms * d[:, 1] * d[:, 2]).sum()])
+    u = np.array([0.6, -0.3, 0.74]); u /= np.linalg.norm(u)
+    errs = {1: [], 2: []}
+    for D in (8.0, 16.0, 32.0, 64.0):
+        x = c + D * u
+        exact = -(ms / np.linalg.norm(x - xs, axis=1)).sum()
+        for order in (1, 2):
+            errs[order].append(abs(orc.cell_potential(1.0, 0.0, order, x, M, c, Q) - exact) / abs(exact))
+    for order, slope in ((1, 2.0), (2, 3.0)):
+        e = np.array(errs[order])
+        k = np.log2(e[:-1] / e[1:])
+        assert np.all(np.abs(k - slope) < 0.35), (order, k)
+    x = c + 5.0 * u
+    h = 1e-5
+    g = [(orc.cell_potential(1.0, 1e-2, 2, x + h * np.eye(3)[a], M, c, Q) -
+          orc.cell_potential(1.0, 1e-2, 2, x - h * np.eye(3)[a], M, c, Q)) / (2 * h) for a in range(3)]
+    acc = orc.cell_accel(1.0, 1e-2, 2, x, M, c, Q)
+    assert np.allclose(acc, -np.array(g), rtol=1e-7, atol=0)
+
+
+def test_tree_potential_theta_zero_equals_direct_bitwise():
+    P = synth.ring(3000, 2, r_in=0.999, r_out=1.001, phi_max=0.01)
+    prm = orc.Params(theta=0.0, n_g=32, n_leaf=4, order=2, r_coll=2e-5)
+    S = orc.rebuild(P, prm)
+    assert np.array_equal(orc.tree_potential(S, prm), orc.direct_potential(S.P, prm))
+
+
+def test_tree_potential_at_theta_half_close_to_direct_and_energy_symmetric():
+    """theta 0.5, quadrupole: per-particle potentials within 1e-4 of the
+    direct sum; W = 1/2 sum m phi equals the sum over unordered pairs."""
+    P = synth.uniform_cube(1500, 3)
+    prm = orc.Params(theta=0.5, n_g=32, n_leaf=8, order=2, eps=1e-3)
+    S = orc.rebuild(P, prm)
+    pt, pd = orc.tree_potential(S, prm), orc.direct_potential(S.P, prm)
+    assert np.max(np.abs(pt - pd) / np.abs(pd)) < 1e-4
+    x = np.stack([S.P["x"], S.P["y"], S.P["z"]], 1); m = S.P["m"]
+    W = 0.0
+    for i in range(len(m)):
+        r = np.sqrt(((x[i + 1:] - x[i]) ** 2).sum(1) + 1e-6)
+        W -= (m[i] * m[i + 1:] / r).sum()
+    assert math.isclose(orc.self_energy(m, pd), W, rel_tol=1e-12)
+
+
+def test_step_conserves_total_energy_without_contacts():
+    """A softened self-gravitating cube starting at rest (no central mass, no
+    contacts, theta 0 so the forces are the potential's exact gradient):
+    kick-drift-kick conserves kinetic + self-gravity energy to O(dt^2), so
+    the total moves by far less than the kinetic energy gained."""
+    P = synth.uniform_cube(300, 6)
+    prm = orc.Params(theta=0.0, n_g=16, n_leaf=4, order=2, eps=0.05, G=1.0, dt=1e-3, rebuild_every=4)
+
+    def parts(Q):
+        return orc.diagnostics(Q, 1.0, 0.0)["kinetic"], orc.self_energy(Q["m"], orc.direct_potential(Q, prm))
+
+    k0, w0 = parts(P)
+    S, _, _ = orc.step(P, prm, 200)
+    k1, w1 = parts(S.P)
+    assert k0 == 0.0 and k1 > 1e-2 * abs(w0)
+    assert abs((k1 + w1) - (k0 + w0)) < 1e-4 * k1
+
+
+# ---- rotating frame (Sec. 4.4) -----------------------------------------------
+def _one(x, y, vx, vy, m=1e-12):
+    return {"x": np.array([x]), "y": np.array([y]), "z": np.array([0.0]), "vx": np.array([vx]),
+            "vy": np.array([vy]), "vz": np.array([0.0]), "m": np.array([m]), "id": np.array([0], np.int64)}
+
+
+def test_rotating_frame_circular_orbit_stands_still():
+    """A particle on the circular orbit r = 1 about M_c = 1 in a frame turning
+    at its Kepler rate 1 stays at (1, 0) up to the integrator's O(dt^2)
+    phase error, while in the inertial frame it goes round."""
+    nst = 500
+    prm = orc.Params(G=1.0, M_central=1.0, dt=1e-2, rebuild_every=4, omega=1.0)
+    S, _, _ = orc.step(_one(1.0, 0.0, 0.0, 1.0), prm, nst)
+    drift = math.hypot(S.P["x"][0] - 1.0, S.P["y"][0])
+    assert drift < nst * prm.dt ** 3 and abs(math.hypot(S.P["x"][0], S.P["y"][0]) - 1.0) < 2 * prm.dt ** 2
+    Si, _, _ = orc.step(_one(1.0, 0.0, 0.0, 1.0), orc.Params(**{**prm.__dict__, "omega": 0.0}), nst)
+    assert math.hypot(Si.P["x"][0] - 1.0, Si.P["y"][0]) > 1.0
+
+
+def test_rotating_frame_jacobi_integral_of_a_test_particle():
+    """An eccentric test particle about M_c in the frame turning at Omega:
+    the Jacobi integral C = 1/2 |v - Omega x r|^2 - 1/2 Omega^2 (x^2 + y^2)
+    - G M_c / r (v the inertial velocity in the turning axes) is conserved to
+    O(dt^2); it moves far less than the particle's speed relative to the
+    frame does."""
+    prm = orc.Params(G=1.0, M_central=1.0, dt=1e-3, rebuild_every=4, omega=1.0)
+
+    def jacobi(Q):
+        x, y, vx, vy = Q["x"][0], Q["y"][0], Q["vx"][0], Q["vy"][0]
+        ux, uy = vx + prm.omega * y, vy - prm.omega * x  # velocity relative to the frame
+        return 0.5 * (ux * ux + uy * uy + Q["vz"][0] ** 2) - 0.5 * prm.omega ** 2 * (x * x + y * y) - \
+            1.0 / math.hypot(x, y)
+
+    P = _one(1.1, 0.0, 0.0, 0.85)
+    c0 = jacobi(P)
+    S, _, _ = orc.step(P, prm, 3000)
+    rel_speed = math.hypot(S.P["vx"][0] + S.P["y"][0], S.P["vy"][0] - S.P["x"][0])
+    assert abs(jacobi(S.P) - c0) < 1e-5 and rel_speed > 1e-2
+
+
+def test_rotating_frame_equals_inertial_run_mapped_back():
+    """theta = 0 (tree forces = direct sums): a ring patch stepped in the
+    turning frame, mapped back by the angle the frame turned, is the
+    inertial run to rounding (the forces are rotation-invariant)."""
+    P = synth.ring(800, 14, r_in=0.999, r_out=1.001, phi_max=0.01, mass=1e-9)
+    kappa, eta = synth.contact_params(1e-3)
+    prm = orc.Params(theta=0.0, n_g=16, n_leaf=4, order=2, G=1.0, M_central=1.0, dt=1e-3, rebuild_every=4,
+                     r_coll=2e-5, kappa=kappa, eta=eta, omega=1.0)
+    nst = 12
+    Sr, _, _ = orc.step(P, prm, nst)
+    Si, _, _ = orc.step(P, orc.Params(**{**prm.__dict__, "omega": 0.0}), nst)
+    back = orc.to_inertial(Sr.P, prm.omega * prm.dt * nst)
+    o_r, o_i = np.argsort(Sr.P["id"]), np.argsort(Si.P["id"])
+    for f in ("x", "y", "z"):
+        assert np.max(np.abs(back[f][o_r] - Si.P[f][o_i])) < 1e-13, f
+    for f in ("vx", "vy", "vz"):
+        assert np.max(np.abs(back[f][o_r] - Si.P[f][o_i])) < 1e-11, f
+    # in the turning frame the ring centre barely moves
+    x0 = np.stack([P["x"], P["y"]], 1)[np.argsort(P["id"])]
+    xr = np.stack([Sr.P["x"], Sr.P["y"]], 1)[o_r]
+    xi = np.stack([Si.P["x"], Si.P["y"]], 1)[o_i]
+    assert np.max(np.linalg.norm(xr - x0, axis=1)) < 0.05 * np.max(np.linalg.norm(xi - x0, axis=1))
+
+
 # ---- diagnostics ------------------------------------------------------------
 def test_diagnostics_circular_orbit_closed_form():
     """One particle of mass m on a circular orbit of radius R about M_c:
