@@ -95,11 +95,22 @@ int stage_end(Ctx* c) {
     return BH_OK;
 }
 
-// Read the recorded stage events into the sums (synchronises the stream).
-static int read_stage_events(Ctx* c) {
+// Read the recorded stage events into the sums: all of them after
+// synchronising the stream (wait), or, without waiting, those already
+// complete (in recording order).
+static int read_stage_events(Ctx* c, bool wait) {
     if (c->ev_stage.empty()) return BH_OK;
-    BH_CUDA(c, cudaStreamSynchronize(c->stream));
-    const size_t keep = c->stage_open.empty() ? c->ev_stage.size() : (size_t)c->stage_open.front();
+    if (wait) BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    size_t keep = c->stage_open.empty() ? c->ev_stage.size() : (size_t)c->stage_open.front();
+    if (!wait)
+        for (size_t k = 0; k < keep; ++k) {
+            const cudaError_t q = cudaEventQuery(c->ev_stage[k].b);
+            if (q == cudaErrorNotReady) {
+                keep = k;
+                break;
+            }
+            BH_CUDA(c, q);
+        }
     for (size_t k = 0; k < keep; ++k) {
         float ms = 0.f;
         BH_CUDA(c, cudaEventElapsedTime(&ms, c->ev_stage[k].a, c->ev_stage[k].b));
@@ -334,6 +345,7 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
     }
     BH_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
     c->n_launches += c->graph_launches;
+    c->refine_pending = c->prm.precision == BH_PREC_FP32;  // its count is read when asked for
     c->k_eval++;
     c->evals_since_build++;
     return BH_OK;
@@ -988,14 +1000,15 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
     out->n_one_walk_builds = c->n_one_walk_builds;
     out->n_h2d_bytes = c->h2d_bytes;
     out->n_d2h_bytes = c->d2h_bytes;
-    out->n_refined = 0;
-    if (c->prm.precision == BH_PREC_FP32 && c->refine.p) {
+    if (c->refine_pending) {  // an evaluation without a read-back since: read its count now
         unsigned long long nr = 0;
         BH_CUDA(c, cudaMemcpyAsync(&nr, c->d_small + 20, sizeof(nr), cudaMemcpyDeviceToHost, c->stream));
         BH_CUDA(c, cudaStreamSynchronize(c->stream));
-        out->n_refined = (int64_t)nr;
+        c->n_refined = (int64_t)nr;
+        c->refine_pending = false;
     }
-    BH_TRY(bh::read_stage_events(c));
+    out->n_refined = c->n_refined;
+    BH_TRY(bh::read_stage_events(c, false));
     for (int s = 0; s < BH_N_STAGES; ++s) {
         out->stage_ms[s] = c->stage_ms[s];
         out->stage_calls[s] = c->stage_calls[s];
@@ -1036,7 +1049,7 @@ int bh_get_timing(bh_ctx* ctx, double* force_ms, int64_t* force_launches, int re
             c->ev_pool.push_back(pr.second);
         }
         c->ev_force.clear();
-        BH_TRY(bh::read_stage_events(c));
+        BH_TRY(bh::read_stage_events(c, true));
         for (int s = 0; s < BH_N_STAGES; ++s) {
             c->stage_ms[s] = 0.0;
             c->stage_calls[s] = 0;

@@ -145,6 +145,8 @@ struct Ctx {
     DBuf<double> pot;                    // per-particle potential when the caller passes none
     DBuf<unsigned long long> contact_acc;  // per particle fixed-point contact sums (3 per particle)
     int64_t n_contacts = 0;
+    int64_t n_refined = 0;              // particles the refinement pass re-evaluated (last read)
+    bool refine_pending = false;        // an evaluation ran since n_refined was read
     bool contact_stats = false;         // the device contact counters hold an FP32 evaluation's counts
 
     // groups

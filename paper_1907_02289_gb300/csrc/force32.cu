@@ -1285,6 +1285,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         }
     }
     c->f32_blocks = nb;
+    c->refine_pending = A.refine != nullptr;
     for (int attempt = 0; attempt < 2; ++attempt) {
         BH_CUDA(c, cudaMemsetAsync(A.nrefine, 0, sizeof(unsigned long long), c->stream));
         BH_TRY(timing_begin(c));
@@ -1301,12 +1302,16 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
             BH_TRY(contact_pass(c, A, fp, p, (unsigned)(c->num_sms * 4)));
             break;
         }
-        // size the FP64 contact pass (one read-back per evaluation); on overflow
-        // grow the list and evaluate again
-        unsigned long long np = 0;
-        BH_CUDA(c, cudaMemcpyAsync(&np, A.ncontact, sizeof(np), cudaMemcpyDeviceToHost, c->stream));
+        // size the FP64 contact pass (one read-back per evaluation, which also
+        // brings the refinement count); on overflow grow the list and
+        // evaluate again
+        unsigned long long w[5] = {0, 0, 0, 0, 0};  // d_small words 16..20
+        BH_CUDA(c, cudaMemcpyAsync(w, A.ncontact, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
         BH_CUDA(c, cudaStreamSynchronize(c->stream));
+        const unsigned long long np = w[0];
         c->n_contacts = (int64_t)np;
+        c->n_refined = (int64_t)w[4];
+        c->refine_pending = false;
         if ((int64_t)np > A.contact_cap) {
             BH_TRY(grow(c, c->contacts, (size_t)(np + np / 4 + 1024), "contact pairs"));
             A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
