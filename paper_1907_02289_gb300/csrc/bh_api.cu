@@ -643,7 +643,7 @@ int bh_destroy(bh_ctx* ctx) {
     release(c->level); release(c->nchild); release(c->begin); release(c->end); release(c->parent);
     release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->skip); release(c->split_cnt);
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
-    release(c->cz); release(c->Q); release(c->cell32); release(c->cell32lo); release(c->refine); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
+    release(c->cz); release(c->Q); release(c->cell32); release(c->cell32lo); release(c->refine); release(c->cbnd); release(c->cslot); release(c->cflag); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);
     release(c->cnt_c); release(c->cnt_j); release(c->cnt_jm); release(c->stash_p); release(c->stash_c); release(c->P); release(c->C); release(c->JJ); release(c->ipp);
     release(c->hbuf); release(c->hid);

@@ -140,6 +140,9 @@ struct Ctx {
     DBuf<float> cell32lo;            // per node: exact mass - M of the record (FP32)
     DBuf<float4> phi, plo;           // per particle FP32 split: (x_hi, m), (x_lo, 0)
     DBuf<uint2> refine;                 // (particle, list slot) queued for the refinement pass
+    DBuf<float> cbnd;                   // particles with contact candidates: FP32 bound,
+    DBuf<uint32_t> cslot;               // list slot,
+    DBuf<unsigned> cflag;               // and a flag the post-contact check claims
     DBuf<unsigned long long> contacts;  // (i, j) contact candidates for the FP64 pass
     DBuf<double> diag;                   // diagnostic partial sums
     DBuf<double> pot;                    // per-particle potential when the caller passes none

@@ -131,6 +131,7 @@ struct Smem32 {
     float ahi[32 * kSlots][3];  // compensated sums (G-free), hi part
     float alo[32 * kSlots][3];  // low part
     float abnd[32 * kSlots];    // sum over folds of squared tile partial sums (conditioning of the sum)
+    uint8_t hasc[32 * kSlots];  // the slot's particle has a contact candidate
 };
 
 struct Args {
@@ -169,6 +170,12 @@ struct Args {
     uint2* refine;
     unsigned long long* nrefine;
     double kref;
+    // particles with a contact candidate are judged after the contact pass
+    // (the spring can cancel the gravity): their bound and list slot wait here
+    float* cbnd;
+    uint32_t* cslot;
+    unsigned* cflag;
+    const double *vx, *vy, *vz, *m;  // FP64 arrays for the refinement's contact terms
 };
 
 __device__ __forceinline__ float rel(float hi, float lo, float ohi, float olo) {
@@ -265,6 +272,7 @@ __device__ __forceinline__ void queue_pair(const Args& A, Smem32& S, int& qn, co
             if (bits & (1u << (2 * r + h))) {
                 S.q_i[pos] = K.iv[r];
                 S.q_j[pos] = jid[h];
+                S.hasc[32 * r + lane] = 1;
                 ++pos;
             }
     qn += total;
@@ -591,6 +599,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
             S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
         }
         S.abnd[32 * r + lane] = 0.f;
+        S.hasc[32 * r + lane] = 0;
     }
     int qn = 0;
     __syncwarp();
@@ -717,18 +726,24 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
 #pragma unroll
         for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
         float bnd = S.abnd[s];
+        int hc = S.hasc[s];
         if (tail)
             for (int o = T; o < 32; o <<= 1) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
                 bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+                hc |= __shfl_xor_sync(0xffffffffu, hc, o);
             }
         if (K.vl[r] && (!tail || tj == 0)) {
             const uint32_t i = K.iv[r];
             // an ill-conditioned sum (terms far larger than the total) goes to
             // the refinement pass, which rewrites a_i
             const double kg = A.kref * A.fp.G;
-            if (A.refine && a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < kg * kg * (double)bnd) {
+            if (A.refine && hc) {  // judged with its contact term, after the contact pass
+                A.cbnd[i] = bnd;
+                A.cslot[i] = (uint32_t)k;
+                A.cflag[i] = 1u;
+            } else if (A.refine && a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < kg * kg * (double)bnd) {
                 const unsigned long long q = atomicAdd(A.nrefine, 1ull);
                 A.refine[q] = make_uint2(i, (uint32_t)k);
             }
@@ -982,9 +997,13 @@ __global__ void k_contacts_apply(const uint2* __restrict__ pairs, const unsigned
 // terms (Eq. (1)'s gravity with the r_coll floor; monopole + quadrupole),
 // in df arithmetic (hi + lo pairs of FP32 numbers, about 44 bits; see
 // dfloat.cuh) from the hi/lo particle coordinates and masses and the cell
-// records with their mass corrections.  One warp per queued particle; the
-// lanes split the entries and the partial sums are reduced in df.  The
-// result replaces a_i (the FP64 contact pass adds its term afterwards).
+// records with their mass corrections, with the contact terms of its pairs
+// within reach evaluated in FP64 as the contact pass does.  One warp per
+// queued particle; the lanes split the entries and the partial sums are
+// reduced in df.  The result replaces a_i; the pass runs after the contact
+// pass, whose terms it includes.  A particle with a contact candidate is
+// judged only after that pass (k_flag_contacts): the spring term can cancel
+// the pull of the neighbour it touches.
 struct RefineConsts {
     df rc2, eps2, rc2eps2;  // r_coll^2, eps^2, r_coll^2 + eps^2
 };
@@ -995,11 +1014,14 @@ __device__ __forceinline__ df df_of(double v) {
 }
 
 __device__ __forceinline__ void ref_pp(const Args& A, const RefineConsts& K, float xh, float xl, float yh, float yl,
-                                       float zh, float zl, uint32_t j, df (&acc)[3]) {
+                                       float zh, float zl, uint32_t i, uint32_t j, df (&acc)[3], double (&ac)[3]) {
     const float4 h = A.phi[j], l = A.plo[j];
     const df d[3] = {df_diff(h.x, l.x, xh, xl), df_diff(h.y, l.y, yh, yl), df_diff(h.z, l.z, zh, zl)};
     const df r2 = df_dot3(d[0], d[1], d[2]);
     if (r2.hi == 0.f) return;  // coincident pair: no term
+    if (r2.hi < A.rc2chk)  // the contact term of the FP64 pass, decided and evaluated as there
+        contact_term64(A.fp, A.x[i], A.y[i], A.z[i], A.vx[i], A.vy[i], A.vz[i], A.m[i], A.x[j], A.y[j], A.z[j],
+                       A.vx[j], A.vy[j], A.vz[j], A.m[j], ac);
     const df s2 = df_gt(r2, K.rc2) ? df_add(r2, K.eps2) : K.rc2eps2;
     const df y = df_rsqrt(s2);
     const df f = df_mul(df_mul(fast_two_sum(h.w, l.w), y), df_mul(y, y));  // m / s^3
@@ -1039,6 +1061,31 @@ __device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, con
     for (int c = 0; c < 3; ++c) acc[c] = df_add(acc[c], t[c]);
 }
 
+// After the contact pass: each particle with a contact candidate (claimed
+// once through its flag) is queued when its tree part, gravity and contact,
+// is small against its FP32 bound.
+__global__ void k_flag_contacts(const Args A, const uint2* __restrict__ pairs, const unsigned long long* count,
+                                int64_t cap) {
+    int64_t np = (int64_t)*count;
+    if (np > cap) np = cap;
+    const double kg = A.kref * A.fp.G;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < np; u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = pairs[u].x;
+        if (i >= A.n || atomicExch(&A.cflag[i], 0u) == 0u) continue;
+        double a[3] = {A.ax[i], A.ay[i], A.az[i]};
+        if (A.add_central) {  // the tree part: the central term taken off again
+            double c[3] = {0.0, 0.0, 0.0};
+            central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], c);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a[q] -= c[q];
+        }
+        if (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] < kg * kg * (double)A.cbnd[i]) {
+            const unsigned long long q = atomicAdd(A.nrefine, 1ull);
+            if ((int64_t)q < (int64_t)A.n) A.refine[q] = make_uint2(i, A.cslot[i]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineConsts K, const float* __restrict__ mlo,
                                                   int64_t cap) {
     const int lane = threadIdx.x & 31;
@@ -1058,8 +1105,9 @@ __global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineCons
         const uint32_t b = A.begin[g], en = A.end[g];
         const float4 hi = A.phi[i], lo = A.plo[i];
         df acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        double ac[3] = {0.0, 0.0, 0.0};  // contact terms (FP64)
         for (uint32_t j = b + lane; j < en; j += 32)
-            if (j != i) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, j, acc);
+            if (j != i) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, acc, ac);
         const int64_t j1 = A.jj_off[k + 1];
         for (int64_t p = A.jj_off[k] + lane; p < j1; p += 32) {
             const uint32_t j = A.JJ[p];
@@ -1067,7 +1115,7 @@ __global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineCons
                 atomicOr(A.status, kStatBounds);
                 continue;
             }
-            ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, j, acc);
+            ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, acc, ac);
         }
         const int64_t c1 = A.pc_off[k + 1];
         for (int64_t p = A.pc_off[k] + lane; p < c1; p += 32) {
@@ -1084,11 +1132,12 @@ __global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineCons
             for (int c = 0; c < 3; ++c) {
                 const df v = {__shfl_xor_sync(0xffffffffu, acc[c].hi, o), __shfl_xor_sync(0xffffffffu, acc[c].lo, o)};
                 acc[c] = df_add(acc[c], v);
+                ac[c] += __shfl_xor_sync(0xffffffffu, ac[c], o);
             }
         if (lane == 0) {
             double a[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) a[c] = A.fp.G * df_to_double(acc[c]);
+            for (int c = 0; c < 3; ++c) a[c] = A.fp.G * df_to_double(acc[c]) + ac[c];
             if (A.add_central) central_newton(A.fp.GMc, A.x[i], A.y[i], A.z[i], a);
             A.ax[i] = a[0];
             A.ay[i] = a[1];
@@ -1190,6 +1239,15 @@ int refine_pass(Ctx* c, const Args& A, const ForceParams& fp) {
     return stage_end(c);
 }
 
+// The particles with contact candidates, judged after the contact pass.
+int flag_pass(Ctx* c, const Args& A, unsigned nb) {
+    if (!A.refine) return BH_OK;
+    BH_TRY(stage_begin(c, BH_STAGE_REFINE));
+    k_flag_contacts<<<nb, 128, 0, c->stream>>>(A, A.contacts, A.ncontact, A.contact_cap);
+    BH_LAUNCH(c);
+    return stage_end(c);
+}
+
 int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, unsigned nb) {
     BH_TRY(stage_begin(c, BH_STAGE_CONTACTS));
     unsigned long long* acc = c->contact_acc.p;
@@ -1263,9 +1321,26 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     A.kref = BH_REFINE_K;
     A.nrefine = c->d_small + 20;
     A.refine = nullptr;
+    A.cbnd = nullptr;
+    A.cslot = nullptr;
+    A.cflag = nullptr;
+    A.vx = p->vx;
+    A.vy = p->vy;
+    A.vz = p->vz;
+    A.m = p->m;
     if (A.kref > 0.0) {
         BH_TRY(grow(c, c->refine, (size_t)c->n, "refinement queue"));
         A.refine = c->refine.p;
+        if (contact) {
+            const bool fresh = c->cflag.cap < (size_t)c->n;
+            BH_TRY(grow(c, c->cbnd, (size_t)c->n, "contact-particle bounds"));
+            BH_TRY(grow(c, c->cslot, (size_t)c->n, "contact-particle list slots"));
+            BH_TRY(grow(c, c->cflag, (size_t)c->n, "contact-particle flags"));
+            if (fresh) BH_CUDA(c, cudaMemsetAsync(c->cflag.p, 0, c->cflag.cap * sizeof(unsigned), c->stream));
+            A.cbnd = c->cbnd.p;
+            A.cslot = c->cslot.p;
+            A.cflag = c->cflag.p;
+        }
     }
     unsigned nb;
     if (c->tune.sched == BH_SCHED_GRID) {
@@ -1285,7 +1360,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         }
     }
     c->f32_blocks = nb;
-    c->refine_pending = A.refine != nullptr;
+    c->refine_pending = A.refine != nullptr;  // its count is read when asked for
     for (int attempt = 0; attempt < 2; ++attempt) {
         BH_CUDA(c, cudaMemsetAsync(A.nrefine, 0, sizeof(unsigned long long), c->stream));
         BH_TRY(timing_begin(c));
@@ -1294,24 +1369,25 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         BH_LAUNCH(c);
         BH_TRY(stage_end(c));
         BH_TRY(timing_end(c));
-        BH_TRY(refine_pass(c, A, fp));
-        if (!contact) break;
-        if (c->capturing) {
-            // inside a captured graph: no read-back; the pass takes the count
-            // from the device and flags an overflow in the status word
-            BH_TRY(contact_pass(c, A, fp, p, (unsigned)(c->num_sms * 4)));
+        if (!contact) {
+            BH_TRY(refine_pass(c, A, fp));
             break;
         }
-        // size the FP64 contact pass (one read-back per evaluation, which also
-        // brings the refinement count); on overflow grow the list and
-        // evaluate again
-        unsigned long long w[5] = {0, 0, 0, 0, 0};  // d_small words 16..20
-        BH_CUDA(c, cudaMemcpyAsync(w, A.ncontact, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+        if (c->capturing) {
+            // inside a captured graph: no read-back; the passes take the count
+            // from the device and an overflow is flagged in the status word
+            const unsigned nbc = (unsigned)(c->num_sms * 4);
+            BH_TRY(contact_pass(c, A, fp, p, nbc));
+            BH_TRY(flag_pass(c, A, nbc));
+            BH_TRY(refine_pass(c, A, fp));
+            break;
+        }
+        // size the FP64 contact pass (one read-back per evaluation); on
+        // overflow grow the list and evaluate again
+        unsigned long long np = 0;
+        BH_CUDA(c, cudaMemcpyAsync(&np, A.ncontact, sizeof(np), cudaMemcpyDeviceToHost, c->stream));
         BH_CUDA(c, cudaStreamSynchronize(c->stream));
-        const unsigned long long np = w[0];
         c->n_contacts = (int64_t)np;
-        c->n_refined = (int64_t)w[4];
-        c->refine_pending = false;
         if ((int64_t)np > A.contact_cap) {
             BH_TRY(grow(c, c->contacts, (size_t)(np + np / 4 + 1024), "contact pairs"));
             A.contacts = reinterpret_cast<uint2*>(c->contacts.p);
@@ -1320,7 +1396,11 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
             if (A.ticket) BH_CUDA(c, cudaMemsetAsync(A.ticket, 0, sizeof(unsigned long long), c->stream));
             continue;
         }
-        if (np > 0) BH_TRY(contact_pass(c, A, fp, p, blocks_for((int64_t)np, 128)));
+        if (np > 0) {
+            BH_TRY(contact_pass(c, A, fp, p, blocks_for((int64_t)np, 128)));
+            BH_TRY(flag_pass(c, A, blocks_for((int64_t)np, 128)));
+        }
+        BH_TRY(refine_pass(c, A, fp));
         break;
     }
     return BH_OK;
