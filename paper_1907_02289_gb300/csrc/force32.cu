@@ -128,8 +128,7 @@ struct Smem32 {
     uint8_t trig[kTileJ / 2];  // list pairs of the current tile with a contact candidate
     uint32_t q_i[kQueueCap];   // contact candidates (i, j) waiting for the global list
     uint32_t q_j[kQueueCap];
-    float ahi[32 * kSlots][3];  // compensated sums (G-free), hi part
-    float alo[32 * kSlots][3];  // low part
+    float2 acc[32 * kSlots][3];  // compensated sums (G-free): (hi, lo), one 8-byte access each
     float abnd[32 * kSlots];    // sum over folds of squared tile partial sums (conditioning of the sum)
     uint8_t hasc[32 * kSlots];  // the slot's particle has a contact candidate
 };
@@ -362,12 +361,12 @@ __device__ __forceinline__ void fold(Smem32& S, int s, float2 (&g)[3]) {
     for (int c = 0; c < 3; ++c) {
         const float t = __fadd_rn(g[c].x, g[c].y);
         bnd = __fmaf_rn(t, t, bnd);
-        const float hi = S.ahi[s][c];
+        const float2 cur = S.acc[s][c];
+        const float hi = cur.x;
         const float s1 = __fadd_rn(hi, t);
         const float bp = __fsub_rn(s1, hi);
         const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bp)), __fsub_rn(t, bp));
-        S.ahi[s][c] = s1;
-        S.alo[s][c] = __fadd_rn(S.alo[s][c], err);
+        S.acc[s][c] = make_float2(s1, __fadd_rn(cur.y, err));
         g[c] = make_float2(0.f, 0.f);
     }
     S.abnd[s] += bnd;
@@ -596,7 +595,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
             K.nh[r][c] = f2(-rh);
             K.nl[r][c] = f2(-rl);
             K.g[r][c] = make_float2(0.f, 0.f);
-            S.ahi[32 * r + lane][c] = S.alo[32 * r + lane][c] = 0.f;
+            S.acc[32 * r + lane][c] = make_float2(0.f, 0.f);
         }
         S.abnd[32 * r + lane] = 0.f;
         S.hasc[32 * r + lane] = 0;
@@ -724,7 +723,7 @@ __device__ __forceinline__ void group_chunk(const Args& A, Smem32& S, int64_t k,
         const int s = 32 * r + lane;
         double a[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.ahi[s][c] + (double)S.alo[s][c]);
+        for (int c = 0; c < 3; ++c) a[c] = A.fp.G * ((double)S.acc[s][c].x + (double)S.acc[s][c].y);
         float bnd = S.abnd[s];
         int hc = S.hasc[s];
         if (tail)
@@ -1045,17 +1044,20 @@ __device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, con
 #pragma unroll
     for (int c = 0; c < 3; ++c) t[c] = df_mul(mono, R[c]);
     if (A.fp.order >= 2) {
+        // the quadrupole part, at most about theta^2 of the monopole, in FP32
+        // from the df separation (its FP32 rounding stays far below the
+        // monopole's df accuracy)
         const float4 r2v = A.cell32[3 * (int64_t)cc + 2];
-        const float qxx = r1.w, qxy = r2v.x, qxz = r2v.y, qyy = r2v.z, qyz = r2v.w;
-        const df qzz = df_neg(two_sum(qxx, qyy));
-        const df q[3] = {df_add(df_add(df_mul_f(R[0], qxx), df_mul_f(R[1], qxy)), df_mul_f(R[2], qxz)),
-                         df_add(df_add(df_mul_f(R[0], qxy), df_mul_f(R[1], qyy)), df_mul_f(R[2], qyz)),
-                         df_add(df_add(df_mul_f(R[0], qxz), df_mul_f(R[1], qyz)), df_mul(R[2], qzz))};
-        const df rqr = df_add(df_add(df_mul(R[0], q[0]), df_mul(R[1], q[1])), df_mul(R[2], q[2]));
-        const df y5 = df_mul(y3, y2);
-        const df w = df_mul_f(df_mul(rqr, df_mul(y5, y2)), -2.5f);  // -5/2 (R.Q.R) / R^7
-#pragma unroll
-        for (int c = 0; c < 3; ++c) t[c] = df_add(t[c], df_add(df_mul(y5, q[c]), df_mul(w, R[c])));
+        const float qxx = r1.w, qxy = r2v.x, qxz = r2v.y, qyy = r2v.z, qyz = r2v.w, qzz = -(qxx + qyy);
+        const float Rx = R[0].hi, Ry = R[1].hi, Rz = R[2].hi;
+        const float qx = qxx * Rx + qxy * Ry + qxz * Rz, qy = qxy * Rx + qyy * Ry + qyz * Rz,
+                    qz = qxz * Rx + qyz * Ry + qzz * Rz;
+        const float rqr = Rx * qx + Ry * qy + Rz * qz;
+        const float yf = y.hi, y2f = yf * yf, y5f = y2f * y2f * yf;
+        const float w = -2.5f * rqr * y5f * y2f;  // -5/2 (R.Q.R) / R^7
+        t[0] = df_add(t[0], df_make(y5f * qx + w * Rx));
+        t[1] = df_add(t[1], df_make(y5f * qy + w * Ry));
+        t[2] = df_add(t[2], df_make(y5f * qz + w * Rz));
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = df_add(acc[c], t[c]);
