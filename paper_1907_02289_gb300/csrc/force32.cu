@@ -405,7 +405,14 @@ template <bool FAR>
 __device__ __forceinline__ void put_particle(Smem32& S, int u, bool real, const float (&oh)[3],
                                              const float (&ol)[3]) {
     float ph[3], pl[3], pm;
-    if (real) {
+    if (real && FAR) {  // the rounded relative coordinates only: 3 additions each
+        const float4 h = S.raw.p.h[u], l = S.raw.p.l[u];
+        ph[0] = rel(h.x, l.x, oh[0], ol[0]);
+        ph[1] = rel(h.y, l.y, oh[1], ol[1]);
+        ph[2] = rel(h.z, l.z, oh[2], ol[2]);
+        pl[0] = pl[1] = pl[2] = 0.f;
+        pm = h.w;
+    } else if (real) {
         const float4 h = S.raw.p.h[u], l = S.raw.p.l[u];
         rel2(h.x, l.x, oh[0], ol[0], ph[0], pl[0]);
         rel2(h.y, l.y, oh[1], ol[1], ph[1], pl[1]);
@@ -1013,8 +1020,8 @@ __device__ __forceinline__ df df_of(double v) {
 }
 
 __device__ __forceinline__ void ref_pp(const Args& A, const RefineConsts& K, float xh, float xl, float yh, float yl,
-                                       float zh, float zl, uint32_t i, uint32_t j, df (&acc)[3], double (&ac)[3]) {
-    const float4 h = A.phi[j], l = A.plo[j];
+                                       float zh, float zl, uint32_t i, uint32_t j, const float4 h, const float4 l,
+                                       df (&acc)[3], double (&ac)[3]) {
     const df d[3] = {df_diff(h.x, l.x, xh, xl), df_diff(h.y, l.y, yh, yl), df_diff(h.z, l.z, zh, zl)};
     const df r2 = df_dot3(d[0], d[1], d[2]);
     if (r2.hi == 0.f) return;  // coincident pair: no term
@@ -1028,17 +1035,25 @@ __device__ __forceinline__ void ref_pp(const Args& A, const RefineConsts& K, flo
     for (int c = 0; c < 3; ++c) acc[c] = df_add(acc[c], df_mul(f, d[c]));
 }
 
-__device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, const float* __restrict__ mlo,
-                                       float xh, float xl, float yh, float yl, float zh, float zl, int32_t cc,
-                                       df (&acc)[3]) {
-    const float4 r0 = A.cell32[3 * (int64_t)cc], r1 = A.cell32[3 * (int64_t)cc + 1];
+struct CellRec {
+    float4 r0, r1, r2;
+    float mlo;
+};
+
+__device__ __forceinline__ CellRec load_cell(const Args& A, const float* __restrict__ mlo, int32_t cc) {
+    return {A.cell32[3 * (int64_t)cc], A.cell32[3 * (int64_t)cc + 1], A.cell32[3 * (int64_t)cc + 2], mlo[cc]};
+}
+
+__device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, float xh, float xl, float yh, float yl,
+                                       float zh, float zl, const CellRec& cr, df (&acc)[3]) {
+    const float4 r0 = cr.r0, r1 = cr.r1;
     // R = x_i - c (the oracle's sign); a = -M R / R^3 + Q R / R^5 - 5/2 (R.Q.R) R / R^7 (G-free)
     const df R[3] = {df_diff(xh, xl, r0.x, r1.x), df_diff(yh, yl, r0.y, r1.y), df_diff(zh, zl, r0.z, r1.z)};
     const df R2 = df_add(df_dot3(R[0], R[1], R[2]), K.eps2);
     const df y = df_rsqrt(R2);
     const df y2 = df_mul(y, y);
     const df y3 = df_mul(y2, y);
-    const df M = fast_two_sum(r0.w, mlo[cc]);
+    const df M = fast_two_sum(r0.w, cr.mlo);
     const df mono = df_neg(df_mul(M, y3));
     df t[3];
 #pragma unroll
@@ -1047,7 +1062,7 @@ __device__ __forceinline__ void ref_pc(const Args& A, const RefineConsts& K, con
         // the quadrupole part, at most about theta^2 of the monopole, in FP32
         // from the df separation (its FP32 rounding stays far below the
         // monopole's df accuracy)
-        const float4 r2v = A.cell32[3 * (int64_t)cc + 2];
+        const float4 r2v = cr.r2;
         const float qxx = r1.w, qxy = r2v.x, qxz = r2v.y, qyy = r2v.z, qyz = r2v.w, qzz = -(qxx + qyy);
         const float Rx = R[0].hi, Ry = R[1].hi, Rz = R[2].hi;
         const float qx = qxx * Rx + qxy * Ry + qxz * Rz, qy = qxy * Rx + qyy * Ry + qyz * Rz,
@@ -1108,25 +1123,82 @@ __global__ void __launch_bounds__(256) k_refine32(const Args A, const RefineCons
         const float4 hi = A.phi[i], lo = A.plo[i];
         df acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         double ac[3] = {0.0, 0.0, 0.0};  // contact terms (FP64)
-        for (uint32_t j = b + lane; j < en; j += 32)
-            if (j != i) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, acc, ac);
-        const int64_t j1 = A.jj_off[k + 1];
-        for (int64_t p = A.jj_off[k] + lane; p < j1; p += 32) {
-            const uint32_t j = A.JJ[p];
-            if (j >= A.n) {
-                atomicOr(A.status, kStatBounds);
-                continue;
+        // each loop loads the next entry's data before evaluating the current one
+        {
+            uint32_t j = b + lane;
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+            if (j < en) {
+                h = A.phi[j];
+                l = A.plo[j];
             }
-            ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, acc, ac);
+            for (; j < en; j += 32) {
+                const uint32_t jn = j + 32;
+                float4 hn = h, ln = l;
+                if (jn < en) {
+                    hn = A.phi[jn];
+                    ln = A.plo[jn];
+                }
+                if (j != i) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, h, l, acc, ac);
+                h = hn;
+                l = ln;
+            }
         }
-        const int64_t c1 = A.pc_off[k + 1];
-        for (int64_t p = A.pc_off[k] + lane; p < c1; p += 32) {
-            const int32_t cc = A.C[p];
-            if (cc < 0 || cc >= A.nn) {
-                atomicOr(A.status, kStatBounds);
-                continue;
+        {
+            const int64_t j1 = A.jj_off[k + 1];
+            int64_t p = A.jj_off[k] + lane;
+            auto index = [&](int64_t q) -> uint32_t {
+                if (q >= j1) return kNone;
+                const uint32_t j = A.JJ[q];
+                if (j >= A.n) {
+                    atomicOr(A.status, kStatBounds);
+                    return kNone;
+                }
+                return j;
+            };
+            uint32_t j = index(p), jn = index(p + 32);
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+            if (j != kNone) {
+                h = A.phi[j];
+                l = A.plo[j];
             }
-            ref_pc(A, K, mlo, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, cc, acc);
+            for (; p < j1; p += 32) {
+                const uint32_t jnn = index(p + 64);
+                float4 hn = h, ln = l;
+                if (jn != kNone) {
+                    hn = A.phi[jn];
+                    ln = A.plo[jn];
+                }
+                if (j != kNone) ref_pp(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, i, j, h, l, acc, ac);
+                j = jn;
+                jn = jnn;
+                h = hn;
+                l = ln;
+            }
+        }
+        {
+            const int64_t c1 = A.pc_off[k + 1];
+            int64_t p = A.pc_off[k] + lane;
+            auto index = [&](int64_t q) -> int32_t {
+                if (q >= c1) return -1;
+                const int32_t cc = A.C[q];
+                if (cc < 0 || cc >= A.nn) {
+                    atomicOr(A.status, kStatBounds);
+                    return -1;
+                }
+                return cc;
+            };
+            int32_t cc = index(p), cn = index(p + 32);
+            CellRec cr = {};
+            if (cc >= 0) cr = load_cell(A, mlo, cc);
+            for (; p < c1; p += 32) {
+                const int32_t cnn = index(p + 64);
+                CellRec crn = cr;
+                if (cn >= 0) crn = load_cell(A, mlo, cn);
+                if (cc >= 0) ref_pc(A, K, hi.x, lo.x, hi.y, lo.y, hi.z, lo.z, cr, acc);
+                cc = cn;
+                cn = cnn;
+                cr = crn;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
