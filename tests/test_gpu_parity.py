@@ -284,15 +284,23 @@ def test_fp32_moments_close(built, name):
     assert np.all(np.abs(mo["Q"] - ref.mom["Q"]) <= 1e-5 * scale)
 
 
-@pytest.mark.parametrize("n_g", [16, 40, 100, 200, 300])
-def test_fp32_every_group_size_class(n_g):
+@pytest.mark.parametrize("n_g,chunk", [(16, 96), (40, 96), (100, 96), (200, 96), (300, 96), (100, 32), (200, 64),
+                                       (300, 32)])
+def test_fp32_every_group_size_class(n_g, chunk):
     """Groups from a few particles to several i-chunks (every slot/tail
-    variant of the FP32 kernel and multi-chunk groups)."""
+    variant of the FP32 kernel and multi-chunk groups, at each i-chunk)."""
+    from paper_1907_02289_gb300 import bh
     P = synth.ring(30000, 21, r_in=0.999, r_out=1.001, phi_max=0.05)
     prm = ring_prm(n_g=n_g, n_leaf=min(8, n_g))
     ref = orc.rebuild(P, orc_params(prm))
     sizes = ref.tree["end"][ref.groups].astype(int) - ref.tree["begin"][ref.groups]
-    assert sizes.max() > min(n_g, 96) // 2
+    assert sizes.max() > min(n_g, chunk) // 2
     aref = orc.tree_forces(ref, orc_params(prm))
-    ctx, D = gpu_build(P, prm, precision=1)
-    assert_force_close(accel_of(D), aref, TOL32, f"n_g={n_g}")
+    ctx = bh.Context(**dict(prm, precision=1))
+    ctx.bh_set_tuning(chunk=chunk)
+    D = bh.Particles(P)
+    ctx.bh_build_tree(D)
+    ctx.bh_make_lists()
+    ctx.bh_compute_forces(D, bh.BH_FORCE_TREE_ONLY)
+    ctx.bh_sync()
+    assert_force_close(accel_of(D), aref, TOL32, f"n_g={n_g} chunk={chunk}")
