@@ -124,6 +124,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ring64m_fp32")
     ap.add_argument("--n", type=int, default=None, help="override the particle count")
+    ap.add_argument("--sector-of", type=int, default=None,
+                    help="with --n: a ring sector of n particles at the surface density of a ring of this many "
+                         "(a small case whose lists look like the large ring's, for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
@@ -395,7 +398,10 @@ def run_ours(args):
         n = int(offsets[-1])
     else:
         n = args.n or pr["n"]
-        P = synth.ring(n, replica_seed(pr["seed"], rank)) if pr["kind"] == "ring" else synth.make(args.workload, n)[0]
+        if args.sector_of and pr["kind"] == "ring":
+            P = synth.ring(n, replica_seed(pr["seed"], rank), phi_max=2 * math.pi * n / args.sector_of)
+        else:
+            P = synth.ring(n, replica_seed(pr["seed"], rank)) if pr["kind"] == "ring" else synth.make(args.workload, n)[0]
     stream = torch.cuda.current_stream()
 
     ctx = bh.Context(offsets=offsets, **prm)
@@ -617,7 +623,9 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32" if prm["precision"] == 1 else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "N": n, "theta": prm["theta"], "n_g": prm["n_g"],
+                "config": {"workload": args.workload, "N": n,
+                           **({"sector_of_N": args.sector_of} if args.sector_of else {}),
+                           "theta": prm["theta"], "n_g": prm["n_g"],
                            "n_leaf": prm["n_leaf"],
                            "key_frame": "cylindrical (phi, r, z)" if prm.get("key_frame", 0) == 1 else "Cartesian",
                            "order": prm["order"], "rebuild_every": prm["rebuild_every"],
