@@ -183,6 +183,15 @@ typedef struct {
                                        * (bh_get_timing); steps run as a captured
                                        * graph are not timed                     */
     int64_t stage_calls[BH_N_STAGES]; /* timed calls of each stage                */
+    int64_t n_graph_builds;      /* list-constructing steps of bh_step run as one CUDA
+                                  * graph launch (bh_tuning.graph = 1)          */
+    int64_t n_graph_build_redos; /* ... of those, steps whose buffers (sized from the
+                                  * previous build with room to grow) turned out
+                                  * too small: the graph stopped after the reordering
+                                  * and the step was finished eagerly, with the
+                                  * same result                                 */
+    int64_t n_graph_captures;    /* step graphs captured (and instantiated) so far,
+                                  * list-reusing and list-constructing         */
 } bh_counters;
 
 /* Create a context.  stream: a cudaStream_t (NULL = legacy default stream).
@@ -309,12 +318,25 @@ typedef struct {
     int warps;         /* warps per block of the FP32 force kernel, 1..8 */
     int sched;         /* BH_SCHED_* */
     int order_by_cost; /* 0 or 1 */
-    int graph;         /* 1: bh_step issues each list-reusing step (kick-drift,
-                          moment refresh, force kernel, contact pass, kick) as
-                          one CUDA graph launch, captured after each list
-                          build; the contact pass then reads its count on the
-                          device, and an overflow of its buffer is reported
-                          (BH_E_LIST_OVERFLOW) at the next synchronising call */
+    int graph;         /* 1: bh_step issues every step as one CUDA graph launch.
+                          A list-reusing step (kick-drift, moment refresh,
+                          force kernel, contact pass, kick) is captured after
+                          each list build.  A list-constructing step (kick-
+                          drift, keys, sort, reordering, tree, moments,
+                          groups, walk, lists, forces, kick) reads no size
+                          back while it runs: its buffers are sized from the
+                          previous build with graph_room percent to grow and
+                          it is captured again when a build has used half of
+                          that room; a step that outgrows them stops after the
+                          reordering and is finished eagerly (same result;
+                          bh_counters.n_graph_build_redos).  The step waits
+                          once, at its end, for the new list sizes.  A list
+                          capacity (bh_params.list_capacity) keeps list-
+                          constructing steps eager.  2: list-reusing steps
+                          only.  In graph steps the contact pass reads its
+                          count on the device, and an overflow of its buffer
+                          is reported (BH_E_LIST_OVERFLOW) at the next
+                          synchronising call */
     int order_window;  /* 0: one global size-class order; w > 0: the size-class
                           order is applied within windows of w consecutive
                           groups (list order = Morton order), so the warps in
@@ -326,6 +348,9 @@ typedef struct {
                           next synchronising call (that step's contact terms
                           are then incomplete); eager evaluations always grow
                           the buffer instead */
+    int graph_room;    /* list-constructing graph steps: percent of room over the
+                          last build's node, group and list counts that their
+                          buffers get (0..1000, default 25) */
 } bh_tuning;
 /* Errors: BH_E_INVAL for a value out of range (n_g < n_leaf included). */
 int bh_set_tuning(bh_ctx* ctx, const bh_tuning* t);

@@ -50,7 +50,9 @@ class bh_counters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n_groups", "n_pp", "n_pc", "n_evals", "n_rebuilds", "n_launches",
                                                "n_contacts", "n_pp_far", "n_one_walk_builds",
                                                "n_h2d_bytes", "n_d2h_bytes", "n_refined")] + [
-        ("stage_ms", ctypes.c_double * BH_N_STAGES), ("stage_calls", ctypes.c_int64 * BH_N_STAGES)]
+        ("stage_ms", ctypes.c_double * BH_N_STAGES), ("stage_calls", ctypes.c_int64 * BH_N_STAGES),
+        ("n_graph_builds", ctypes.c_int64), ("n_graph_build_redos", ctypes.c_int64),
+        ("n_graph_captures", ctypes.c_int64)]
 
 
 class bh_diagnostics(ctypes.Structure):
@@ -62,7 +64,7 @@ class bh_diagnostics(ctypes.Structure):
 
 class bh_tuning(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int) for f in ("n_g", "chunk", "warps", "sched", "order_by_cost", "graph", "order_window",
-                                            "graph_contact_room")]
+                                            "graph_contact_room", "graph_room")]
 
 
 _lib = None

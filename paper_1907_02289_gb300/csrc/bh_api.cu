@@ -22,6 +22,8 @@ int fail(Ctx* c, int code, const char* fmt, ...) {
 
 int grow_raw(Ctx* c, void** p, size_t* cap, size_t need, const char* what, bool keep) {
     if (need <= *cap && *p) return BH_OK;
+    // a captured step cannot allocate: its buffers are sized before capture
+    if (c->capturing) return fail(c, BH_E_STATE, "%s would have to grow inside a captured step", what);
     void* q = nullptr;
     // A buffer that has to grow again (list sizes vary a little from one
     // build to the next) gets a quarter of headroom: each regrowth costs a
@@ -192,6 +194,7 @@ int read_status(Ctx* c) {
     BH_CUDA(c, cudaStreamSynchronize(c->stream));
     if (st) BH_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     if (st & kStatNonFinite) return fail(c, BH_E_INVAL, "non-finite particle coordinate");
+    if (st & kStatAxis) return fail(c, BH_E_INVAL, "the cylindrical key frame needs every particle off the axis (r > 0)");
     if (st & kStatListOverflow) return fail(c, BH_E_LIST_OVERFLOW, "list buffer overflow");
     if (st & kStatTimeout) return fail(c, BH_E_TIMEOUT, "device wait timed out");
     if (st & kStatBounds) return fail(c, BH_E_STATE, "internal index check failed (access skipped)");
@@ -212,15 +215,7 @@ int build_tree(Ctx* c, bh_particles* p) {
         BH_TRY(setup_patches(c, 1, off));
     }
     BH_STAGE(c, BH_STAGE_KEYS, stage_keys(c, p));
-    BH_TRY(read_status(c));
-    c->h_box.resize(8 * (size_t)c->n_patches);
-    BH_CUDA(c, cudaMemcpyAsync(c->h_box.data(), c->d_box, c->h_box.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                               c->stream));
-    BH_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (c->prm.key_frame == 1)
-        for (int q = 0; q < c->n_patches; ++q)
-            if (!(c->h_box[8 * q + 1] > 0.0))
-                return fail(c, BH_E_INVAL, "the cylindrical key frame needs every particle off the axis (r > 0)");
+    BH_TRY(read_status(c));  // non-finite coordinates; a particle on the axis of the cylindrical frame
     BH_STAGE(c, BH_STAGE_SORT, stage_sort(c));
     BH_STAGE(c, BH_STAGE_PERMUTE, stage_permute(c, p));
     BH_TRY(stage_begin(c, BH_STAGE_TREE));
@@ -342,6 +337,7 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
         }
         c->graph_ok = true;
         c->graph_p = *p;
+        ++c->n_graph_captures;
     }
     BH_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
     c->n_launches += c->graph_launches;
@@ -351,16 +347,269 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
     return BH_OK;
 }
 
+// ---- list-constructing steps as one graph ---------------------------------
+// With graph tuning 1, a list-constructing step of bh_step (kick-drift, keys,
+// sort, permutation, tree, moments, groups, walk, lists, forces, contact and
+// refinement passes, kick) is one graph launch.  Its buffers are sized before
+// capture from the previous build, with room to grow; the step reads nothing
+// back while it runs (sizes stay on the device, kSz*).  Two conditional nodes
+// guard it: the work after the tree runs only if the nodes fitted their
+// capacity, the work after the walk only if the lists fitted theirs.  When
+// one did not, the step stops there (positions kicked and drifted, particles
+// reordered, accelerations and the final kick not yet done); the host grows
+// the buffers and finishes the step eagerly, which gives the same result.
+
+__global__ void k_cond_set(cudaGraphConditionalHandle h, const unsigned long long* sz, unsigned long long mask) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, (sz[kSzOvf] & mask) ? 0u : 1u);
+}
+
+namespace {
+
+// The graph being captured on c->stream and its current dependencies.
+int capture_state(Ctx* c, cudaGraph_t* g, const cudaGraphNode_t** deps, size_t* nd) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    BH_CUDA(c, cudaStreamGetCaptureInfo(c->stream, &st, nullptr, g, deps, nullptr, nd));
+    if (st != cudaStreamCaptureStatusActive) return fail(c, BH_E_STATE, "stream capture is not active");
+    return BH_OK;
+}
+
+// Set h from the device (non-zero when none of the mask's overflow bits is
+// set), then add an IF node on h to the graph being captured on c->stream and
+// issue work into its body, captured on body_stream.
+template <class F>
+int capture_if(Ctx* c, unsigned long long mask, cudaStream_t body_stream, F issue) {
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    BH_TRY(capture_state(c, &g, &deps, &nd));
+    cudaGraphConditionalHandle h;
+    BH_CUDA(c, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    k_cond_set<<<1, 32, 0, c->stream>>>(h, c->d_sz, mask);
+    BH_LAUNCH(c);
+    BH_TRY(capture_state(c, &g, &deps, &nd));
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeIf;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    BH_CUDA(c, cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+    BH_CUDA(c, cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = prm.conditional.phGraph_out[0];
+    BH_CUDA(c, cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t s0 = c->stream;
+    c->stream = body_stream;
+    const int rc = issue();
+    c->stream = s0;
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(body_stream, &out);
+    BH_TRY(rc);
+    BH_CUDA(c, e);
+    return BH_OK;
+}
+
+struct HostSizes {
+    int64_t n_nodes, n_groups;
+    int key_cur;
+    std::vector<int64_t> lvl_start;
+};
+
+// Buffers of a device-sized build, grown before capture (nothing can grow
+// inside it): node arrays to the node capacity, group arrays to one group
+// per particle, slots, lists and the FP32 pass buffers.
+int size_dev_build(Ctx* c, const int64_t cap[5]) {
+    const int64_t n = c->n, nodes = cap[0];
+    const bool f32 = c->prm.precision == BH_PREC_FP32;
+    for (auto* b : {&c->level, &c->nchild}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
+    for (auto* b : {&c->begin, &c->end}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
+    for (auto* b : {&c->parent, &c->first_child, &c->skip}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
+    BH_TRY(grow(c, c->qlo, 3 * (size_t)nodes, "node qlo"));
+    BH_TRY(grow(c, c->qhi, 3 * (size_t)nodes, "node qhi"));
+    BH_TRY(grow(c, c->wnode, (size_t)nodes, "walk records"));
+    BH_TRY(grow(c, c->split_cnt, (size_t)nodes, "split counts"));
+    BH_TRY(grow(c, c->split_bnd, 9 * (size_t)nodes, "split bounds"));
+    BH_TRY(grow(c, c->split_off, (size_t)nodes / 256 + 2, "split tile sums"));
+    if (f32) {
+        BH_TRY(grow(c, c->cell32, 3 * (size_t)nodes, "FP32 cell records"));
+        BH_TRY(grow(c, c->cell32lo, (size_t)nodes, "FP32 cell mass corrections"));
+    } else {
+        for (auto* b : {&c->M, &c->cx, &c->cy, &c->cz}) BH_TRY(grow(c, *b, (size_t)nodes, "moments"));
+        BH_TRY(grow(c, c->Q, 6 * (size_t)nodes, "moments Q"));
+    }
+    BH_TRY(grow(c, c->groups, (size_t)n + 1, "groups"));
+    for (auto* b : {&c->cnt_p, &c->cnt_c, &c->cnt_j, &c->cnt_jm})
+        BH_TRY(grow(c, *b, (size_t)n + 1, "list offsets"));
+    BH_TRY(grow(c, c->order, (size_t)n + 1, "group order"));
+    // scans over up to n group counts (8-byte words, 2048 per tile)
+    BH_TRY(grow(c, c->scan_tmp, ((size_t)n / 2048 + 2) * sizeof(int64_t), "scan block sums"));
+    BH_TRY(grow(c, c->stash_p, (size_t)std::max<int64_t>(1, cap[1] * c->walk_cap_p), "stashed particle lists"));
+    BH_TRY(grow(c, c->stash_c, (size_t)std::max<int64_t>(1, cap[1] * c->walk_cap_c), "stashed cell lists"));
+    BH_TRY(grow(c, c->P, (size_t)cap[2] + 1, "particle lists"));
+    BH_TRY(grow(c, c->C, (size_t)cap[3] + 1, "cell lists"));
+    BH_TRY(grow(c, c->JJ, (size_t)cap[4] + 1, "list particle indices"));
+    if (f32 && c->prm.r_coll > 0.0) {
+        const size_t want = c->tune.graph_contact_room > 0 ? (size_t)c->tune.graph_contact_room
+                                                           : (size_t)(2 * c->n_contacts + 65536);
+        if (c->contacts.cap < want) BH_TRY(grow(c, c->contacts, want, "contact pairs"));
+    }
+    return BH_OK;
+}
+
+int capture_rebuild(Ctx* c, bh_particles* p) {
+    const double dt = c->prm.dt;
+    // capacities: the last build's sizes with graph_room percent to grow
+    const int64_t r = c->tune.graph_room;
+    auto room = [r](int64_t v) { return v + v * r / 100 + 64; };
+    int64_t cap[5];
+    cap[0] = room(c->n_nodes);
+    cap[1] = std::min<int64_t>(c->n, room(c->n_groups));
+    cap[2] = room(c->n_pp);
+    cap[3] = room(c->n_pc);
+    cap[4] = room(c->n_jj);
+    BH_TRY(size_dev_build(c, cap));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaStream_t* ss[3] = {&c->cap_stream, &c->body_stream[0], &c->body_stream[1]};
+    for (cudaStream_t* q : ss)
+        if (!*q) BH_CUDA(c, cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
+    const HostSizes keep{c->n_nodes, c->n_groups, c->key_cur, c->lvl_start};
+    c->cap_nodes = cap[0];
+    c->dev_slots = cap[1];
+    const cudaStream_t s0 = c->stream;
+    c->stream = c->cap_stream;
+    {  // (relaxed: the conditional nodes' handles are made while capturing)
+        const cudaError_t eb = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+        if (eb != cudaSuccess) {
+            c->stream = s0;
+            BH_CUDA(c, eb);
+        }
+    }
+    c->capturing = true;
+    c->dev_build = true;
+    const int64_t l0 = c->n_launches;
+    int rc = stage_kick_drift(c, p, 0.5 * dt, dt);
+    if (rc == BH_OK) rc = stage_keys(c, p);
+    if (rc == BH_OK) rc = stage_sort(c);
+    if (rc == BH_OK) rc = stage_permute(c, p);
+    if (rc == BH_OK) rc = stage_octree(c);
+    if (rc == BH_OK)
+        rc = capture_if(c, kOvfNodes, c->body_stream[0], [&]() -> int {
+            BH_TRY(stage_boxes(c));
+            BH_TRY(stage_moments(c, p));
+            BH_TRY(stage_groups(c));
+            BH_TRY(stage_lists_dev_walk(c));
+            return capture_if(c, kOvfLists, c->body_stream[1], [&]() -> int {
+                BH_TRY(stage_lists_dev_fill(c));
+                BH_TRY(stage_force(c, p, true));
+                return stage_kick(c, p, 0.5 * dt);
+            });
+        });
+    c->capturing = false;
+    c->dev_build = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+    c->stream = s0;
+    c->rgraph_launches = c->n_launches - l0;
+    c->n_launches = l0;
+    c->n_nodes = keep.n_nodes;
+    c->n_groups = keep.n_groups;
+    c->lvl_start = keep.lvl_start;
+    if (rc != BH_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->key_cur = keep.key_cur;  // nothing ran: the sorted keys are where they were
+        if (rc != BH_OK) return rc;
+        return fail(c, BH_E_CUDA, "stream capture of the list-constructing step failed: %s", cudaGetErrorString(ec));
+    }
+    if (c->rgraph_exec) {
+        cudaGraphExecDestroy(c->rgraph_exec);
+        c->rgraph_exec = nullptr;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->rgraph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->rgraph_exec = nullptr;
+        cudaGetLastError();
+        return fail(c, BH_E_CUDA, "cudaGraphInstantiate of the list-constructing step failed: %s",
+                    cudaGetErrorString(ei));
+    }
+    ++c->n_graph_captures;
+    for (int k = 0; k < 5; ++k) c->rgraph_cap[k] = cap[k];
+    c->rgraph_walk_cap[0] = c->walk_cap_p;
+    c->rgraph_walk_cap[1] = c->walk_cap_c;
+    c->rgraph_ok = true;
+    c->rgraph_p = *p;
+    return BH_OK;
+}
+
+// The captured step still leaves the last build at least half its room (and
+// slot sizes within a tenth), on the same arrays.
+bool rebuild_graph_fits(const Ctx* c, const bh_particles* p) {
+    if (!c->rgraph_ok || !c->rgraph_exec || !same_arrays(c->rgraph_p, *p)) return false;
+    const int64_t now[5] = {c->n_nodes, c->n_groups, c->n_pp, c->n_pc, c->n_jj};
+    for (int k = 0; k < 5; ++k)
+        if (now[k] + now[k] * c->tune.graph_room / 200 > c->rgraph_cap[k]) return false;
+    return c->walk_cap_p <= c->rgraph_walk_cap[0] + c->rgraph_walk_cap[0] / 10 &&
+           c->walk_cap_c <= c->rgraph_walk_cap[1] + c->rgraph_walk_cap[1] / 10;
+}
+
+}  // namespace
+
+int graph_rebuild_step(Ctx* c, bh_particles* p) {
+    if (!rebuild_graph_fits(c, p)) BH_TRY(capture_rebuild(c, p));
+    BH_CUDA(c, cudaGraphLaunch(c->rgraph_exec, c->stream));
+    c->n_launches += c->rgraph_launches;
+    unsigned long long sz[kSzWords], sm[24];
+    BH_CUDA(c, cudaMemcpyAsync(sz, c->d_sz, sizeof(sz), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaMemcpyAsync(sm, c->d_small, sizeof(sm), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    BH_TRY(read_status(c));
+    ++c->n_graph_builds;
+    if (sz[kSzOvf] != 0) {
+        // a capacity ran out: the step stopped after the kick-drift and the
+        // reordering; grow at the next capture and finish it eagerly
+        ++c->n_graph_build_redos;
+        c->rgraph_ok = false;  // captured again from the eager build's sizes
+        c->have_tree = c->have_lists = false;
+        BH_TRY(evaluate(c, p));
+        return stage_kick(c, p, 0.5 * c->prm.dt);
+    }
+    // the sizes of the build, as an eager build leaves them
+    c->n_nodes = (int64_t)sz[kSzLvl + kLevels + 2];
+    c->lvl_start.assign(1, 0);
+    for (int l = 0; l <= kLevels && sz[kSzLvl + l + 1] > sz[kSzLvl + l]; ++l)
+        c->lvl_start.push_back((int64_t)sz[kSzLvl + l + 1]);
+    c->n_groups = (int64_t)sz[kSzNg];
+    c->n_pp = (int64_t)sm[0];
+    c->n_pc = (int64_t)sm[1];
+    c->n_jj = (int64_t)sm[2];
+    c->n_int_pp = (int64_t)sm[8];
+    c->n_int_pc = (int64_t)sm[9];
+    c->n_int_pp_far = c->prm.precision == BH_PREC_FP32 ? (int64_t)sm[10] : 0;
+    if (sm[11] == 0) ++c->n_one_walk_builds;
+    c->walk_cap_p = (int64_t)(((sm[12] + sm[12] / 4 + 4) + 3) & ~3ull);
+    c->walk_cap_c = (int64_t)(((sm[13] + sm[13] / 4 + 4) + 3) & ~3ull);
+    if (c->prm.precision == BH_PREC_FP32 && c->prm.r_coll > 0.0) c->n_contacts = (int64_t)sm[16];
+    c->have_tree = c->have_lists = true;
+    c->list_overflowed = false;
+    c->graph_ok = false;  // the list-reusing graph follows the new lists
+    c->n_rebuilds++;
+    c->evals_since_build = 1;
+    c->k_eval++;
+    c->refine_pending = c->prm.precision == BH_PREC_FP32;
+    return BH_OK;
+}
+
 int check_tuning(Ctx* c, const bh_tuning* t) {
     if (!t) return fail(c, BH_E_INVAL, "tuning is NULL");
     if (t->n_g < c->prm.n_leaf) return fail(c, BH_E_INVAL, "n_g must be >= n_leaf");
     if (t->chunk != 32 && t->chunk != 64 && t->chunk != 96) return fail(c, BH_E_INVAL, "chunk must be 32, 64 or 96");
     if (t->warps < 1 || t->warps > 8) return fail(c, BH_E_INVAL, "warps must be 1..8");
     if (t->sched < BH_SCHED_GRID || t->sched > BH_SCHED_DYNAMIC) return fail(c, BH_E_INVAL, "unknown schedule");
-    if ((t->order_by_cost != 0 && t->order_by_cost != 1) || (t->graph != 0 && t->graph != 1))
-        return fail(c, BH_E_INVAL, "order_by_cost and graph must be 0 or 1");
+    if ((t->order_by_cost != 0 && t->order_by_cost != 1) || t->graph < 0 || t->graph > 2)
+        return fail(c, BH_E_INVAL, "order_by_cost must be 0 or 1, graph 0, 1 or 2");
     if (t->order_window < 0) return fail(c, BH_E_INVAL, "order_window must be >= 0");
     if (t->graph_contact_room < 0) return fail(c, BH_E_INVAL, "graph_contact_room must be >= 0");
+    if (t->graph_room < 0 || t->graph_room > 1000) return fail(c, BH_E_INVAL, "graph_room must be 0..1000");
     return BH_OK;
 }
 
@@ -375,7 +624,9 @@ void apply_tuning(Ctx* c, const bh_tuning* t) {
     c->tune.graph = t->graph;
     c->tune.order_window = t->order_window;
     c->tune.graph_contact_room = t->graph_contact_room;
+    c->tune.graph_room = t->graph_room;
     c->graph_ok = false;
+    c->rgraph_ok = false;
     (void)relist;
 }
 
@@ -388,6 +639,7 @@ void read_tuning(const Ctx* c, bh_tuning* t) {
     t->graph = c->tune.graph;
     t->order_window = c->tune.order_window;
     t->graph_contact_room = c->tune.graph_contact_room;
+    t->graph_room = c->tune.graph_room;
 }
 
 // Elapsed device time of fn() on the context's stream (ms).
@@ -586,6 +838,8 @@ static int create_ctx(const char* who, const bh_params* p, int n_patches, const 
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_box, 8 * sizeof(double) * (size_t)n_patches);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_small, 64 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_sz, bh::kSzWords * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_sz, 0, bh::kSzWords * sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -622,12 +876,16 @@ int bh_destroy(bh_ctx* ctx) {
     if (!c) return BH_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->rgraph_exec) cudaGraphExecDestroy(c->rgraph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaStream_t q : c->body_stream)
+        if (q) cudaStreamDestroy(q);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pos_event) cudaEventDestroy(c->pos_event);
     cudaFree(c->d_status);
     cudaFree(c->d_box);
     cudaFree(c->d_small);
+    cudaFree(c->d_sz);
     using bh::release;
     release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag); release(c->pot);
     for (int b = 0; b < 2; ++b) {
@@ -708,6 +966,11 @@ int bh_step(bh_ctx* ctx, bh_particles* p, int nsteps) {
         c->early_now = s == nsteps - 1;  // only the last step's evaluation counts
         if (c->tune.graph && c->have_lists && c->k_eval % c->prm.rebuild_every != 0) {
             BH_TRY(bh::graph_reuse_step(c, p));
+            continue;
+        }
+        // a list capacity needs the eager build's exact sizes
+        if (c->tune.graph == 1 && c->have_lists && c->prm.list_capacity == 0) {
+            BH_TRY(bh::graph_rebuild_step(c, p));
             continue;
         }
         BH_TRY(bh::stage_kick_drift(c, p, 0.5 * dt, dt));
@@ -903,12 +1166,15 @@ int bh_get_root(bh_ctx* ctx, double* lo3, double* L) {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BH_E_INVAL;
     if (!c->have_tree) return bh::fail(c, BH_E_STATE, "no tree");
+    std::vector<double> box(8 * (size_t)c->n_patches);
+    BH_CUDA(c, cudaMemcpyAsync(box.data(), c->d_box, box.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int q = 0; q < c->n_patches; ++q) {
         if (lo3)
-            for (int a = 0; a < 3; ++a) lo3[3 * q + a] = c->h_box[8 * q + a];
-        if (L) L[q] = c->h_box[8 * q + 3];
+            for (int a = 0; a < 3; ++a) lo3[3 * q + a] = box[8 * q + a];
+        if (L) L[q] = box[8 * q + 3];
     }
-    return BH_OK;
+    return bh::read_status(c);
 }
 
 int bh_get_tree(bh_ctx* ctx, uint8_t* level, uint32_t* begin, uint32_t* end, int32_t* parent,
@@ -1008,6 +1274,9 @@ int bh_get_counters(bh_ctx* ctx, bh_counters* out) {
         c->refine_pending = false;
     }
     out->n_refined = c->n_refined;
+    out->n_graph_builds = c->n_graph_builds;
+    out->n_graph_build_redos = c->n_graph_build_redos;
+    out->n_graph_captures = c->n_graph_captures;
     BH_TRY(bh::read_stage_events(c, false));
     for (int s = 0; s < BH_N_STAGES; ++s) {
         out->stage_ms[s] = c->stage_ms[s];

@@ -22,6 +22,16 @@ constexpr int kStatListOverflow = 2;
 constexpr int kStatTimeout = 4;
 constexpr int kStatBounds = 8;  // an internal index check failed (access skipped)
 constexpr int kStatRange = 16;  // a contact term outside the fixed-point accumulator's range
+constexpr int kStatAxis = 32;   // cylindrical key frame with a particle on the axis (r = 0)
+
+// Sizes of a device-sized list build (a list-constructing step captured as
+// one graph: nothing is read back while it runs), in Ctx::d_sz.
+constexpr int kSzLvl = 0;                   // kLevels + 3 words: first node of each level, then the node count
+constexpr int kSzNg = kLevels + 3;          // group count
+constexpr int kSzOvf = kSzNg + 1;           // overflow bits
+constexpr int kSzNeedNodes = kSzOvf + 1;    // nodes wanted when the node capacity ran out (a lower bound)
+constexpr int kSzWords = 32;
+constexpr unsigned long long kOvfNodes = 1, kOvfLists = 2;
 
 // Device buffer that only grows.
 template <typename T>
@@ -58,6 +68,7 @@ struct Tuning {
     int graph = 0;           // capture list-reusing steps of bh_step in a CUDA graph
     int order_window = 0;    // > 0: size-class order within windows of this many groups
     int graph_contact_room = 0;  // > 0: contact candidates a graph step may hold (0: automatic)
+    int graph_room = 25;         // percent of room over the last build in a list-constructing graph step
 };
 
 struct Ctx {
@@ -107,7 +118,6 @@ struct Ctx {
     // status and small device scalars
     int* d_status = nullptr;
     double* d_box = nullptr;   // per patch: lo[3], L, S, spare x3 (8 doubles)
-    std::vector<double> h_box; // host copy of d_box
     unsigned long long* d_small = nullptr;  // scan totals etc. (64 words)
 
     // keys and sort
@@ -186,6 +196,23 @@ struct Ctx {
     bh_particles graph_p{};              // particle arrays the graph was captured with
     int64_t graph_launches = 0;          // kernels in the graph
 
+    // device-sized list builds: a list-constructing step of bh_step issued as
+    // one graph (graph tuning on), its buffers sized from the previous build
+    unsigned long long* d_sz = nullptr;  // kSzWords device words (level bounds, group count, overflow)
+    bool dev_build = false;              // issuing a device-sized build (no size read-backs)
+    int64_t cap_nodes = 0;               // node capacity of the build being issued
+    int64_t dev_slots = 0;               // groups with a list slot in it
+    cudaGraphExec_t rgraph_exec = nullptr;  // the captured list-constructing step
+    bool rgraph_ok = false;              // rgraph_exec matches the arrays and capacities
+    bh_particles rgraph_p{};
+    int64_t rgraph_launches = 0;
+    int64_t rgraph_cap[5] = {};          // nodes, slots, P, C, JJ it was captured with
+    int64_t rgraph_walk_cap[2] = {};     // and list slot sizes
+    cudaStream_t body_stream[2] = {nullptr, nullptr};  // its conditional bodies are captured on these
+    int64_t n_graph_builds = 0;          // list builds that ran inside a graph
+    int64_t n_graph_build_redos = 0;     // of those, builds redone eagerly after a capacity ran out
+    int64_t n_graph_captures = 0;        // step graphs captured
+
     // lists
     int64_t n_pp = 0, n_pc = 0, n_jj = 0;
     int64_t n_int_pp = 0, n_int_pc = 0;
@@ -233,8 +260,11 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 // ---- stage entry points (one translation unit each) ------------------------
 // scan.cu: exclusive prefix sums; *total written to d_total (device) if given.
-int scan_u32(Ctx* c, const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* d_total);
-int scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, unsigned long long* d_total);
+// With dn, the element count is read on the device (*dn, at most n).
+int scan_u32(Ctx* c, const uint32_t* in, uint32_t* out, int64_t n, unsigned long long* d_total,
+             const unsigned long long* dn = nullptr);
+int scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, unsigned long long* d_total,
+             const unsigned long long* dn = nullptr);
 int64_t scan_sums_count(int64_t n);
 cudaError_t scan_u32_with(cudaStream_t s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums);
 
@@ -252,6 +282,7 @@ cudaError_t sort_pairs_with(cudaStream_t s, uint64_t* keys, uint32_t* idx, uint6
 
 // tree.cu
 int stage_octree(Ctx* c);                          // level-by-level split; sets n_nodes
+int stage_octree_dev(Ctx* c);                      // the same, device-sized (c->dev_build)
 int stage_boxes(Ctx* c);                           // integer boxes + walk records
 int stage_moments(Ctx* c, const bh_particles* p);  // M, c, Q (+ FP32 cell records)
 int stage_moments64(Ctx* c, const bh_particles* p);  // FP64 M, c, Q whatever the precision
@@ -259,6 +290,8 @@ int stage_groups(Ctx* c);                          // groups ordered by begin
 
 // walk.cu
 int stage_lists(Ctx* c);                           // walk (count, fill) + particle expansion
+int stage_lists_dev_walk(Ctx* c);                  // device-sized: walk, offsets, room check
+int stage_lists_dev_fill(Ctx* c);                  // device-sized: lists, expansion, group order
 
 // force.cu
 int stage_split(Ctx* c, const bh_particles* p);    // FP32 hi/lo split of particles

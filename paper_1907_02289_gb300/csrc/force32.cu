@@ -135,6 +135,7 @@ struct Smem32 {
 
 struct Args {
     int64_t ng;
+    const unsigned long long* dng;  // device group count (device-sized list builds; NULL: ng)
     const int32_t* order;  // processing order of the groups (NULL: list order)
     const int32_t* groups;
     const uint32_t* begin;
@@ -814,17 +815,18 @@ __global__ void __launch_bounds__(32 * BH_F32_MAXW, 2) k_force32(const Args A) {
     const int64_t wid = (int64_t)blockIdx.x * nw + w;
     Smem32& S = sm[w];
     const unsigned long long t0 = A.warp_time ? global_ns() : 0ull;
+    const int64_t ng = A.dng ? min(A.ng, (int64_t)*A.dng) : A.ng;
     if (A.ticket) {  // persistent, dynamic: the next list slot from the shared counter
         for (;;) {
             unsigned long long s = 0;
             if (lane == 0) s = atomicAdd(A.ticket, 1ull);
             s = __shfl_sync(0xffffffffu, s, 0);
-            if ((int64_t)s >= A.ng) break;
+            if ((int64_t)s >= ng) break;
             force_group<ORDER, MODE>(A, S, (int64_t)s, lane);
         }
     } else {  // static: one slot per warp (grid) or every stride-th slot (persistent)
         const int64_t stride = (int64_t)gridDim.x * nw;
-        for (int64_t s = wid; s < A.ng; s += stride) force_group<ORDER, MODE>(A, S, s, lane);
+        for (int64_t s = wid; s < ng; s += stride) force_group<ORDER, MODE>(A, S, s, lane);
     }
     if (A.warp_time && lane == 0) {
         A.warp_time[2 * wid] = t0;
@@ -871,13 +873,14 @@ __device__ __forceinline__ int order_bucket(int64_t k, const int32_t* __restrict
     return size_class(ni, chunk) * kCostBuckets + cb;
 }
 
-__global__ void k_order_hist(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+__global__ void k_order_hist(int64_t ng, const unsigned long long* __restrict__ dng,
+                             const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
                              const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
                              const int64_t* __restrict__ pc_off, uint32_t chunk, bool by_cost,
                              unsigned long long* cnt) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ng) return;
-    atomicAdd(&cnt[order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost)], 1ull);
+    if (dng) ng = min(ng, (int64_t)*dng);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost)], 1ull);
 }
 
 // Windowed order: key = (group index / window, bucket); a stable sort of the
@@ -910,15 +913,17 @@ __global__ void k_order_prefix(unsigned long long* cnt) {
     cnt[threadIdx.x] = v[threadIdx.x];
 }
 
-__global__ void k_order_scatter(int64_t ng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+__global__ void k_order_scatter(int64_t ng, const unsigned long long* __restrict__ dng,
+                                const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
                                 const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off,
                                 const int64_t* __restrict__ pc_off, uint32_t chunk, bool by_cost,
                                 const unsigned long long* __restrict__ start, unsigned long long* cursor,
                                 int32_t* __restrict__ order) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ng) return;
-    const int b = order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost);
-    order[start[b] + atomicAdd(&cursor[b], 1ull)] = (int32_t)k;
+    if (dng) ng = min(ng, (int64_t)*dng);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += (int64_t)gridDim.x * blockDim.x) {
+        const int b = order_bucket(k, groups, begin, end, jj_off, pc_off, chunk, by_cost);
+        order[start[b] + atomicAdd(&cursor[b], 1ull)] = (int32_t)k;
+    }
 }
 
 // FP64 pass over the contact candidates: Eq. (1) in the oracle's operation
@@ -1259,7 +1264,7 @@ int build_order32(Ctx* c) {
     unsigned long long* cnt = c->order_cnt.p;
     const uint32_t chunk = (uint32_t)std::min(c->tune.chunk, 32 * BH_F32_MAXR);
     const bool by_cost = c->tune.order_by_cost != 0;
-    if (c->tune.order_window > 0 && ng > c->tune.order_window) {
+    if (c->tune.order_window > 0 && ng > c->tune.order_window && !c->dev_build) {  // (device-sized: plain order)
         for (int b = 0; b < 2; ++b) {
             BH_TRY(grow(c, c->ord_key[b], (size_t)ng, "group order keys"));
             BH_TRY(grow(c, c->ord_idx[b], (size_t)ng, "group order indices"));
@@ -1280,15 +1285,17 @@ int build_order32(Ctx* c) {
                                    c->stream));
         return BH_OK;
     }
+    // device-sized build: the group count is read on the device
+    const unsigned long long* dng = c->dev_build ? c->d_sz + kSzNg : nullptr;
+    const unsigned nb = dng ? (unsigned)(4 * c->num_sms) : blocks_for(ng, 256);
     BH_CUDA(c, cudaMemsetAsync(cnt, 0, 2 * kOrderBuckets * sizeof(unsigned long long), c->stream));
-    k_order_hist<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
-                                                             c->cnt_c.p, chunk, by_cost, cnt);
+    k_order_hist<<<nb, 256, 0, c->stream>>>(ng, dng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p, c->cnt_c.p, chunk,
+                                            by_cost, cnt);
     BH_LAUNCH(c);
     k_order_prefix<<<1, kOrderBuckets, 0, c->stream>>>(cnt);
     BH_LAUNCH(c);
-    k_order_scatter<<<blocks_for(ng, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p,
-                                                                c->cnt_c.p, chunk, by_cost, cnt,
-                                                                cnt + kOrderBuckets, c->order.p);
+    k_order_scatter<<<nb, 256, 0, c->stream>>>(ng, dng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p, c->cnt_c.p,
+                                               chunk, by_cost, cnt, cnt + kOrderBuckets, c->order.p);
     BH_LAUNCH(c);
     return BH_OK;
 }
@@ -1340,6 +1347,7 @@ int contact_pass(Ctx* c, const Args& A, const ForceParams& fp, bh_particles* p, 
 int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_central) {
     Args A;
     A.ng = c->n_groups;
+    A.dng = c->dev_build ? c->d_sz + kSzNg : nullptr;
     A.order = c->order.p;
     A.groups = c->groups.p;
     A.begin = c->begin.p;
@@ -1417,9 +1425,9 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
         }
     }
     unsigned nb;
-    if (c->tune.sched == BH_SCHED_GRID) {
+    if (c->tune.sched == BH_SCHED_GRID && !A.dng) {
         nb = blocks_for(A.ng, W);
-    } else {
+    } else {  // (a device-sized build runs the grid schedule as a persistent static one)
         nb = (unsigned)(c->num_sms * resident_blocks(kern, W));
         const int64_t need = (A.ng + W - 1) / W;
         if ((int64_t)nb > need) nb = (unsigned)(need > 0 ? need : 1);

@@ -62,8 +62,9 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
 }
 
 // box of patch q = blockIdx.x from its nb partials: {lo_x, lo_y, lo_z, L, S}
-// at box + 8 q
-__global__ void k_box_final(const double* __restrict__ part_all, int nb, double* box_all) {
+// at box + 8 q.  Cylindrical frame (cyl): every particle must be off the axis
+// (r > 0), else kStatAxis.
+__global__ void k_box_final(const double* __restrict__ part_all, int nb, double* box_all, int cyl, int* status) {
     const double* part = part_all + 6 * (int64_t)blockIdx.x * nb;
     double* box = box_all + 8 * blockIdx.x;
     __shared__ double r[6];
@@ -84,6 +85,7 @@ __global__ void k_box_final(const double* __restrict__ part_all, int nb, double*
         double L = ext > 0.0 ? ext : 1.0;
         box[3] = L;
         box[4] = __ddiv_rn(2097152.0, L);
+        if (cyl && !(r[1] > 0.0)) atomicOr(status, kStatAxis);
     }
 }
 
@@ -375,7 +377,7 @@ int stage_keys(Ctx* c, const bh_particles* p) {
     BH_TRY(grow(c, c->box_part, 6 * (size_t)nb * np, "box partials"));
     k_box_partial<<<dim3(nb, np), kBoxThreads, 0, c->stream>>>(cx, cy, p->z, c->d_off.p, c->box_part.p, c->d_status);
     BH_LAUNCH(c);
-    k_box_final<<<np, 32, 0, c->stream>>>(c->box_part.p, nb, c->d_box);
+    k_box_final<<<np, 32, 0, c->stream>>>(c->box_part.p, nb, c->d_box, c->prm.key_frame == 1, c->d_status);
     BH_LAUNCH(c);
     k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(cx, cy, p->z, n, c->d_off.p, np, c->d_box, c->key[0].p,
                                                       c->idx[0].p);
@@ -391,11 +393,16 @@ int stage_sort(Ctx* c) {
     BH_TRY(grow(c, c->digit_hist, 8 * kRadix, "digit histogram"));
     BH_TRY(grow(c, c->sort_hist, (size_t)kRadix * ntiles, "sort histogram"));
     BH_CUDA(c, cudaMemsetAsync(c->digit_hist.p, 0, 8 * kRadix * sizeof(uint32_t), c->stream));
-    k_digit_hist<<<c->num_sms * 2, 256, 0, c->stream>>>(c->key[c->key_cur].p, n, c->digit_hist.p);
-    BH_LAUNCH(c);
-    uint32_t h[8 * kRadix];
-    BH_CUDA(c, cudaMemcpyAsync(h, c->digit_hist.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    // passes whose digit is the same for every key leave the order as it is
+    // and are skipped (a device-sized build runs all eight: nothing is read
+    // back; the sort is stable, so the result is the same)
+    uint32_t h[8 * kRadix] = {};
+    if (!c->dev_build) {
+        k_digit_hist<<<c->num_sms * 2, 256, 0, c->stream>>>(c->key[c->key_cur].p, n, c->digit_hist.p);
+        BH_LAUNCH(c);
+        BH_CUDA(c, cudaMemcpyAsync(h, c->digit_hist.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     const int smem = (int)sizeof(DownSmem);
     if (c->sort_attr_device != c->device) {  // once per device
         BH_CUDA(c, cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -26,6 +26,7 @@
 // single FP32 coordinates relative to the group origin (the arithmetic of
 // Sec. 4.7), whose error relative to the separation is then bounded by a
 // few FP32 roundings, and skips the contact test for them.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -113,7 +114,8 @@ struct ListOut {
 constexpr int kWalkCount = 0, kWalkFill = 1, kWalkStash = 2;
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restrict__ groups,
+__global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long long* __restrict__ dng,
+                                              int64_t slots, const int32_t* __restrict__ groups,
                                               const WalkNode* __restrict__ wn,
                                               const int32_t* __restrict__ skip,
                                               const uint32_t* __restrict__ begin,
@@ -124,88 +126,96 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
                                               int64_t nn, int* status, int64_t capP, int64_t capC,
                                               unsigned long long* longest, unsigned long long* overflow) {
     constexpr bool WRITE = MODE != kWalkCount, COUNT = MODE != kWalkFill;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = k < ng;
-    int64_t np = 0, nc = 0, nj = 0, ni = 0, nown = 0;
-    if (active) {
-        const int32_t g = groups[k];
-        const WalkNode G = wn[g];
-        const uint32_t gb = begin[g], ge = end[g];
-        const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
-        const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
-        ni = (int64_t)(end[g] - begin[g]);
-        ListOut po{P, 0, 0, INT64_MAX, 0, 0, 0, 0}, co{C, 0, 0, INT64_MAX, 0, 0, 0, 0};
-        if (MODE == kWalkFill) {
-            po.base = po.pos = np_io[k];
-            co.base = co.pos = nc_io[k];
-        } else if (MODE == kWalkStash) {
-            po.dst = P + k * capP;
-            po.cap = capP;
-            co.dst = C + k * capC;
-            co.cap = capC;
-        }
-        const int root = patch_of(wp, gb);
-        const long long rcq = wp.rcq[root];
-        const int period = (int)wp.period[root];
-        int node = root;
-        for (int64_t visits = 0;; ++visits) {
-            const WalkNode R = wn[node];
-            const int after = skip[node];
-            const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
-            const long long d2 = box_gap2(R, glo, ghi, period);
-            const bool open = d2 < wp.D[lev] || d2 <= rcq;
-            int next = after;
-            if (open) {
-                if (nch == 0) {
-                    if (WRITE) po.put(node);
-                    ++np;
-                    const uint32_t lb = begin[node];
-                    if (lb >= gb && lb < ge)
-                        nown += (int64_t)(end[node] - lb);  // the group's own particles
-                    else
-                        nj += (int64_t)(end[node] - lb);
+    if (dng) ng = min(ng, (int64_t)*dng);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ng; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        bool active = k < ng;
+        if (MODE == kWalkFill && active && slots >= 0)  // only the groups that did not fit their slot
+            active = !(k < slots && np_io[k + 1] - np_io[k] <= capP && nc_io[k + 1] - nc_io[k] <= capC);
+        int64_t np = 0, nc = 0, nj = 0, ni = 0, nown = 0;
+        if (active) {
+            const int32_t g = groups[k];
+            const WalkNode G = wn[g];
+            const uint32_t gb = begin[g], ge = end[g];
+            const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
+            const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
+            ni = (int64_t)(end[g] - begin[g]);
+            ListOut po{P, 0, 0, INT64_MAX, 0, 0, 0, 0}, co{C, 0, 0, INT64_MAX, 0, 0, 0, 0};
+            if (MODE == kWalkFill) {
+                po.base = po.pos = np_io[k];
+                co.base = co.pos = nc_io[k];
+            } else if (MODE == kWalkStash && (slots < 0 || k < slots)) {
+                po.dst = P + k * capP;
+                po.cap = capP;
+                co.dst = C + k * capC;
+                co.cap = capC;
+            } else if (MODE == kWalkStash) {  // no slot: counted only, filled later
+                po.cap = 0;
+                co.cap = 0;
+            }
+            const int root = patch_of(wp, gb);
+            const long long rcq = wp.rcq[root];
+            const int period = (int)wp.period[root];
+            int node = root;
+            for (int64_t visits = 0;; ++visits) {
+                const WalkNode R = wn[node];
+                const int after = skip[node];
+                const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
+                const long long d2 = box_gap2(R, glo, ghi, period);
+                const bool open = d2 < wp.D[lev] || d2 <= rcq;
+                int next = after;
+                if (open) {
+                    if (nch == 0) {
+                        if (WRITE) po.put(node);
+                        ++np;
+                        const uint32_t lb = begin[node];
+                        if (lb >= gb && lb < ge)
+                            nown += (int64_t)(end[node] - lb);  // the group's own particles
+                        else
+                            nj += (int64_t)(end[node] - lb);
+                    } else {
+                        next = (int)R.b.w;
+                    }
                 } else {
-                    next = (int)R.b.w;
+                    if (WRITE) co.put(node);
+                    ++nc;
                 }
-            } else {
-                if (WRITE) co.put(node);
-                ++nc;
+                if (next < 0) break;
+                if (next >= nn || visits >= nn) {  // never taken for a valid tree
+                    atomicOr(status, kStatBounds);
+                    break;
+                }
+                node = next;
             }
-            if (next < 0) break;
-            if (next >= nn || visits >= nn) {  // never taken for a valid tree
-                atomicOr(status, kStatBounds);
-                break;
+            if (WRITE) {
+                po.flush();
+                co.flush();
             }
-            node = next;
+            if (MODE == kWalkStash && (np > po.cap || nc > co.cap)) atomicOr(overflow, 1ull);
+            if (COUNT) {
+                np_io[k] = np;
+                nc_io[k] = nc;
+                nj_io[k] = nj;
+            }
         }
-        if (WRITE) {
-            po.flush();
-            co.flush();
-        }
-        if (MODE == kWalkStash && (np > capP || nc > capC)) atomicOr(overflow, 1ull);
         if (COUNT) {
-            np_io[k] = np;
-            nc_io[k] = nc;
-            nj_io[k] = nj;
-        }
-    }
-    if (COUNT) {
-        // interaction counts: n_i * (list particles) and n_i * (list cells);
-        // longest particle and cell lists
-        unsigned long long ipp = (unsigned long long)(ni * (nj + nown)), ipc = (unsigned long long)(ni * nc);
-        unsigned long long lp = (unsigned long long)np, lc = (unsigned long long)nc;
+            // interaction counts: n_i * (list particles) and n_i * (list cells);
+            // longest particle and cell lists
+            unsigned long long ipp = (unsigned long long)(ni * (nj + nown)), ipc = (unsigned long long)(ni * nc);
+            unsigned long long lp = (unsigned long long)np, lc = (unsigned long long)nc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
-            ipc += __shfl_xor_sync(0xffffffffu, ipc, o);
-            lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o));
-            lc = max(lc, __shfl_xor_sync(0xffffffffu, lc, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&inter[0], ipp);
-            atomicAdd(&inter[1], ipc);
-            atomicMax(&longest[0], lp);
-            atomicMax(&longest[1], lc);
+            for (int o = 16; o > 0; o >>= 1) {
+                ipp += __shfl_xor_sync(0xffffffffu, ipp, o);
+                ipc += __shfl_xor_sync(0xffffffffu, ipc, o);
+                lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o));
+                lc = max(lc, __shfl_xor_sync(0xffffffffu, lc, o));
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&inter[0], ipp);
+                atomicAdd(&inter[1], ipc);
+                atomicMax(&longest[0], lp);
+                atomicMax(&longest[1], lc);
+            }
         }
     }
 }
@@ -216,104 +226,151 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const int32_t* __restr
 // (each run in list order); jm[k] = index of the first far particle, and
 // the far interactions n_i x (far particles) are summed into *n_far.
 template <bool SPLIT>
-__global__ void k_expand(int64_t ng, const int32_t* __restrict__ groups, const int64_t* __restrict__ pp_off,
-                         const int32_t* __restrict__ P, const uint32_t* __restrict__ begin,
+__global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng, const int32_t* __restrict__ groups,
+                         const int64_t* __restrict__ pp_off, const int32_t* __restrict__ P, const uint32_t* __restrict__ begin,
                          const uint32_t* __restrict__ end, const WalkNode* __restrict__ wn, WalkParams wp,
                          const int64_t* __restrict__ jj_off, uint32_t* __restrict__ JJ, int64_t* __restrict__ jm,
                          unsigned long long* n_far) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (dng) ng = min(ng, (int64_t)*dng);
     const int lane = threadIdx.x & 31;
-    if (k >= ng) return;
-    const int32_t g = groups[k];
-    const uint32_t gb = begin[g], ge = end[g];
-    const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
-    int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
-    long long rfar = 0, ext2 = 0;
-    int period = 0;
-    if (SPLIT) {
-        const WalkNode G = wn[g];
-        glo[0] = (int)G.a.x; glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
-        ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
-        const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
-        ext2 = ext * ext;
-        const int root = patch_of(wp, gb);
-        rfar = wp.rfar[root];
-        period = (int)wp.period[root];
-    }
-    // leaf entry e -> (first particle, count); far? by the box test, or from
-    // the first pass's flags (bit c = the lane's entry of round c < 32)
-    auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt) {
-        b = 0;
-        cnt = 0;
-        if (e < e1) {
-            const int32_t leaf = P[e];
-            b = begin[leaf];
-            cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < ng; k += wstride) {
+        const int32_t g = groups[k];
+        const uint32_t gb = begin[g], ge = end[g];
+        const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
+        int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+        long long rfar = 0, ext2 = 0;
+        int period = 0;
+        if (SPLIT) {
+            const WalkNode G = wn[g];
+            glo[0] = (int)G.a.x; glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
+            ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
+            const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
+            ext2 = ext * ext;
+            const int root = patch_of(wp, gb);
+            rfar = wp.rfar[root];
+            period = (int)wp.period[root];
         }
-    };
-    auto far_of = [&](int64_t e) -> bool {
-        const long long d2 = box_gap2(wn[P[e]], glo, ghi, period);
-        return d2 > rfar && 16 * d2 >= ext2;
-    };
-    int64_t jn = jj_off[k], jf = jn;
-    uint32_t flags = 0;
-    if (SPLIT) {  // far run starts after every near particle
-        uint32_t near = 0;
-        int c = 0;
-        for (int64_t e = e0 + lane; e < e1; e += 32, ++c) {
-            uint32_t b, cnt;
-            entry(e, b, cnt);
-            const bool far = cnt > 0 && far_of(e);
-            if (far && c < 32) flags |= 1u << c;
-            near += far ? 0u : cnt;
-        }
+        // leaf entry e -> (first particle, count); far? by the box test, or from
+        // the first pass's flags (bit c = the lane's entry of round c < 32)
+        auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt) {
+            b = 0;
+            cnt = 0;
+            if (e < e1) {
+                const int32_t leaf = P[e];
+                b = begin[leaf];
+                cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
+            }
+        };
+        auto far_of = [&](int64_t e) -> bool {
+            const long long d2 = box_gap2(wn[P[e]], glo, ghi, period);
+            return d2 > rfar && 16 * d2 >= ext2;
+        };
+        int64_t jn = jj_off[k], jf = jn;
+        uint32_t flags = 0;
+        if (SPLIT) {  // far run starts after every near particle
+            uint32_t near = 0;
+            int c = 0;
+            for (int64_t e = e0 + lane; e < e1; e += 32, ++c) {
+                uint32_t b, cnt;
+                entry(e, b, cnt);
+                const bool far = cnt > 0 && far_of(e);
+                if (far && c < 32) flags |= 1u << c;
+                near += far ? 0u : cnt;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(0xffffffffu, near, o);
-        jf = jn + near;
-        if (lane == 0) {
-            jm[k] = jf;
-            const unsigned long long ni = ge - gb;
-            atomicAdd(n_far, ni * (unsigned long long)(jj_off[k + 1] - jf));
-        }
-    }
-    for (int64_t e = e0, c = 0; e < e1; e += 32, ++c) {
-        uint32_t b, cnt;
-        entry(e + lane, b, cnt);
-        const bool far = SPLIT && cnt > 0 && (c < 32 ? ((flags >> c) & 1u) != 0 : far_of(e + lane));
-        const uint32_t cn = far ? 0u : cnt, cf = far ? cnt : 0u;
-        uint32_t xn = cn, xf = cf;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t yn = __shfl_up_sync(0xffffffffu, xn, o);
-            const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
-            if (lane >= o) {
-                xn += yn;
-                xf += yf;
+            for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(0xffffffffu, near, o);
+            jf = jn + near;
+            if (lane == 0) {
+                jm[k] = jf;
+                const unsigned long long ni = ge - gb;
+                atomicAdd(n_far, ni * (unsigned long long)(jj_off[k + 1] - jf));
             }
         }
-        const uint32_t tn = __shfl_sync(0xffffffffu, xn, 31), tf = __shfl_sync(0xffffffffu, xf, 31);
-        const int64_t pos = far ? jf + (xf - cf) : jn + (xn - cn);
-        for (uint32_t t = 0; t < cnt; ++t) JJ[pos + t] = b + t;
-        jn += tn;
-        jf += tf;
+        for (int64_t e = e0, c = 0; e < e1; e += 32, ++c) {
+            uint32_t b, cnt;
+            entry(e + lane, b, cnt);
+            const bool far = SPLIT && cnt > 0 && (c < 32 ? ((flags >> c) & 1u) != 0 : far_of(e + lane));
+            const uint32_t cn = far ? 0u : cnt, cf = far ? cnt : 0u;
+            uint32_t xn = cn, xf = cf;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t yn = __shfl_up_sync(0xffffffffu, xn, o);
+                const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
+                if (lane >= o) {
+                    xn += yn;
+                    xf += yf;
+                }
+            }
+            const uint32_t tn = __shfl_sync(0xffffffffu, xn, 31), tf = __shfl_sync(0xffffffffu, xf, 31);
+            const int64_t pos = far ? jf + (xf - cf) : jn + (xn - cn);
+            for (uint32_t t = 0; t < cnt; ++t) JJ[pos + t] = b + t;
+            jn += tn;
+            jf += tf;
+        }
     }
 }
 
 // One warp per group: the group's stashed lists (slots of capP / capC
-// entries) to their places in the packed lists.
-__global__ void k_unstash(int64_t ng, const int64_t* __restrict__ pp_off, const int64_t* __restrict__ pc_off,
+// entries) to their places in the packed lists.  slots >= 0 (device-sized
+// build): only the groups below slots whose lists fit their slot.
+__global__ void k_unstash(int64_t ng, const unsigned long long* __restrict__ dng, int64_t slots,
+                          const int64_t* __restrict__ pp_off, const int64_t* __restrict__ pc_off,
                           const int32_t* __restrict__ sP, const int32_t* __restrict__ sC, int64_t capP,
                           int64_t capC, int32_t* __restrict__ P, int32_t* __restrict__ C) {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (dng) ng = min(ng, (int64_t)*dng);
     const int lane = threadIdx.x & 31;
-    if (k >= ng) return;
-    const int64_t p0 = pp_off[k], np = pp_off[k + 1] - p0, c0 = pc_off[k], nc = pc_off[k + 1] - c0;
-    for (int64_t t = lane; t < np; t += 32) P[p0 + t] = sP[k * capP + t];
-    for (int64_t t = lane; t < nc; t += 32) C[c0 + t] = sC[k * capC + t];
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < ng; k += wstride) {
+        const int64_t p0 = pp_off[k], np = pp_off[k + 1] - p0, c0 = pc_off[k], nc = pc_off[k + 1] - c0;
+        if (slots >= 0 && !(k < slots && np <= capP && nc <= capC)) continue;
+        for (int64_t t = lane; t < np; t += 32) P[p0 + t] = sP[k * capP + t];
+        for (int64_t t = lane; t < nc; t += 32) C[c0 + t] = sC[k * capC + t];
+    }
 }
 
-__global__ void k_set_last(int64_t* off, int64_t ng, const unsigned long long* total) {
-    off[ng] = (int64_t)*total;
+__global__ void k_set_last(int64_t* off, int64_t ng, const unsigned long long* dng, const unsigned long long* total) {
+    off[dng ? min(ng, (int64_t)*dng) : ng] = (int64_t)*total;
+}
+
+// Walk thresholds per patch from its key grid (S = 2^21 / L).  Contact
+// reach in grid units: Cartesian r_coll S; cylindrical (phi, r, z): two
+// particles within r_coll have |dr|, |dz| <= r_coll and a phi difference of
+// at most ~r_coll / r_min, so (r_coll / r_min + 2e-8) S bounds their grid
+// distance (2e-8 covers the angle's approximation error), and the phi axis
+// wraps after floor(2 pi S) cells.  rcq = floor(reach^2); the far threshold
+// of the split expansion widens the reach by 1e-5 of itself plus two cells,
+// so that no rounding of a coordinate into its cell can put a touching pair
+// into a far leaf.  Round-to-nearest operations throughout (no contraction).
+__global__ void k_walk_thresholds(const double* __restrict__ box, int np, double r_coll, int cyl,
+                                  long long* __restrict__ rcq, long long* __restrict__ rfar,
+                                  long long* __restrict__ period) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    const double S = __ddiv_rn(2097152.0, box[8 * q + 3]);
+    double a;
+    long long per = 0;
+    if (cyl) {
+        a = __ddiv_rn(r_coll, box[8 * q + 1]);
+        a = __dadd_rn(a, 2e-8);
+        a = __dmul_rn(a, S);
+        per = (long long)floor(__dmul_rn(6.283185307179586, S));
+    } else {
+        a = __dmul_rn(r_coll, S);
+    }
+    const double r2 = __dmul_rn(a, a);
+    rcq[q] = (r2 >= 9.0e18) ? (long long)9.0e18 : (long long)floor(r2);
+    const double w = r_coll > 0.0 ? __dadd_rn(__dmul_rn(a, 1.0 + 1e-5), 2.0) : 0.0;
+    const double w2 = __dmul_rn(w, w);
+    rfar[q] = (w2 >= 9.0e18) ? (long long)9.0e18 : (long long)floor(w2);
+    period[q] = per;
+}
+
+// Device-sized build: the list totals against the buffers' room.
+__global__ void k_list_room(const unsigned long long* __restrict__ tot, long long roomP, long long roomC,
+                            long long roomJ, unsigned long long* sz) {
+    if (threadIdx.x != 0) return;
+    if ((long long)tot[0] > roomP || (long long)tot[1] > roomC || (long long)tot[2] > roomJ) sz[kSzOvf] |= kOvfLists;
 }
 
 WalkParams walk_params(const Ctx* c) {
@@ -347,46 +404,45 @@ WalkParams walk_params(const Ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// Walk thresholds of every patch, on the device from the root boxes.
+int walk_thresholds(Ctx* c) {
+    const int np = c->n_patches;
+    BH_TRY(grow(c, c->d_rcq, (size_t)np, "walk contact thresholds"));
+    BH_TRY(grow(c, c->d_rfar, (size_t)np, "far thresholds"));
+    BH_TRY(grow(c, c->d_period, (size_t)np, "walk periods"));
+    k_walk_thresholds<<<blocks_for(np, 64), 64, 0, c->stream>>>(c->d_box, np, c->prm.r_coll, c->prm.key_frame == 1,
+                                                                c->d_rcq.p, c->d_rfar.p, c->d_period.p);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+
+// Particle entries -> particle indices (near run, then far run for the FP32
+// kernel) and the FP32 kernel's group order.
+int expand_lists(Ctx* c, const WalkParams& wp, const unsigned long long* dng, unsigned grid) {
+    const int64_t ng = c->n_groups;
+    const bool split = c->prm.precision == BH_PREC_FP32;
+    unsigned long long* n_far = c->d_small + 10;
+    if (split) {
+        BH_TRY(grow(c, c->cnt_jm, (size_t)ng + 1, "list split points"));
+        BH_CUDA(c, cudaMemsetAsync(n_far, 0, sizeof(unsigned long long), c->stream));
+    }
+    auto expand = split ? k_expand<true> : k_expand<false>;
+    expand<<<grid, 256, 0, c->stream>>>(ng, dng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p, c->end.p, c->wnode.p,
+                                        wp, c->cnt_j.p, c->JJ.p, split ? c->cnt_jm.p : nullptr, n_far);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+
+}  // namespace
+
 int stage_lists(Ctx* c) {
     const int64_t ng = c->n_groups;
     BH_TRY(grow(c, c->cnt_p, (size_t)ng + 1, "list offsets P"));
     BH_TRY(grow(c, c->cnt_c, (size_t)ng + 1, "list offsets C"));
     BH_TRY(grow(c, c->cnt_j, (size_t)ng + 1, "list offsets J"));
-    // contact thresholds on each patch's grid (S = 2^21 / L).  Cartesian:
-    // (r_coll S)^2.  Cylindrical (phi, r, z): two particles within r_coll have
-    // |dr|, |dz| <= r_coll and a phi difference of at most ~r_coll / r_min, so
-    // (r_coll / r_min + 2e-8) S bounds their grid distance (2e-8 covers the
-    // angle's approximation error); the phi axis wraps after floor(2 pi S) cells.
-    // The far threshold of the split expansion widens the contact reach by
-    // 1e-5 of itself plus two cells, so that no rounding of a coordinate into
-    // its cell can put a touching pair into a far leaf.
-    std::vector<long long> rcq(c->n_patches), rfar(c->n_patches), period(c->n_patches, 0);
-    for (int q = 0; q < c->n_patches; ++q) {
-        const double L = c->h_box[8 * q + 3];
-        const double S = 2097152.0 / L;
-        double a;
-        if (c->prm.key_frame == 1) {
-            a = c->prm.r_coll / c->h_box[8 * q + 1];
-            a = a + 2e-8;
-            a = a * S;
-            period[q] = (long long)std::floor(6.283185307179586 * S);
-        } else {
-            a = c->prm.r_coll * S;
-        }
-        const double r2 = a * a;
-        rcq[q] = (r2 >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(r2);
-        const double w = c->prm.r_coll > 0.0 ? a * (1.0 + 1e-5) + 2.0 : 0.0;
-        rfar[q] = (w * w >= 9.0e18) ? (long long)9.0e18 : (long long)std::floor(w * w);
-    }
-    BH_TRY(grow(c, c->d_rcq, rcq.size(), "walk contact thresholds"));
-    BH_TRY(grow(c, c->d_rfar, rfar.size(), "far thresholds"));
-    BH_TRY(grow(c, c->d_period, period.size(), "walk periods"));
-    BH_CUDA(c, cudaMemcpyAsync(c->d_rcq.p, rcq.data(), rcq.size() * sizeof(long long), cudaMemcpyHostToDevice,
-                               c->stream));
-    BH_CUDA(c, cudaMemcpyAsync(c->d_rfar.p, rfar.data(), rfar.size() * sizeof(long long), cudaMemcpyHostToDevice,
-                               c->stream));
-    BH_CUDA(c, cudaMemcpyAsync(c->d_period.p, period.data(), period.size() * sizeof(long long),
-                               cudaMemcpyHostToDevice, c->stream));
+    BH_TRY(walk_thresholds(c));
     const WalkParams wp = walk_params(c);
     unsigned long long* inter = c->d_small + 8;
     unsigned long long* overflow = c->d_small + 11;
@@ -406,17 +462,17 @@ int stage_lists(Ctx* c) {
     const unsigned nb = blocks_for(ng, 128);
     if (stash)
         k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(
-            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
-            c->stash_p.p, c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest, overflow);
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            c->cnt_j.p, c->stash_p.p, c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest, overflow);
     else
         k_walk<kWalkCount><<<nb, 128, 0, c->stream>>>(
-            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
-            nullptr, nullptr, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            c->cnt_j.p, nullptr, nullptr, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
     BH_LAUNCH(c);
     DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
     for (int a = 0; a < 3; ++a) {
         BH_TRY(scan_i64(c, arr[a]->p, arr[a]->p, ng, c->d_small + a));
-        k_set_last<<<1, 1, 0, c->stream>>>(arr[a]->p, ng, c->d_small + a);
+        k_set_last<<<1, 1, 0, c->stream>>>(arr[a]->p, ng, nullptr, c->d_small + a);
         BH_LAUNCH(c);
     }
     unsigned long long h[16];
@@ -442,37 +498,88 @@ int stage_lists(Ctx* c) {
     BH_TRY(grow(c, c->C, (size_t)c->n_pc + 1, "cell lists"));
     BH_TRY(grow(c, c->JJ, (size_t)c->n_jj + 1, "list particle indices"));
     if (stash && h[11] == 0) {
-        k_unstash<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->cnt_p.p, c->cnt_c.p, c->stash_p.p,
-                                                                   c->stash_c.p, capP, capC, c->P.p, c->C.p);
+        k_unstash<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, nullptr, -1, c->cnt_p.p, c->cnt_c.p,
+                                                                   c->stash_p.p, c->stash_c.p, capP, capC, c->P.p,
+                                                                   c->C.p);
         ++c->n_one_walk_builds;
     } else {
         k_walk<kWalkFill><<<nb, 128, 0, c->stream>>>(
-            ng, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p,
-            c->P.p, c->C.p, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            c->cnt_j.p, c->P.p, c->C.p, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
     }
     BH_LAUNCH(c);
     // slots of the next build: the longest lists of this one plus a quarter,
     // in whole 16-byte units
     c->walk_cap_p = (int64_t)(((h[12] + h[12] / 4 + 4) + 3) & ~3ull);
     c->walk_cap_c = (int64_t)(((h[13] + h[13] / 4 + 4) + 3) & ~3ull);
-    const bool split = c->prm.precision == BH_PREC_FP32;
-    unsigned long long* n_far = c->d_small + 10;
-    if (split) {
-        BH_TRY(grow(c, c->cnt_jm, (size_t)ng + 1, "list split points"));
-        BH_CUDA(c, cudaMemsetAsync(n_far, 0, sizeof(unsigned long long), c->stream));
-    }
-    auto expand = split ? k_expand<true> : k_expand<false>;
-    expand<<<blocks_for(ng * 32, 256), 256, 0, c->stream>>>(ng, c->groups.p, c->cnt_p.p, c->P.p, c->begin.p,
-                                                           c->end.p, c->wnode.p, wp, c->cnt_j.p, c->JJ.p,
-                                                           split ? c->cnt_jm.p : nullptr, n_far);
-    BH_LAUNCH(c);
+    BH_TRY(expand_lists(c, wp, nullptr, blocks_for(ng * 32, 256)));
     c->n_int_pp_far = 0;
-    if (split) {
+    if (c->prm.precision == BH_PREC_FP32) {
         unsigned long long hf = 0;
-        BH_CUDA(c, cudaMemcpyAsync(&hf, n_far, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
+        BH_CUDA(c, cudaMemcpyAsync(&hf, c->d_small + 10, sizeof(hf), cudaMemcpyDeviceToHost, c->stream));
         BH_CUDA(c, cudaStreamSynchronize(c->stream));
         c->n_int_pp_far = (int64_t)hf;
+        BH_TRY(build_order32(c));
     }
+    return BH_OK;
+}
+
+// Device-sized list build, first part: the walk of every group (counting,
+// and writing each group's lists into its slot when it has one that fits:
+// c->dev_slots slots of walk_cap_p / walk_cap_c entries), the list offsets,
+// and the room check of the totals against the P, C and JJ buffers as they
+// are (kOvfLists).  Group count on the device; c->n_groups is its bound.
+int stage_lists_dev_walk(Ctx* c) {
+    const int64_t ng = c->n_groups;
+    const unsigned long long* dng = c->d_sz + kSzNg;
+    BH_TRY(grow(c, c->cnt_p, (size_t)ng + 1, "list offsets P"));
+    BH_TRY(grow(c, c->cnt_c, (size_t)ng + 1, "list offsets C"));
+    BH_TRY(grow(c, c->cnt_j, (size_t)ng + 1, "list offsets J"));
+    BH_TRY(walk_thresholds(c));
+    const WalkParams wp = walk_params(c);
+    unsigned long long* inter = c->d_small + 8;
+    unsigned long long* overflow = c->d_small + 11;
+    unsigned long long* longest = c->d_small + 12;
+    const int64_t slots = c->dev_slots, capP = c->walk_cap_p, capC = c->walk_cap_c;
+    BH_TRY(grow(c, c->stash_p, (size_t)std::max<int64_t>(1, slots * capP), "stashed particle lists"));
+    BH_TRY(grow(c, c->stash_c, (size_t)std::max<int64_t>(1, slots * capC), "stashed cell lists"));
+    BH_CUDA(c, cudaMemsetAsync(inter, 0, 6 * sizeof(unsigned long long), c->stream));  // words 8..13
+    const unsigned nb = blocks_for(std::max<int64_t>(slots, 1), 128);
+    k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(ng, dng, slots, c->groups.p, c->wnode.p, c->skip.p, c->begin.p,
+                                                  c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, c->stash_p.p,
+                                                  c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest,
+                                                  overflow);
+    BH_LAUNCH(c);
+    DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
+    for (int a = 0; a < 3; ++a) {
+        BH_TRY(scan_i64(c, arr[a]->p, arr[a]->p, ng, c->d_small + a, dng));
+        k_set_last<<<1, 1, 0, c->stream>>>(arr[a]->p, ng, dng, c->d_small + a);
+        BH_LAUNCH(c);
+    }
+    k_list_room<<<1, 32, 0, c->stream>>>(c->d_small, (long long)c->P.cap - 1, (long long)c->C.cap - 1,
+                                         (long long)c->JJ.cap - 1, c->d_sz);
+    BH_LAUNCH(c);
+    return BH_OK;
+}
+
+// Second part (issued to run only when the lists fit): the groups' lists
+// from their slots or, for the groups without a fitting slot, from a second
+// walk; the expansion into particle indices; the FP32 kernel's group order.
+int stage_lists_dev_fill(Ctx* c) {
+    const int64_t ng = c->n_groups;
+    const unsigned long long* dng = c->d_sz + kSzNg;
+    const WalkParams wp = walk_params(c);
+    const int64_t slots = c->dev_slots, capP = c->walk_cap_p, capC = c->walk_cap_c;
+    const unsigned grid = blocks_for(std::max<int64_t>(slots, 1) * 32, 256);  // a warp per expected group
+    k_unstash<<<grid, 256, 0, c->stream>>>(ng, dng, slots, c->cnt_p.p, c->cnt_c.p, c->stash_p.p, c->stash_c.p, capP,
+                                           capC, c->P.p, c->C.p);
+    BH_LAUNCH(c);
+    k_walk<kWalkFill><<<blocks_for(std::max<int64_t>(slots, 1), 128), 128, 0, c->stream>>>(
+        ng, dng, slots, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+        c->cnt_j.p, c->P.p, c->C.p, c->d_small + 8, c->n_nodes, c->d_status, capP, capC, c->d_small + 12,
+        c->d_small + 11);
+    BH_LAUNCH(c);
+    BH_TRY(expand_lists(c, wp, dng, grid));
     if (c->prm.precision == BH_PREC_FP32) BH_TRY(build_order32(c));
     return BH_OK;
 }

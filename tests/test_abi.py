@@ -44,8 +44,8 @@ def test_binding_struct_layout_matches_header():
     from paper_1907_02289_gb300 import bh
     assert ctypes.sizeof(bh.bh_params) == 8 * 8 + 6 * 4 + 8 + 8
     assert ctypes.sizeof(bh.bh_particles) == 11 * 8 + 8
-    assert ctypes.sizeof(bh.bh_counters) == 12 * 8 + bh.BH_N_STAGES * (8 + 8)
-    assert ctypes.sizeof(bh.bh_tuning) == 8 * 4
+    assert ctypes.sizeof(bh.bh_counters) == 12 * 8 + bh.BH_N_STAGES * (8 + 8) + 3 * 8
+    assert ctypes.sizeof(bh.bh_tuning) == 9 * 4
 
 
 def test_load_fails_loudly_when_missing(tmp_path):

@@ -83,14 +83,14 @@ def test_tuning_validation(ring):
     from paper_1907_02289_gb300 import bh
     P, prm, _, _ = ring
     ctx = bh.Context(**prm)
-    for kw in (dict(chunk=48), dict(warps=0), dict(warps=9), dict(sched=3), dict(n_g=4), dict(graph=2),
-               dict(order_window=-1), dict(graph_contact_room=-1)):
+    for kw in (dict(chunk=48), dict(warps=0), dict(warps=9), dict(sched=3), dict(n_g=4), dict(graph=3),
+               dict(order_window=-1), dict(graph_contact_room=-1), dict(graph_room=-1), dict(graph_room=1001)):
         with pytest.raises(bh.BHError) as e:
             ctx.bh_set_tuning(**kw)
         assert e.value.code == bh.BH_E_INVAL
     t = ctx.bh_get_tuning()
     assert t == dict(n_g=64, chunk=96, warps=4, sched=2, order_by_cost=1, graph=0, order_window=0,
-                     graph_contact_room=0)
+                     graph_contact_room=0, graph_room=25)
 
 
 @pytest.mark.parametrize("precision,dense", [(0, False), (1, False), (1, True)])
