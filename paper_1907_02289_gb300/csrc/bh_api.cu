@@ -64,8 +64,26 @@ static cudaEvent_t take_event(Ctx* c) {
     return e;
 }
 
+// While a step graph is captured: an event-record node (recording a
+// placeholder event) before (k = 0) or after (k = 1) the force kernel, whose
+// event each launch then sets (launch_graph).
+static int graph_timing_node(Ctx* c, int k) {
+    Ctx::GraphTiming* gt = c->gt_cur;
+    if (!gt || !c->gt_idle[k]) return BH_OK;
+    BH_CUDA(c, cudaEventRecordWithFlags(c->gt_idle[k], c->stream, cudaEventRecordExternal));
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    BH_CUDA(c, cudaStreamGetCaptureInfo(c->stream, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    if (nd != 1) return fail(c, BH_E_STATE, "timing node of a captured step: %zu dependencies", nd);
+    gt->node[k] = deps[0];
+    gt->have = k == 1 && gt->node[0] != nullptr;
+    return BH_OK;
+}
+
 int timing_begin(Ctx* c) {
-    if (!c->timing || c->capturing) return BH_OK;
+    if (c->capturing) return graph_timing_node(c, 0);
+    if (!c->timing) return BH_OK;
     cudaEvent_t a = take_event(c), b = take_event(c);
     if (!a || !b) return fail(c, BH_E_CUDA, "cudaEventCreate failed");
     BH_CUDA(c, cudaEventRecord(a, c->stream));
@@ -74,7 +92,8 @@ int timing_begin(Ctx* c) {
 }
 
 int timing_end(Ctx* c) {
-    if (!c->timing || c->capturing || c->ev_force.empty()) return BH_OK;
+    if (c->capturing) return graph_timing_node(c, 1);
+    if (!c->timing || c->ev_force.empty()) return BH_OK;
     BH_CUDA(c, cudaEventRecord(c->ev_force.back().second, c->stream));
     return BH_OK;
 }
@@ -271,6 +290,40 @@ int evaluate(Ctx* c, bh_particles* p) {
     return BH_OK;
 }
 
+// Step-graph timing: the placeholder events (made before any capture), the
+// launch that sets the force kernel's timing events, and the graph kept for
+// its node handles.
+int ensure_graph_events(Ctx* c) {
+    for (cudaEvent_t& e : c->gt_idle)
+        if (!e) BH_CUDA(c, cudaEventCreate(&e));
+    return BH_OK;
+}
+
+int launch_graph(Ctx* c, cudaGraphExec_t exec, const Ctx::GraphTiming& gt) {
+    if (gt.have) {
+        cudaEvent_t a = c->gt_idle[0], b = c->gt_idle[1];
+        const bool timed = c->timing;
+        if (timed) {
+            a = take_event(c);
+            b = take_event(c);
+            if (!a || !b) return fail(c, BH_E_CUDA, "cudaEventCreate failed");
+        }
+        BH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(exec, gt.node[0], a));
+        BH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(exec, gt.node[1], b));
+        BH_CUDA(c, cudaGraphLaunch(exec, c->stream));
+        if (timed) c->ev_force.push_back({a, b});
+        return BH_OK;
+    }
+    BH_CUDA(c, cudaGraphLaunch(exec, c->stream));
+    return BH_OK;
+}
+
+void keep_graph(Ctx::GraphTiming& dst, Ctx::GraphTiming& src) {
+    if (dst.g && dst.g != src.g) cudaGraphDestroy(dst.g);
+    dst = src;
+    src = Ctx::GraphTiming{};
+}
+
 bool same_arrays(const bh_particles& a, const bh_particles& b) {
     return a.x == b.x && a.y == b.y && a.z == b.z && a.vx == b.vx && a.vy == b.vy && a.vz == b.vz && a.m == b.m &&
            a.id == b.id && a.ax == b.ax && a.ay == b.ay && a.az == b.az && a.n == b.n;
@@ -292,6 +345,9 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
         // capture on a private stream (the legacy default stream cannot be
         // captured); the graph is then launched on the context's stream
         if (!c->cap_stream) BH_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        BH_TRY(ensure_graph_events(c));
+        c->gt_tmp = Ctx::GraphTiming{};
+        c->gt_cur = &c->gt_tmp;
         cudaGraph_t g = nullptr;
         const cudaStream_t s0 = c->stream;
         c->stream = c->cap_stream;
@@ -309,6 +365,7 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
         if (rc == BH_OK) rc = stage_force(c, p, true);
         if (rc == BH_OK) rc = stage_kick(c, p, 0.5 * dt);
         c->capturing = false;
+        c->gt_cur = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
         c->stream = s0;
         c->graph_launches = c->n_launches - l0;
@@ -318,6 +375,8 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
             return rc;
         }
         if (ec != cudaSuccess) return fail(c, BH_E_CUDA, "stream capture of the step failed: %s", cudaGetErrorString(ec));
+        // an update keeps the executable's nodes (those of the graph it was
+        // instantiated from, kept for the timing nodes)
         bool updated = false;
         if (c->graph_exec) {
             cudaGraphExecUpdateResultInfo info;
@@ -329,8 +388,13 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
             }
         }
         cudaError_t ei = cudaSuccess;
-        if (!updated) ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
-        cudaGraphDestroy(g);
+        if (updated) {
+            cudaGraphDestroy(g);
+        } else {
+            ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+            c->gt_tmp.g = g;
+            keep_graph(c->gt_reuse, c->gt_tmp);
+        }
         if (ei != cudaSuccess) {
             c->graph_exec = nullptr;
             return fail(c, BH_E_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ei));
@@ -339,7 +403,7 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
         c->graph_p = *p;
         ++c->n_graph_captures;
     }
-    BH_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    BH_TRY(launch_graph(c, c->graph_exec, c->gt_reuse));
     c->n_launches += c->graph_launches;
     c->refine_pending = c->prm.precision == BH_PREC_FP32;  // its count is read when asked for
     c->k_eval++;
@@ -471,8 +535,11 @@ int capture_rebuild(Ctx* c, bh_particles* p) {
     cudaStream_t* ss[3] = {&c->cap_stream, &c->body_stream[0], &c->body_stream[1]};
     for (cudaStream_t* q : ss)
         if (!*q) BH_CUDA(c, cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
+    BH_TRY(ensure_graph_events(c));
     const HostSizes keep{c->n_nodes, c->n_groups, c->key_cur, c->lvl_start};
     c->cap_nodes = cap[0];
+    c->gt_tmp = Ctx::GraphTiming{};
+    c->gt_cur = &c->gt_tmp;
     c->dev_slots = cap[1];
     const cudaStream_t s0 = c->stream;
     c->stream = c->cap_stream;
@@ -497,14 +564,19 @@ int capture_rebuild(Ctx* c, bh_particles* p) {
             BH_TRY(stage_moments(c, p));
             BH_TRY(stage_groups(c));
             BH_TRY(stage_lists_dev_walk(c));
-            return capture_if(c, kOvfLists, c->body_stream[1], [&]() -> int {
-                BH_TRY(stage_lists_dev_fill(c));
-                BH_TRY(stage_force(c, p, true));
-                return stage_kick(c, p, 0.5 * dt);
-            });
+            return capture_if(c, kOvfLists, c->body_stream[1], [&]() -> int { return stage_lists_dev_fill(c); });
         });
+    // forces and kick at the top level (where the force kernel's timing
+    // nodes may sit): they read the overflow bits and do nothing when the
+    // build outgrew its buffers; the contact and refinement passes then find
+    // no candidates
+    c->abort = c->d_sz + kSzOvf;
+    if (rc == BH_OK) rc = stage_force(c, p, true);
+    if (rc == BH_OK) rc = stage_kick(c, p, 0.5 * dt);
+    c->abort = nullptr;
     c->capturing = false;
     c->dev_build = false;
+    c->gt_cur = nullptr;
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
     c->stream = s0;
@@ -525,7 +597,8 @@ int capture_rebuild(Ctx* c, bh_particles* p) {
         c->rgraph_exec = nullptr;
     }
     const cudaError_t ei = cudaGraphInstantiate(&c->rgraph_exec, g, 0);
-    cudaGraphDestroy(g);
+    c->gt_tmp.g = g;  // kept with the executable (its timing nodes)
+    keep_graph(c->gt_rebuild, c->gt_tmp);
     if (ei != cudaSuccess) {
         c->rgraph_exec = nullptr;
         cudaGetLastError();
@@ -556,7 +629,7 @@ bool rebuild_graph_fits(const Ctx* c, const bh_particles* p) {
 
 int graph_rebuild_step(Ctx* c, bh_particles* p) {
     if (!rebuild_graph_fits(c, p)) BH_TRY(capture_rebuild(c, p));
-    BH_CUDA(c, cudaGraphLaunch(c->rgraph_exec, c->stream));
+    BH_TRY(launch_graph(c, c->rgraph_exec, c->gt_rebuild));
     c->n_launches += c->rgraph_launches;
     unsigned long long sz[kSzWords], sm[24];
     BH_CUDA(c, cudaMemcpyAsync(sz, c->d_sz, sizeof(sz), cudaMemcpyDeviceToHost, c->stream));
@@ -877,6 +950,10 @@ int bh_destroy(bh_ctx* ctx) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->rgraph_exec) cudaGraphExecDestroy(c->rgraph_exec);
+    for (Ctx::GraphTiming* gt : {&c->gt_reuse, &c->gt_rebuild, &c->gt_tmp})
+        if (gt->g) cudaGraphDestroy(gt->g);
+    for (cudaEvent_t e : c->gt_idle)
+        if (e) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaStream_t q : c->body_stream)
         if (q) cudaStreamDestroy(q);

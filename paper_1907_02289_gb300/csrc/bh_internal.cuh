@@ -200,6 +200,8 @@ struct Ctx {
     // one graph (graph tuning on), its buffers sized from the previous build
     unsigned long long* d_sz = nullptr;  // kSzWords device words (level bounds, group count, overflow)
     bool dev_build = false;              // issuing a device-sized build (no size read-backs)
+    const unsigned long long* abort = nullptr;  // while issuing the forces and kick of such a step: its
+                                                // overflow bits (nonzero: those kernels do nothing)
     int64_t cap_nodes = 0;               // node capacity of the build being issued
     int64_t dev_slots = 0;               // groups with a list slot in it
     cudaGraphExec_t rgraph_exec = nullptr;  // the captured list-constructing step
@@ -209,6 +211,16 @@ struct Ctx {
     int64_t rgraph_cap[5] = {};          // nodes, slots, P, C, JJ it was captured with
     int64_t rgraph_walk_cap[2] = {};     // and list slot sizes
     cudaStream_t body_stream[2] = {nullptr, nullptr};  // its conditional bodies are captured on these
+    // force-kernel timing inside step graphs: event-record nodes around the
+    // kernel, given fresh events before each launch while timing is on
+    struct GraphTiming {
+        cudaGraph_t g = nullptr;             // the graph the executable was instantiated from
+        cudaGraphNode_t node[2] = {nullptr, nullptr};
+        bool have = false;
+    };
+    GraphTiming gt_reuse, gt_rebuild, gt_tmp;
+    GraphTiming* gt_cur = nullptr;           // the graph being captured
+    cudaEvent_t gt_idle[2] = {nullptr, nullptr};  // recorded by those nodes while timing is off
     int64_t n_graph_builds = 0;          // list builds that ran inside a graph
     int64_t n_graph_build_redos = 0;     // of those, builds redone eagerly after a capacity ran out
     int64_t n_graph_captures = 0;        // step graphs captured

@@ -34,7 +34,8 @@ struct Smem64 {
 };
 
 __global__ void __launch_bounds__(32 * kWarps) k_force64(
-    int64_t ng, const unsigned long long* __restrict__ dng, const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
+    int64_t ng, const unsigned long long* __restrict__ dng, const unsigned long long* __restrict__ abort,
+    const int32_t* __restrict__ groups, const uint32_t* __restrict__ begin,
     const uint32_t* __restrict__ end, const int64_t* __restrict__ jj_off, const uint32_t* __restrict__ JJ,
     const int64_t* __restrict__ pc_off, const int32_t* __restrict__ C, const double* __restrict__ x,
     const double* __restrict__ y, const double* __restrict__ z, const double* __restrict__ vx,
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_force64(
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * kWarps + w;
     if (dng) ng = min(ng, (int64_t)*dng);  // device-sized list build
-    if (k >= ng) return;
+    if (k >= ng || (abort && *abort)) return;  // (abort: that build outgrew its buffers)
     Smem64& S = sm[w];
     const int32_t g = groups[k];
     const uint32_t b = begin[g], e = end[g];
@@ -331,7 +332,7 @@ int stage_force(Ctx* c, bh_particles* p, bool add_central) {
         BH_TRY(timing_begin(c));
         BH_TRY(stage_begin(c, BH_STAGE_FORCE));
         const unsigned long long* dng = c->dev_build ? c->d_sz + kSzNg : nullptr;
-        k_force64<<<nb, 32 * kWarps, 0, c->stream>>>(ng, dng, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p, c->JJ.p,
+        k_force64<<<nb, 32 * kWarps, 0, c->stream>>>(ng, dng, c->abort, c->groups.p, c->begin.p, c->end.p, c->cnt_j.p, c->JJ.p,
                                                      c->cnt_c.p, c->C.p, p->x, p->y, p->z, p->vx, p->vy, p->vz,
                                                      p->m, c->M.p, c->cx.p, c->cy.p, c->cz.p, c->Q.p, fp,
                                                      add_central, p->ax, p->ay, p->az, (uint32_t)c->n,

@@ -136,6 +136,7 @@ struct Smem32 {
 struct Args {
     int64_t ng;
     const unsigned long long* dng;  // device group count (device-sized list builds; NULL: ng)
+    const unsigned long long* abort;  // device-sized build: nonzero overflow bits skip the launch
     const int32_t* order;  // processing order of the groups (NULL: list order)
     const int32_t* groups;
     const uint32_t* begin;
@@ -815,6 +816,7 @@ __global__ void __launch_bounds__(32 * BH_F32_MAXW, 2) k_force32(const Args A) {
     const int64_t wid = (int64_t)blockIdx.x * nw + w;
     Smem32& S = sm[w];
     const unsigned long long t0 = A.warp_time ? global_ns() : 0ull;
+    if (A.abort && *A.abort) return;  // that build outgrew its buffers: the step is finished eagerly
     const int64_t ng = A.dng ? min(A.ng, (int64_t)*A.dng) : A.ng;
     if (A.ticket) {  // persistent, dynamic: the next list slot from the shared counter
         for (;;) {
@@ -1348,6 +1350,7 @@ int launch_force32(Ctx* c, bh_particles* p, const ForceParams& fp, bool add_cent
     Args A;
     A.ng = c->n_groups;
     A.dng = c->dev_build ? c->d_sz + kSzNg : nullptr;
+    A.abort = c->abort;
     A.order = c->order.p;
     A.groups = c->groups.p;
     A.begin = c->begin.p;

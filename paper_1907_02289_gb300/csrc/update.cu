@@ -8,11 +8,13 @@
 namespace bh {
 namespace {
 
+// abort (a list-constructing graph step): nonzero overflow bits mean the
+// step's forces were not computed, so the kick is skipped.
 __global__ void k_kick(int64_t n, double h, const double* __restrict__ ax, const double* __restrict__ ay,
                        const double* __restrict__ az, double* __restrict__ vx, double* __restrict__ vy,
-                       double* __restrict__ vz) {
+                       double* __restrict__ vz, const unsigned long long* __restrict__ abort) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (abort && *abort)) return;
     vx[i] += h * ax[i];
     vy[i] += h * ay[i];
     vz[i] += h * az[i];
@@ -111,7 +113,8 @@ int stage_diagnostics(Ctx* c, const bh_particles* p, double* host_out) {
 
 int stage_kick(Ctx* c, bh_particles* p, double h) {
     BH_TRY(stage_begin(c, BH_STAGE_UPDATE));
-    k_kick<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, p->ax, p->ay, p->az, p->vx, p->vy, p->vz);
+    k_kick<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->n, h, p->ax, p->ay, p->az, p->vx, p->vy, p->vz,
+                                                         c->abort);
     BH_LAUNCH(c);
     return stage_end(c);
 }

@@ -152,3 +152,31 @@ def test_outgrown_graph_build_is_finished_eagerly(what):
     k1 = c1.bh_get_counters()
     assert k1["n_graph_builds"] == 2
     assert k1["n_graph_build_redos"] >= 1
+
+
+@pytest.mark.parametrize("graph", [1, 2])
+def test_force_kernel_timed_in_graph_steps(graph):
+    """With timing on, every force launch is timed, those inside step
+    graphs included (event-record nodes around the kernel, given fresh
+    events at each launch); off again, the graphs record nothing."""
+    from paper_1907_02289_gb300 import bh
+    P = synth.ring(20000, 37)
+    prm = _ring_prm()
+    ctx = bh.Context(**prm)
+    ctx.bh_set_tuning(graph=graph, sched=2)
+    D = bh.Particles(P)
+    ctx.bh_step(D, 3)  # evaluations 0..3 (graphs captured)
+    ctx.bh_sync()
+    ctx.bh_set_timing(True)
+    ctx.bh_get_timing(reset=True)
+    ctx.bh_step(D, 8)  # evaluations 4..11: two list builds, six reuses
+    ctx.bh_sync()
+    ms, launches = ctx.bh_get_timing(reset=True)
+    assert launches == 8
+    assert ms > 0.0
+    ctx.bh_set_timing(False)
+    ctx.bh_step(D, 2)
+    ctx.bh_sync()
+    ctx.bh_set_timing(True)
+    ms, launches = ctx.bh_get_timing(reset=True)
+    assert launches == 0
