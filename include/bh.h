@@ -180,8 +180,8 @@ typedef struct {
     double stage_ms[BH_N_STAGES];     /* device time of each stage (CUDA events on the
                                        * context's stream) summed over the calls made
                                        * with timing on since the last reset
-                                       * (bh_get_timing); steps run as a captured
-                                       * graph are not timed                     */
+                                       * (bh_get_timing); the stages of steps run
+                                       * as a graph are not timed                */
     int64_t stage_calls[BH_N_STAGES]; /* timed calls of each stage                */
     int64_t n_graph_builds;      /* list-constructing steps of bh_step run as one CUDA
                                   * graph launch (bh_tuning.graph = 1)          */
@@ -291,7 +291,9 @@ int bh_set_list_capacity(bh_ctx* ctx, int64_t entries);
 
 /* Measurement hooks.  bh_set_timing(ctx, 1) makes every force-kernel launch,
  * and every stage of the path (BH_STAGE_*), record a pair of CUDA events on
- * the context's stream (work inside a captured graph step is not timed);
+ * the context's stream.  In a step issued as a CUDA graph only the force
+ * kernel is timed (event-record nodes around it, given a fresh pair of
+ * events at each launch); its other stages are not;
  * bh_get_timing synchronises the stream and returns the summed force-kernel
  * time (ms) and the number of timed launches, clearing them and the stage
  * times of bh_counters when reset != 0. */
