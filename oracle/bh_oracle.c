@@ -133,41 +133,44 @@ void orc_keys(int64_t n, const double* x, const double* y, const double* z,
  * (phi, r, z), which for a narrow ring at r ~ 1 measure distance like
  * (x, y, z) (the paper's Eq. for ds^2); forces stay Cartesian.
  *
- * phi comes from atan reduced to [0, tan(pi/12)] by
+ * phi and r are FP32 numbers (a tree coordinate only has to place a
+ * particle within its key cell, 2^-21 of the box, and the contact clause's
+ * margin covers their error): x and y are rounded to FP32; phi comes from
+ * atan reduced to [0, tan(pi/12)] by
  * atan(t) = pi/6 + atan((sqrt(3) t - 1) / (t + sqrt(3))) and the Taylor
  * series u - u^3/3 + ... - u^11/11 (truncation below 3e-9 rad), then placed
- * in its octant.  Only IEEE-rounded +, -, *, / are used, in a fixed order, so
- * the angle (and the key) is a deterministic function of (x, y).
- * r = sqrt(x^2 + y^2) (correctly rounded).
+ * in its octant; r = sqrt(x^2 + y^2).  Only IEEE-rounded FP32 +, -, *, / and
+ * sqrt are used, in a fixed order, so the angle (and the key) is a
+ * deterministic function of (x, y); its error is below 1e-6 rad.
  * ---------------------------------------------------------------------- */
-static double orc_atan01(double t)
+static float orc_atan01(float t)
 {
-    const double sqrt3 = 1.7320508075688772, tan15 = 0.2679491924311227, pi6 = 0.5235987755982988;
-    double base = 0.0, u = t;
+    const float sqrt3 = 1.7320508075688772f, tan15 = 0.2679491924311227f, pi6 = 0.5235987755982988f;
+    float base = 0.0f, u = t;
     if (t > tan15) {
-        u = (t * sqrt3 - 1.0) / (t + sqrt3);
+        u = (t * sqrt3 - 1.0f) / (t + sqrt3);
         base = pi6;
     }
-    double u2 = u * u;
-    double p = -1.0 / 11.0;
-    p = p * u2 + 1.0 / 9.0;
-    p = p * u2 + -1.0 / 7.0;
-    p = p * u2 + 1.0 / 5.0;
-    p = p * u2 + -1.0 / 3.0;
-    p = p * u2 + 1.0;
+    float u2 = u * u;
+    float p = -1.0f / 11.0f;
+    p = p * u2 + 1.0f / 9.0f;
+    p = p * u2 + -1.0f / 7.0f;
+    p = p * u2 + 1.0f / 5.0f;
+    p = p * u2 + -1.0f / 3.0f;
+    p = p * u2 + 1.0f;
     return base + u * p;
 }
 
-static double orc_phi(double x, double y)
+static float orc_phi(float x, float y)
 {
-    const double pi2 = 1.5707963267948966, pi = 3.141592653589793, twopi = 6.283185307179586;
-    double ax = fabs(x), ay = fabs(y);
-    double mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
-    if (mx == 0.0) return 0.0;
-    double a = orc_atan01(mn / mx);
+    const float pi2 = 1.5707963267948966f, pi = 3.141592653589793f, twopi = 6.283185307179586f;
+    float ax = fabsf(x), ay = fabsf(y);
+    float mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
+    if (mx == 0.0f) return 0.0f;
+    float a = orc_atan01(mn / mx);
     if (ay > ax) a = pi2 - a;
-    if (x < 0.0) a = pi - a;
-    if (y < 0.0) a = twopi - a;
+    if (x < 0.0f) a = pi - a;
+    if (y < 0.0f) a = twopi - a;
     return a;
 }
 
@@ -175,8 +178,9 @@ void orc_cyl(int64_t n, const double* x, const double* y, double* phi, double* r
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        phi[i] = orc_phi(x[i], y[i]);
-        r[i] = sqrt(x[i] * x[i] + y[i] * y[i]);
+        const float xf = (float)x[i], yf = (float)y[i];
+        phi[i] = (double)orc_phi(xf, yf);
+        r[i] = (double)sqrtf(xf * xf + yf * yf);
     }
 }
 
@@ -538,14 +542,14 @@ void orc_lists(int64_t ng, const int32_t* groups, const uint8_t* level,
 
 /* Cylindrical frame (phi, r, z grid with scale S = 2^21 / L): two particles
  * within r_coll have |dr|, |dz| <= r_coll and a phi difference of at most
- * ~r_coll / r_min, so (r_coll / r_min + 2e-8) S, squared, bounds their grid
- * distance (2e-8 covers the angle's approximation error); the phi axis has
- * period floor(2 pi S) cells. */
+ * ~r_coll / r_min, so (r_coll / r_min + 4e-6) S, squared, bounds their grid
+ * distance (4e-6 covers twice the FP32 tree coordinates' error, and r_min's);
+ * the phi axis has period floor(2 pi S) cells. */
 void orc_cyl_geometry(double r_coll, double r_min, double L, double* rcq2, int64_t* period)
 {
     double S = 2097152.0 / L;
     double a = r_coll / r_min;
-    a = a + 2e-8;
+    a = a + 4e-6;
     a = a * S;
     *rcq2 = a * a;
     *period = (int64_t)floor(6.283185307179586 * S);

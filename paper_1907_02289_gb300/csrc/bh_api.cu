@@ -160,14 +160,34 @@ int setup_patches(Ctx* c, int n_patches, const int64_t* off) {
     BH_TRY(grow(c, c->d_off, (size_t)n_patches + 1, "patch offsets"));
     BH_CUDA(c, cudaMemcpyAsync(c->d_off.p, c->h_off.data(), c->h_off.size() * sizeof(int64_t),
                                cudaMemcpyHostToDevice, c->stream));
+    std::vector<uint32_t> meta;
+    std::vector<uint2> map;
+    std::vector<int> poff;
     if (n_patches > 1) {
-        std::vector<uint32_t> meta;
         c->n_tiles = sort_tiles_for(c->h_off, &meta);
         BH_TRY(grow(c, c->tile_meta, meta.size(), "sort tile table"));
         BH_CUDA(c, cudaMemcpyAsync(c->tile_meta.p, meta.data(), meta.size() * sizeof(uint32_t),
                                    cudaMemcpyHostToDevice, c->stream));
+        // root-box blocks in proportion to the patch sizes (at least one
+        // each; about four per SM in all)
+        const double total = (double)(off[n_patches] - off[0]);
+        const double want = 4.0 * c->num_sms;
+        poff.push_back(0);
+        for (int q = 0; q < n_patches; ++q) {
+            const int64_t sz = off[q + 1] - off[q];
+            const int nbq = (int)std::max<double>(1.0, std::ceil(want * (double)sz / total));
+            for (int j = 0; j < nbq; ++j) map.push_back(make_uint2((unsigned)q, (unsigned)j));
+            poff.push_back((int)map.size());
+        }
+        c->n_box_blocks = (int)map.size();
+        BH_TRY(grow(c, c->box_map, map.size(), "root-box block map"));
+        BH_TRY(grow(c, c->box_poff, poff.size(), "root-box block offsets"));
+        BH_CUDA(c, cudaMemcpyAsync(c->box_map.p, map.data(), map.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                                   c->stream));
+        BH_CUDA(c, cudaMemcpyAsync(c->box_poff.p, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                   c->stream));
     }
-    BH_CUDA(c, cudaStreamSynchronize(c->stream));
+    BH_CUDA(c, cudaStreamSynchronize(c->stream));  // (the host tables above outlive no call)
     return BH_OK;
 }
 
@@ -964,7 +984,7 @@ int bh_destroy(bh_ctx* ctx) {
     cudaFree(c->d_small);
     cudaFree(c->d_sz);
     using bh::release;
-    release(c->d_off); release(c->tile_meta); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag); release(c->pot);
+    release(c->d_off); release(c->tile_meta); release(c->box_map); release(c->box_poff); release(c->d_rcq); release(c->d_rfar); release(c->d_period); release(c->cyl); release(c->box_part); release(c->order_cnt); release(c->warp_time); release(c->contact_acc); release(c->diag); release(c->pot);
     for (int b = 0; b < 2; ++b) {
         release(c->ord_key[b]);
         release(c->ord_idx[b]);

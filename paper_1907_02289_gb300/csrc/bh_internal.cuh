@@ -111,6 +111,9 @@ struct Ctx {
     DBuf<int64_t> d_off;                // the same on the device
     DBuf<uint32_t> tile_meta;           // sort tiles per patch (4 words per tile), n_patches > 1
     int64_t n_tiles = 0;
+    DBuf<uint2> box_map;                // root-box blocks of the patches: (patch, block within it)
+    DBuf<int> box_poff;                 // first root-box block of each patch (n_patches + 1)
+    int n_box_blocks = 0;
     DBuf<long long> d_rcq;              // per patch walk contact threshold
     DBuf<long long> d_rfar;             // per patch far threshold of the split expansion
     DBuf<long long> d_period;           // per patch phi period in grid cells (cylindrical frame; 0 = none)

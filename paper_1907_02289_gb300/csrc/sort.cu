@@ -23,17 +23,35 @@ __device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
     }
 }
 
-// Per-block min/max of each axis of patch blockIdx.y (particles
-// [off[q], off[q+1])) -> part[6 * (q * gridDim.x + block) + {mn x,y,z, mx x,y,z}].
+// Per-block min/max of each axis of one patch -> 6 partials per block
+// {mn x,y,z, mx x,y,z}.  Without a block map: patch blockIdx.y, its
+// gridDim.x blocks, partials at q * gridDim.x + block.  With one (several
+// patches of uneven sizes): block b works on patch map[b].x as its map[b].y-th
+// of poff[q + 1] - poff[q] blocks (blocks in proportion to the patch sizes),
+// partials at b.
 __global__ void k_box_partial(const double* __restrict__ x, const double* __restrict__ y,
                               const double* __restrict__ z, const int64_t* __restrict__ off,
+                              const uint2* __restrict__ map, const int* __restrict__ poff,
                               double* __restrict__ part, int* status) {
     __shared__ double s[6][kBoxThreads / 32];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    const int64_t e = off[blockIdx.y + 1];
-    for (int64_t i = off[blockIdx.y] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    int q, j, nbq;
+    int64_t slot;
+    if (map) {
+        const uint2 e = map[blockIdx.x];
+        q = (int)e.x;
+        j = (int)e.y;
+        nbq = poff[q + 1] - poff[q];
+        slot = blockIdx.x;
+    } else {
+        q = blockIdx.y;
+        j = blockIdx.x;
+        nbq = gridDim.x;
+        slot = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    }
+    const int64_t e = off[q + 1];
+    for (int64_t i = off[q] + (int64_t)j * blockDim.x + threadIdx.x; i < e; i += (int64_t)nbq * blockDim.x) {
         double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -57,15 +75,18 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
         double r = s[threadIdx.x][0];
         for (int k = 1; k < kBoxThreads / 32; ++k)
             r = threadIdx.x < 3 ? fmin(r, s[threadIdx.x][k]) : fmax(r, s[threadIdx.x][k]);
-        part[6 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] = r;
+        part[6 * slot + threadIdx.x] = r;
     }
 }
 
-// box of patch q = blockIdx.x from its nb partials: {lo_x, lo_y, lo_z, L, S}
-// at box + 8 q.  Cylindrical frame (cyl): every particle must be off the axis
-// (r > 0), else kStatAxis.
-__global__ void k_box_final(const double* __restrict__ part_all, int nb, double* box_all, int cyl, int* status) {
-    const double* part = part_all + 6 * (int64_t)blockIdx.x * nb;
+// box of patch q = blockIdx.x from its partials (nb per patch, or those of
+// blocks poff[q] .. poff[q + 1] - 1): {lo_x, lo_y, lo_z, L, S} at box + 8 q.
+// Cylindrical frame (cyl): every particle must be off the axis (r > 0), else
+// kStatAxis.
+__global__ void k_box_final(const double* __restrict__ part_all, int nb, const int* __restrict__ poff,
+                            double* box_all, int cyl, int* status) {
+    const double* part = part_all + 6 * (poff ? (int64_t)poff[blockIdx.x] : (int64_t)blockIdx.x * nb);
+    if (poff) nb = poff[blockIdx.x + 1] - poff[blockIdx.x];
     double* box = box_all + 8 * blockIdx.x;
     __shared__ double r[6];
     if (threadIdx.x < 6) {
@@ -89,45 +110,49 @@ __global__ void k_box_final(const double* __restrict__ part_all, int nb, double*
     }
 }
 
-// Sec. 4.3: tree coordinates (phi, r, z) for a ring.  phi from atan of the
-// octant-reduced ratio, itself reduced to [0, tan(pi/12)] with
+// Sec. 4.3: tree coordinates (phi, r, z) for a ring, phi and r as FP32
+// numbers (a tree coordinate only has to place a particle within its key
+// cell, 2^-21 of the box; the walk's contact clause has a margin for their
+// error).  x, y rounded to FP32; phi from atan of the octant-reduced ratio,
+// itself reduced to [0, tan(pi/12)] with
 // atan(t) = pi/6 + atan((sqrt(3) t - 1) / (t + sqrt(3))) and summed as the
-// Taylor series to u^11 (truncation below 3e-9 rad); every operation is an
-// IEEE-rounded +, -, *, / in a fixed order, so phi is a deterministic
-// function of (x, y).  r = sqrt(x^2 + y^2), correctly rounded.
-__device__ __forceinline__ double atan01(double t) {
-    const double sqrt3 = 1.7320508075688772, tan15 = 0.2679491924311227, pi6 = 0.5235987755982988;
-    double base = 0.0, u = t;
+// Taylor series to u^11 (truncation below 3e-9 rad); r = sqrt(x^2 + y^2).
+// Every operation is an IEEE-rounded FP32 +, -, *, / or sqrt in a fixed
+// order, so phi is a deterministic function of (x, y), within 1e-6 rad of
+// the true angle.
+__device__ __forceinline__ float atan01(float t) {
+    const float sqrt3 = 1.7320508075688772f, tan15 = 0.2679491924311227f, pi6 = 0.5235987755982988f;
+    float base = 0.0f, u = t;
     if (t > tan15) {
-        u = __ddiv_rn(__dsub_rn(__dmul_rn(t, sqrt3), 1.0), __dadd_rn(t, sqrt3));
+        u = __fdiv_rn(__fsub_rn(__fmul_rn(t, sqrt3), 1.0f), __fadd_rn(t, sqrt3));
         base = pi6;
     }
-    const double u2 = __dmul_rn(u, u);
-    double p = -1.0 / 11.0;
-    p = __dadd_rn(__dmul_rn(p, u2), 1.0 / 9.0);
-    p = __dadd_rn(__dmul_rn(p, u2), -1.0 / 7.0);
-    p = __dadd_rn(__dmul_rn(p, u2), 1.0 / 5.0);
-    p = __dadd_rn(__dmul_rn(p, u2), -1.0 / 3.0);
-    p = __dadd_rn(__dmul_rn(p, u2), 1.0);
-    return __dadd_rn(base, __dmul_rn(u, p));
+    const float u2 = __fmul_rn(u, u);
+    float p = -1.0f / 11.0f;
+    p = __fadd_rn(__fmul_rn(p, u2), 1.0f / 9.0f);
+    p = __fadd_rn(__fmul_rn(p, u2), -1.0f / 7.0f);
+    p = __fadd_rn(__fmul_rn(p, u2), 1.0f / 5.0f);
+    p = __fadd_rn(__fmul_rn(p, u2), -1.0f / 3.0f);
+    p = __fadd_rn(__fmul_rn(p, u2), 1.0f);
+    return __fadd_rn(base, __fmul_rn(u, p));
 }
 
 __global__ void k_cyl(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
                       double* __restrict__ phi, double* __restrict__ r) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double X = x[i], Y = y[i];
-    const double ax = fabs(X), ay = fabs(Y);
-    const double mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
-    double a = 0.0;
-    if (mx != 0.0) {
-        a = atan01(__ddiv_rn(mn, mx));
-        if (ay > ax) a = __dsub_rn(1.5707963267948966, a);
-        if (X < 0.0) a = __dsub_rn(3.141592653589793, a);
-        if (Y < 0.0) a = __dsub_rn(6.283185307179586, a);
+    const float X = __double2float_rn(x[i]), Y = __double2float_rn(y[i]);
+    const float ax = fabsf(X), ay = fabsf(Y);
+    const float mx = ax > ay ? ax : ay, mn = ax > ay ? ay : ax;
+    float a = 0.0f;
+    if (mx != 0.0f) {
+        a = atan01(__fdiv_rn(mn, mx));
+        if (ay > ax) a = __fsub_rn(1.5707963267948966f, a);
+        if (X < 0.0f) a = __fsub_rn(3.141592653589793f, a);
+        if (Y < 0.0f) a = __fsub_rn(6.283185307179586f, a);
     }
-    phi[i] = a;
-    r[i] = __dsqrt_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)));
+    phi[i] = (double)a;
+    r[i] = (double)__fsqrt_rn(__fadd_rn(__fmul_rn(X, X), __fmul_rn(Y, Y)));
 }
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
@@ -369,16 +394,28 @@ int stage_keys(Ctx* c, const bh_particles* p) {
         cx = c->cyl.p;
         cy = c->cyl.p + n;
     }
-    // all patches at once: nb blocks per patch for the boxes, then one pass
-    // for the keys
+    // all patches at once: blocks for the boxes (in proportion to the patch
+    // sizes when there are several), then one pass for the keys
     const int np = c->n_patches;
-    const int64_t per = n / np;
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nbmax / std::min(np, nbmax), blocks_for(per, 4 * kBoxThreads)));
-    BH_TRY(grow(c, c->box_part, 6 * (size_t)nb * np, "box partials"));
-    k_box_partial<<<dim3(nb, np), kBoxThreads, 0, c->stream>>>(cx, cy, p->z, c->d_off.p, c->box_part.p, c->d_status);
-    BH_LAUNCH(c);
-    k_box_final<<<np, 32, 0, c->stream>>>(c->box_part.p, nb, c->d_box, c->prm.key_frame == 1, c->d_status);
-    BH_LAUNCH(c);
+    if (np > 1) {
+        const int nbt = c->n_box_blocks;
+        BH_TRY(grow(c, c->box_part, 6 * (size_t)nbt, "box partials"));
+        k_box_partial<<<nbt, kBoxThreads, 0, c->stream>>>(cx, cy, p->z, c->d_off.p, c->box_map.p, c->box_poff.p,
+                                                          c->box_part.p, c->d_status);
+        BH_LAUNCH(c);
+        k_box_final<<<np, 32, 0, c->stream>>>(c->box_part.p, 0, c->box_poff.p, c->d_box, c->prm.key_frame == 1,
+                                              c->d_status);
+        BH_LAUNCH(c);
+    } else {
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nbmax, blocks_for(n, 4 * kBoxThreads)));
+        BH_TRY(grow(c, c->box_part, 6 * (size_t)nb, "box partials"));
+        k_box_partial<<<nb, kBoxThreads, 0, c->stream>>>(cx, cy, p->z, c->d_off.p, nullptr, nullptr,
+                                                         c->box_part.p, c->d_status);
+        BH_LAUNCH(c);
+        k_box_final<<<1, 32, 0, c->stream>>>(c->box_part.p, nb, nullptr, c->d_box, c->prm.key_frame == 1,
+                                             c->d_status);
+        BH_LAUNCH(c);
+    }
     k_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(cx, cy, p->z, n, c->d_off.p, np, c->d_box, c->key[0].p,
                                                       c->idx[0].p);
     BH_LAUNCH(c);

@@ -336,9 +336,9 @@ __global__ void k_set_last(int64_t* off, int64_t ng, const unsigned long long* d
 // Walk thresholds per patch from its key grid (S = 2^21 / L).  Contact
 // reach in grid units: Cartesian r_coll S; cylindrical (phi, r, z): two
 // particles within r_coll have |dr|, |dz| <= r_coll and a phi difference of
-// at most ~r_coll / r_min, so (r_coll / r_min + 2e-8) S bounds their grid
-// distance (2e-8 covers the angle's approximation error), and the phi axis
-// wraps after floor(2 pi S) cells.  rcq = floor(reach^2); the far threshold
+// at most ~r_coll / r_min, so (r_coll / r_min + 4e-6) S bounds their grid
+// distance (4e-6 covers twice the FP32 tree coordinates' error), and the phi
+// axis wraps after floor(2 pi S) cells.  rcq = floor(reach^2); the far threshold
 // of the split expansion widens the reach by 1e-5 of itself plus two cells,
 // so that no rounding of a coordinate into its cell can put a touching pair
 // into a far leaf.  Round-to-nearest operations throughout (no contraction).
@@ -352,7 +352,7 @@ __global__ void k_walk_thresholds(const double* __restrict__ box, int np, double
     long long per = 0;
     if (cyl) {
         a = __ddiv_rn(r_coll, box[8 * q + 1]);
-        a = __dadd_rn(a, 2e-8);
+        a = __dadd_rn(a, 4e-6);
         a = __dmul_rn(a, S);
         per = (long long)floor(__dmul_rn(6.283185307179586, S));
     } else {

@@ -59,7 +59,7 @@ def _thresholds(prm, lo, L):
     stated rule."""
     S = 2097152.0 / L
     if prm.get("key_frame", 0) == 1:
-        a = (prm["r_coll"] / lo[1] + 2e-8) * S
+        a = (prm["r_coll"] / lo[1] + 4e-6) * S
         period = int(math.floor(2 * math.pi * S))
     else:
         a = prm["r_coll"] * S

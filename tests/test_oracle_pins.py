@@ -701,15 +701,21 @@ def test_cyl_angle_against_atan2_and_special_angles():
     y = rng.normal(size=20000)
     phi, r = orc.cyl_coords(x, y)
     ref = np.mod(np.arctan2(y, x), 2 * np.pi)
-    assert np.abs(phi - ref).max() < 3.5e-9  # Taylor truncation of the reduced atan
-    assert np.all((phi >= 0) & (phi < 2 * np.pi))
-    assert np.allclose(r, np.hypot(x, y), rtol=1e-15, atol=0)
+    # FP32 coordinates: x, y rounded to FP32, a few FP32 roundings of a value
+    # below 2 pi (ulp 4.8e-7) and the series' truncation (3e-9)
+    assert np.abs(phi - ref).max() < 1e-6
+    assert np.all((phi >= 0) & (phi <= 2 * np.pi))
+    assert np.allclose(r, np.hypot(x, y), rtol=3e-7, atol=0)
+    # r is the correctly rounded FP32 root of the FP32 sum of squares
+    xf, yf = x.astype(np.float32), y.astype(np.float32)
+    assert np.array_equal(r, np.sqrt(xf * xf + yf * yf).astype(np.float64))
     # axes and diagonals
     xs = np.array([1.0, 0.0, -1.0, 0.0, 1.0, -1.0, -1.0, 1.0, 0.0])
     ys = np.array([0.0, 1.0, 0.0, -1.0, 1.0, 1.0, -1.0, -1.0, 0.0])
     phi, _ = orc.cyl_coords(xs, ys)
     want = np.array([0, 0.5, 1, 1.5, 0.25, 0.75, 1.25, 1.75, 0]) * np.pi
-    assert np.abs(phi - want).max() < 3.5e-9
+    assert np.abs(phi - want).max() < 1e-6
+    assert phi[0] == 0.0 and phi[8] == 0.0  # the positive x axis and the origin
 
 
 def test_cyl_angle_monotone_around_the_circle():
@@ -727,14 +733,16 @@ def _cyl_state(n, seed=7, **kw):
 def test_cyl_lists_brute_force_periodic_definition():
     """Same ancestor definition as the Cartesian case, with the opening test
     written out independently: phi gap the shorter way round a period of
-    floor(2 pi S) cells, contact clause ((r_coll / r_min + 2e-8) S)^2."""
+    floor(2 pi S) cells, contact clause ((r_coll / r_min + 4e-6) S)^2 with
+    r_min the smallest FP32 radius."""
     P, prm, S = _cyl_state(64, n_g=8, n_leaf=2, theta=0.7)
     t = S.tree
     nn = len(t["level"])
     Sg = 2097152.0 / S.L
     period = int(np.floor(2 * np.pi * Sg))
-    rmin = np.sqrt(S.P["x"] ** 2 + S.P["y"] ** 2).min()
-    rc = (prm.r_coll / rmin + 2e-8) * Sg
+    xf, yf = S.P["x"].astype(np.float32), S.P["y"].astype(np.float32)
+    rmin = float(np.sqrt(xf * xf + yf * yf).min())
+    rc = (prm.r_coll / rmin + 4e-6) * Sg
     rcq2 = rc * rc
 
     def gap(lo_c, hi_c, lo_g, hi_g, periodic):
