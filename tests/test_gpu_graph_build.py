@@ -40,16 +40,20 @@ def _cube_prm(**kw):
 
 def _run(P, prm, graph, steps, offsets=None, tune=None, between=None):
     """steps: list of step counts per bh_step call; between(k, D) may change
-    the particles after call k (the same change for every run)."""
+    the particles after call k (the same change for every run); tune
+    "retune" changes the launch settings after every call."""
     from paper_1907_02289_gb300 import bh
     ctx = bh.Context(offsets=offsets, **prm) if offsets is not None else bh.Context(**prm)
-    ctx.bh_set_tuning(graph=graph, sched=2, **(tune or {}))
+    retune = tune == "retune"
+    ctx.bh_set_tuning(graph=graph, sched=2, **({} if retune or not tune else tune))
     D = bh.Particles(P)
     for k, s in enumerate(steps):
         ctx.bh_step(D, s)
         ctx.bh_sync()
         if between:
             between(k, D)
+        if retune:
+            ctx.bh_set_tuning(warps=(2, 8, 4, 8)[k % 4], sched=(1, 2)[k % 2], chunk=(64, 96)[k % 2])
     return ctx, D
 
 
@@ -82,6 +86,11 @@ CASES = {
     "cube_fp64": (lambda: synth.uniform_cube(6000, 33), lambda: _cube_prm(), None, None),
     # uneven patches (a forest of trees), FP32
     "patches": (None, lambda: _ring_prm(), [4000, 25000, 900, 12000], None),
+    # frame rotating at the Kepler rate of r = 1 (Sec. 4.4), cylindrical keys
+    "ring_rotating": (lambda: synth.ring(25013, 38, phi_max=0.1), lambda: _ring_prm(omega=1.0, key_frame=1), None,
+                      None),
+    # settings changed between steps: the step graphs are captured again
+    "retuned": (lambda: synth.ring(20011, 39), lambda: _ring_prm(), None, "retune"),
 }
 
 
@@ -99,7 +108,7 @@ def test_graph_builds_equal_eager_builds(case):
         P = make()
     # evaluations 0..12: builds at 0 (eager: the first), 4, 8, 12
     steps = [3, 1, 4, 4]
-    c0, D0 = _run(P, prm, 0, steps, offsets)
+    c0, D0 = _run(P, prm, 0, steps, offsets, tune="retune" if tune == "retune" else None)
     c1, D1 = _run(P, prm, 1, steps, offsets, tune=tune)
     _same_state(c0, D0, c1, D1)
     k0, k1 = c0.bh_get_counters(), c1.bh_get_counters()
