@@ -437,11 +437,13 @@ int graph_reuse_step(Ctx* c, bh_particles* p) {
 // refinement passes, kick) is one graph launch.  Its buffers are sized before
 // capture from the previous build, with room to grow; the step reads nothing
 // back while it runs (sizes stay on the device, kSz*).  Two conditional nodes
-// guard it: the work after the tree runs only if the nodes fitted their
-// capacity, the work after the walk only if the lists fitted theirs.  When
-// one did not, the step stops there (positions kicked and drifted, particles
-// reordered, accelerations and the final kick not yet done); the host grows
-// the buffers and finishes the step eagerly, which gives the same result.
+// guard the build: the work after the tree runs only if the nodes fitted
+// their capacity, the list writing after the walk only if the lists fitted
+// theirs.  The forces and the final kick sit at the graph's top level (where
+// the force kernel's timing nodes can be) and do nothing when an overflow bit
+// is set.  A step that outgrew its buffers thus stops with positions kicked
+// and drifted and particles reordered; the host, which reads the sizes at the
+// step's end, grows the buffers and finishes it eagerly, with the same result.
 
 __global__ void k_cond_set(cudaGraphConditionalHandle h, const unsigned long long* sz, unsigned long long mask) {
     if (threadIdx.x == 0) cudaGraphSetConditional(h, (sz[kSzOvf] & mask) ? 0u : 1u);
