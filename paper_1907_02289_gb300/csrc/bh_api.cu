@@ -508,7 +508,7 @@ int size_dev_build(Ctx* c, const int64_t cap[5]) {
     const bool f32 = c->prm.precision == BH_PREC_FP32;
     for (auto* b : {&c->level, &c->nchild}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
     for (auto* b : {&c->begin, &c->end}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
-    for (auto* b : {&c->parent, &c->first_child, &c->skip}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
+    for (auto* b : {&c->parent, &c->first_child}) BH_TRY(grow(c, *b, (size_t)nodes, "node arrays"));
     BH_TRY(grow(c, c->qlo, 3 * (size_t)nodes, "node qlo"));
     BH_TRY(grow(c, c->qhi, 3 * (size_t)nodes, "node qhi"));
     BH_TRY(grow(c, c->wnode, (size_t)nodes, "walk records"));
@@ -998,7 +998,7 @@ int bh_destroy(bh_ctx* ctx) {
     }
     release(c->sort_hist); release(c->digit_hist); release(c->pscratch); release(c->scan_tmp);
     release(c->level); release(c->nchild); release(c->begin); release(c->end); release(c->parent);
-    release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->skip); release(c->split_cnt);
+    release(c->first_child); release(c->qlo); release(c->qhi); release(c->wnode); release(c->split_cnt);
     release(c->split_off); release(c->split_bnd); release(c->M); release(c->cx); release(c->cy);
     release(c->cz); release(c->Q); release(c->cell32); release(c->cell32lo); release(c->refine); release(c->cbnd); release(c->cslot); release(c->cflag); release(c->phi); release(c->plo); release(c->contacts); release(c->gmark);
     release(c->gflag); release(c->gpos); release(c->groups); release(c->order); release(c->cnt_p);

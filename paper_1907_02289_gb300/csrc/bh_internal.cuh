@@ -53,8 +53,9 @@ int grow(Ctx* c, DBuf<T>& b, size_t n, const char* what, bool keep = false) {
     return rc;
 }
 
-// Per-node packed record read by the walk: (qlo.xyz, level | nchild << 8),
-// (qhi.xyz, first_child).
+// Per-node packed record read by the walk: (qlo.x | level << 21, qlo.y,
+// qlo.z, successor of the subtree or -1), (qhi.xyz, first child or ~0 for a
+// leaf).
 struct WalkNode {
     uint4 a, b;
 };
@@ -142,7 +143,6 @@ struct Ctx {
     DBuf<int32_t> parent, first_child;
     DBuf<uint32_t> qlo, qhi;         // 3 per node
     DBuf<WalkNode> wnode;
-    DBuf<int32_t> skip;                 // depth-first successor of each node's subtree (-1: none)
     DBuf<uint32_t> split_cnt;        // per node of a level
     DBuf<uint32_t> split_off;
     DBuf<uint32_t> split_bnd;        // 9 per node of a level

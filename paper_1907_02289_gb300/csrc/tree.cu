@@ -255,14 +255,34 @@ __global__ void __launch_bounds__(kLvTile) k_split_write_d(
     }
 }
 
+// Depth-first successor of node u's subtree: the node a pre-order walk
+// visits after u when it does not descend into u.  Children of a node are
+// consecutive ids, so that is u + 1 unless u is its parent's last child, in
+// which case it is the parent's successor; a root has none (-1), which ends
+// the walk of its patch.
+__device__ __forceinline__ int32_t skip_of(int64_t u, const int32_t* __restrict__ parent,
+                                           const int32_t* __restrict__ first_child,
+                                           const uint8_t* __restrict__ nchild, int* status) {
+    int64_t v = u;
+    for (int up = 0; up <= kLevels + 1; ++up) {
+        const int32_t p = parent[v];
+        if (p < 0) return -1;
+        if (v + 1 < (int64_t)first_child[p] + nchild[p]) return (int32_t)(v + 1);
+        v = p;
+    }
+    atomicOr(status, kStatBounds);  // deeper than the key grid: never for a valid tree
+    return -1;
+}
+
 // Integer tight boxes (grid coordinates recovered from the keys) and the
-// packed records the walk reads.
+// packed records the walk reads: (lo.x | level << 21, lo.y, lo.z, successor
+// of the subtree), (hi.xyz, first child or ~0 for a leaf).
 __global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cnt,
                         const unsigned long long* __restrict__ lvl, int lev,
                         const uint8_t* __restrict__ level, const uint32_t* __restrict__ begin,
-                        const uint32_t* __restrict__ end, const int32_t* __restrict__ first_child,
-                        const uint8_t* __restrict__ nchild, uint32_t* qlo, uint32_t* qhi,
-                        WalkNode* wnode) {
+                        const uint32_t* __restrict__ end, const int32_t* __restrict__ parent,
+                        const int32_t* __restrict__ first_child, const uint8_t* __restrict__ nchild,
+                        uint32_t* qlo, uint32_t* qhi, WalkNode* wnode, int* status) {
     level_range(ls, cnt, lvl, lev);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = ls + t;
@@ -293,40 +313,12 @@ __global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cn
             qhi[3 * k + a] = hi[a];
         }
         WalkNode w;
-        w.a = make_uint4(lo[0], lo[1], lo[2], (uint32_t)level[k] | ((uint32_t)nc << 8));
-        w.b = make_uint4(hi[0], hi[1], hi[2], (uint32_t)first_child[k]);
+        w.a = make_uint4(lo[0] | ((uint32_t)level[k] << kLevels), lo[1], lo[2],
+                         (uint32_t)skip_of(k, parent, first_child, nchild, status));
+        w.b = make_uint4(hi[0], hi[1], hi[2], nc == 0 ? 0xffffffffu : (uint32_t)first_child[k]);
         wnode[k] = w;
     }
 }
-
-// Depth-first successor of node u's subtree: the node a pre-order walk
-// visits after u when it does not descend into u.  Children of a node are
-// consecutive ids, so that is u + 1 unless u is its parent's last child, in
-// which case it is the parent's successor; a root has none (-1), which ends
-// the walk of its patch.
-__device__ __forceinline__ int32_t skip_of(int64_t u, const int32_t* __restrict__ parent,
-                                           const int32_t* __restrict__ first_child,
-                                           const uint8_t* __restrict__ nchild, int* status) {
-    int64_t v = u;
-    for (int up = 0; up <= kLevels + 1; ++up) {
-        const int32_t p = parent[v];
-        if (p < 0) return -1;
-        if (v + 1 < (int64_t)first_child[p] + nchild[p]) return (int32_t)(v + 1);
-        v = p;
-    }
-    atomicOr(status, kStatBounds);  // deeper than the key grid: never for a valid tree
-    return -1;
-}
-
-// nn nodes, or *dnn (device-sized builds; at most nn).
-__global__ void k_skip(int64_t nn, const unsigned long long* __restrict__ dnn, const int32_t* __restrict__ parent,
-                       const int32_t* __restrict__ first_child, const uint8_t* __restrict__ nchild,
-                       int32_t* __restrict__ skip, int* status) {
-    if (dnn) nn = min(nn, (int64_t)*dnn);
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nn; u += (int64_t)gridDim.x * blockDim.x)
-        skip[u] = skip_of(u, parent, first_child, nchild, status);
-}
-
 
 // Moments of the nodes of one level (children already done).
 template <int ORDER>
@@ -639,20 +631,15 @@ int stage_boxes(Ctx* c) {
     BH_TRY(grow(c, c->qlo, (size_t)nn * 3, "node qlo"));
     BH_TRY(grow(c, c->qhi, (size_t)nn * 3, "node qhi"));
     BH_TRY(grow(c, c->wnode, (size_t)nn, "walk records"));
-    BH_TRY(grow(c, c->skip, (size_t)nn, "walk successors"));
     const unsigned long long* lvl = c->dev_build ? c->d_sz + kSzLvl : nullptr;
     const int depth = c->dev_build ? kLevels + 1 : (int)c->lvl_start.size() - 1;
     for (int lev = depth - 1; lev >= 0; --lev) {
         const int64_t ls = lvl ? 0 : c->lvl_start[lev], cnt = lvl ? 0 : c->lvl_start[lev + 1] - ls;
         k_boxes<<<lvl ? dev_level_grid(c, lev, 128) : blocks_for(cnt, 128), 128, 0, c->stream>>>(
-            c->key[c->key_cur].p, ls, cnt, lvl, lev, c->level.p, c->begin.p, c->end.p, c->first_child.p,
-            c->nchild.p, c->qlo.p, c->qhi.p, c->wnode.p);
+            c->key[c->key_cur].p, ls, cnt, lvl, lev, c->level.p, c->begin.p, c->end.p, c->parent.p,
+            c->first_child.p, c->nchild.p, c->qlo.p, c->qhi.p, c->wnode.p, c->d_status);
         BH_LAUNCH(c);
     }
-    k_skip<<<blocks_for(nn, 256), 256, 0, c->stream>>>(nn, lvl ? lvl + kLevels + 2 : nullptr,
-                                                                    c->parent.p, c->first_child.p, c->nchild.p,
-                                                                    c->skip.p, c->d_status);
-    BH_LAUNCH(c);
     return BH_OK;
 }
 

@@ -61,10 +61,11 @@ __device__ __forceinline__ int patch_of(const WalkParams& wp, uint32_t gb) {
 // (axis 0 periodic with the given period in cells when period > 0).
 __device__ __forceinline__ long long box_gap2(const WalkNode& R, const int (&glo)[3], const int (&ghi)[3],
                                               int period) {
-    const int t1 = (int)R.a.x - ghi[0] - 1, t2 = glo[0] - (int)R.b.x - 1;
+    const int lo0 = (int)(R.a.x & kQMax);
+    const int t1 = lo0 - ghi[0] - 1, t2 = glo[0] - (int)R.b.x - 1;
     int d0 = max(0, max(t1, t2));
     if (period > 0 && d0 > 0)  // periodic phi axis: the shorter way round
-        d0 = min(d0, max(0, t1 > 0 ? glo[0] + period - (int)R.b.x - 1 : (int)R.a.x + period - ghi[0] - 1));
+        d0 = min(d0, max(0, t1 > 0 ? glo[0] + period - (int)R.b.x - 1 : lo0 + period - ghi[0] - 1));
     const int d1 = max(0, max((int)R.a.y - ghi[1] - 1, glo[1] - (int)R.b.y - 1));
     const int d2 = max(0, max((int)R.a.z - ghi[2] - 1, glo[2] - (int)R.b.z - 1));
     return (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2 * d2;
@@ -117,7 +118,6 @@ template <int MODE>
 __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long long* __restrict__ dng,
                                               int64_t slots, const int32_t* __restrict__ groups,
                                               const WalkNode* __restrict__ wn,
-                                              const int32_t* __restrict__ skip,
                                               const uint32_t* __restrict__ begin,
                                               const uint32_t* __restrict__ end, WalkParams wp,
                                               int64_t* __restrict__ np_io, int64_t* __restrict__ nc_io,
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long lo
             const int32_t g = groups[k];
             const WalkNode G = wn[g];
             const uint32_t gb = begin[g], ge = end[g];
-            const int glo[3] = {(int)G.a.x, (int)G.a.y, (int)G.a.z};
+            const int glo[3] = {(int)(G.a.x & kQMax), (int)G.a.y, (int)G.a.z};
             const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
             ni = (int64_t)(end[g] - begin[g]);
             ListOut po{P, 0, 0, INT64_MAX, 0, 0, 0, 0}, co{C, 0, 0, INT64_MAX, 0, 0, 0, 0};
@@ -159,13 +159,14 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long lo
             int node = root;
             for (int64_t visits = 0;; ++visits) {
                 const WalkNode R = wn[node];
-                const int after = skip[node];
-                const int lev = (int)(R.a.w & 0xffu), nch = (int)(R.a.w >> 8);
+                const int after = (int)R.a.w;
+                const int lev = (int)(R.a.x >> kLevels);
+                const bool leaf = (int)R.b.w < 0;
                 const long long d2 = box_gap2(R, glo, ghi, period);
                 const bool open = d2 < wp.D[lev] || d2 <= rcq;
                 int next = after;
                 if (open) {
-                    if (nch == 0) {
+                    if (leaf) {
                         if (WRITE) po.put(node);
                         ++np;
                         const uint32_t lb = begin[node];
@@ -243,7 +244,7 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
         int period = 0;
         if (SPLIT) {
             const WalkNode G = wn[g];
-            glo[0] = (int)G.a.x; glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
+            glo[0] = (int)(G.a.x & kQMax); glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
             ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
             const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
             ext2 = ext * ext;
@@ -462,11 +463,11 @@ int stage_lists(Ctx* c) {
     const unsigned nb = blocks_for(ng, 128);
     if (stash)
         k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(
-            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
             c->cnt_j.p, c->stash_p.p, c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest, overflow);
     else
         k_walk<kWalkCount><<<nb, 128, 0, c->stream>>>(
-            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
             c->cnt_j.p, nullptr, nullptr, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
     BH_LAUNCH(c);
     DBuf<int64_t>* arr[3] = {&c->cnt_p, &c->cnt_c, &c->cnt_j};
@@ -504,7 +505,7 @@ int stage_lists(Ctx* c) {
         ++c->n_one_walk_builds;
     } else {
         k_walk<kWalkFill><<<nb, 128, 0, c->stream>>>(
-            ng, nullptr, -1, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+            ng, nullptr, -1, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
             c->cnt_j.p, c->P.p, c->C.p, inter, c->n_nodes, c->d_status, 0, 0, longest, overflow);
     }
     BH_LAUNCH(c);
@@ -545,7 +546,7 @@ int stage_lists_dev_walk(Ctx* c) {
     BH_TRY(grow(c, c->stash_c, (size_t)std::max<int64_t>(1, slots * capC), "stashed cell lists"));
     BH_CUDA(c, cudaMemsetAsync(inter, 0, 6 * sizeof(unsigned long long), c->stream));  // words 8..13
     const unsigned nb = blocks_for(std::max<int64_t>(slots, 1), 128);
-    k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(ng, dng, slots, c->groups.p, c->wnode.p, c->skip.p, c->begin.p,
+    k_walk<kWalkStash><<<nb, 128, 0, c->stream>>>(ng, dng, slots, c->groups.p, c->wnode.p, c->begin.p,
                                                   c->end.p, wp, c->cnt_p.p, c->cnt_c.p, c->cnt_j.p, c->stash_p.p,
                                                   c->stash_c.p, inter, c->n_nodes, c->d_status, capP, capC, longest,
                                                   overflow);
@@ -575,7 +576,7 @@ int stage_lists_dev_fill(Ctx* c) {
                                            capC, c->P.p, c->C.p);
     BH_LAUNCH(c);
     k_walk<kWalkFill><<<blocks_for(std::max<int64_t>(slots, 1), 128), 128, 0, c->stream>>>(
-        ng, dng, slots, c->groups.p, c->wnode.p, c->skip.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
+        ng, dng, slots, c->groups.p, c->wnode.p, c->begin.p, c->end.p, wp, c->cnt_p.p, c->cnt_c.p,
         c->cnt_j.p, c->P.p, c->C.p, c->d_small + 8, c->n_nodes, c->d_status, capP, capC, c->d_small + 12,
         c->d_small + 11);
     BH_LAUNCH(c);
