@@ -53,12 +53,16 @@ int grow(Ctx* c, DBuf<T>& b, size_t n, const char* what, bool keep = false) {
     return rc;
 }
 
-// Per-node packed record read by the walk: (qlo.x | level << 21, qlo.y,
-// qlo.z, successor of the subtree or -1), (qhi.xyz, first child or ~0 for a
-// leaf).
+// Per-node packed record read by the walk (one 32-byte load per visit):
+// a = (qlo.x | level << 21 | leaf flag, qlo.y | leaf count << 21, qlo.z,
+// successor of the subtree or -1), b = (qhi.xyz, first child, or for a leaf
+// its first particle).  A leaf count of kWalkCntMax means "that many or
+// more": the walk then reads the node's end.
 struct WalkNode {
     uint4 a, b;
 };
+constexpr uint32_t kWalkLeaf = 1u << 26;
+constexpr uint32_t kWalkCntMax = (1u << 11) - 1;
 
 // Launch tuning of the FP32 force kernel (bh_set_tuning / the autotuner).
 struct Tuning {

@@ -275,8 +275,7 @@ __device__ __forceinline__ int32_t skip_of(int64_t u, const int32_t* __restrict_
 }
 
 // Integer tight boxes (grid coordinates recovered from the keys) and the
-// packed records the walk reads: (lo.x | level << 21, lo.y, lo.z, successor
-// of the subtree), (hi.xyz, first child or ~0 for a leaf).
+// packed records the walk reads (WalkNode).
 __global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cnt,
                         const unsigned long long* __restrict__ lvl, int lev,
                         const uint8_t* __restrict__ level, const uint32_t* __restrict__ begin,
@@ -313,9 +312,13 @@ __global__ void k_boxes(const uint64_t* __restrict__ key, int64_t ls, int64_t cn
             qhi[3 * k + a] = hi[a];
         }
         WalkNode w;
-        w.a = make_uint4(lo[0] | ((uint32_t)level[k] << kLevels), lo[1], lo[2],
+        // a leaf carries its first particle and (up to kWalkCntMax - 1) its
+        // particle count instead of a first child
+        const uint32_t leafcnt = nc == 0 ? min(end[k] - begin[k], kWalkCntMax) : 0u;
+        w.a = make_uint4(lo[0] | ((uint32_t)level[k] << kLevels) | (nc == 0 ? kWalkLeaf : 0u),
+                         lo[1] | (leafcnt << kLevels), lo[2],
                          (uint32_t)skip_of(k, parent, first_child, nchild, status));
-        w.b = make_uint4(hi[0], hi[1], hi[2], nc == 0 ? 0xffffffffu : (uint32_t)first_child[k]);
+        w.b = make_uint4(hi[0], hi[1], hi[2], nc == 0 ? begin[k] : (uint32_t)first_child[k]);
         wnode[k] = w;
     }
 }

@@ -66,7 +66,8 @@ __device__ __forceinline__ long long box_gap2(const WalkNode& R, const int (&glo
     int d0 = max(0, max(t1, t2));
     if (period > 0 && d0 > 0)  // periodic phi axis: the shorter way round
         d0 = min(d0, max(0, t1 > 0 ? glo[0] + period - (int)R.b.x - 1 : lo0 + period - ghi[0] - 1));
-    const int d1 = max(0, max((int)R.a.y - ghi[1] - 1, glo[1] - (int)R.b.y - 1));
+    const int lo1 = (int)(R.a.y & kQMax);
+    const int d1 = max(0, max(lo1 - ghi[1] - 1, glo[1] - (int)R.b.y - 1));
     const int d2 = max(0, max((int)R.a.z - ghi[2] - 1, glo[2] - (int)R.b.z - 1));
     return (long long)d0 * d0 + (long long)d1 * d1 + (long long)d2 * d2;
 }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long lo
             const int32_t g = groups[k];
             const WalkNode G = wn[g];
             const uint32_t gb = begin[g], ge = end[g];
-            const int glo[3] = {(int)(G.a.x & kQMax), (int)G.a.y, (int)G.a.z};
+            const int glo[3] = {(int)(G.a.x & kQMax), (int)(G.a.y & kQMax), (int)G.a.z};
             const int ghi[3] = {(int)G.b.x, (int)G.b.y, (int)G.b.z};
             ni = (int64_t)(end[g] - begin[g]);
             ListOut po{P, 0, 0, INT64_MAX, 0, 0, 0, 0}, co{C, 0, 0, INT64_MAX, 0, 0, 0, 0};
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long lo
             for (int64_t visits = 0;; ++visits) {
                 const WalkNode R = wn[node];
                 const int after = (int)R.a.w;
-                const int lev = (int)(R.a.x >> kLevels);
-                const bool leaf = (int)R.b.w < 0;
+                const int lev = (int)((R.a.x >> kLevels) & 31u);
+                const bool leaf = (R.a.x & kWalkLeaf) != 0;
                 const long long d2 = box_gap2(R, glo, ghi, period);
                 const bool open = d2 < wp.D[lev] || d2 <= rcq;
                 int next = after;
@@ -169,11 +170,13 @@ __global__ void __launch_bounds__(128) k_walk(int64_t ng, const unsigned long lo
                     if (leaf) {
                         if (WRITE) po.put(node);
                         ++np;
-                        const uint32_t lb = begin[node];
+                        const uint32_t lb = R.b.w;
+                        uint32_t lc = R.a.y >> kLevels;
+                        if (lc == kWalkCntMax) lc = end[node] - lb;
                         if (lb >= gb && lb < ge)
-                            nown += (int64_t)(end[node] - lb);  // the group's own particles
+                            nown += (int64_t)lc;  // the group's own particles
                         else
-                            nj += (int64_t)(end[node] - lb);
+                            nj += (int64_t)lc;
                     } else {
                         next = (int)R.b.w;
                     }
@@ -244,7 +247,7 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
         int period = 0;
         if (SPLIT) {
             const WalkNode G = wn[g];
-            glo[0] = (int)(G.a.x & kQMax); glo[1] = (int)G.a.y; glo[2] = (int)G.a.z;
+            glo[0] = (int)(G.a.x & kQMax); glo[1] = (int)(G.a.y & kQMax); glo[2] = (int)G.a.z;
             ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
             const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
             ext2 = ext * ext;
@@ -252,31 +255,32 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
             rfar = wp.rfar[root];
             period = (int)wp.period[root];
         }
-        // leaf entry e -> (first particle, count); far? by the box test, or from
-        // the first pass's flags (bit c = the lane's entry of round c < 32)
-        auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt) {
+        // leaf entry e -> (first particle, count; 0 for the group's own
+        // leaves) from its walk record, and whether it is far
+        auto entry = [&](int64_t e, uint32_t& b, uint32_t& cnt, bool& far) {
             b = 0;
             cnt = 0;
+            far = false;
             if (e < e1) {
                 const int32_t leaf = P[e];
-                b = begin[leaf];
-                cnt = (b >= gb && b < ge) ? 0u : end[leaf] - b;
+                const WalkNode R = wn[leaf];
+                b = R.b.w;
+                cnt = R.a.y >> kLevels;
+                if (cnt == kWalkCntMax) cnt = end[leaf] - b;
+                if (b >= gb && b < ge) cnt = 0;
+                if (SPLIT && cnt > 0) {
+                    const long long d2 = box_gap2(R, glo, ghi, period);
+                    far = d2 > rfar && 16 * d2 >= ext2;
+                }
             }
         };
-        auto far_of = [&](int64_t e) -> bool {
-            const long long d2 = box_gap2(wn[P[e]], glo, ghi, period);
-            return d2 > rfar && 16 * d2 >= ext2;
-        };
         int64_t jn = jj_off[k], jf = jn;
-        uint32_t flags = 0;
         if (SPLIT) {  // far run starts after every near particle
             uint32_t near = 0;
-            int c = 0;
-            for (int64_t e = e0 + lane; e < e1; e += 32, ++c) {
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
                 uint32_t b, cnt;
-                entry(e, b, cnt);
-                const bool far = cnt > 0 && far_of(e);
-                if (far && c < 32) flags |= 1u << c;
+                bool far;
+                entry(e, b, cnt, far);
                 near += far ? 0u : cnt;
             }
 #pragma unroll
@@ -288,10 +292,10 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
                 atomicAdd(n_far, ni * (unsigned long long)(jj_off[k + 1] - jf));
             }
         }
-        for (int64_t e = e0, c = 0; e < e1; e += 32, ++c) {
+        for (int64_t e = e0; e < e1; e += 32) {
             uint32_t b, cnt;
-            entry(e + lane, b, cnt);
-            const bool far = SPLIT && cnt > 0 && (c < 32 ? ((flags >> c) & 1u) != 0 : far_of(e + lane));
+            bool far;
+            entry(e + lane, b, cnt, far);
             const uint32_t cn = far ? 0u : cnt, cf = far ? cnt : 0u;
             uint32_t xn = cn, xf = cf;
 #pragma unroll
