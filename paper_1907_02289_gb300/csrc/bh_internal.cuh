@@ -136,7 +136,7 @@ struct Ctx {
     DBuf<uint32_t> digit_hist; // 8 x 256 global digit counts
     DBuf<double> pscratch;     // permutation scratch (8 bytes per particle)
     DBuf<double> cyl;          // cylindrical frame: phi[n], r[n]
-    DBuf<double> box_part;     // root-box partials (6 per block)
+    DBuf<unsigned long long> box_part;  // root-box partials (6 per block, as ordered integers)
     DBuf<uint8_t> scan_tmp;
 
     // tree

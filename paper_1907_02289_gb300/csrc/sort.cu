@@ -15,11 +15,23 @@ namespace {
 
 constexpr int kBoxThreads = 256;
 
-__device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
+// Order-preserving map of a finite double's bits to an unsigned integer
+// (negative values: all bits flipped; others: the sign bit set), so that the
+// box's min/max are integer comparisons (the FP64 ones run at 1/64 of the
+// FP32 rate here).  -0 orders below +0; the value selected is exact either way.
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double val_of(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+__device__ __forceinline__ void warp_minmax(unsigned long long& mn, unsigned long long& mx) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
 }
 
@@ -32,9 +44,9 @@ __device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
 __global__ void k_box_partial(const double* __restrict__ x, const double* __restrict__ y,
                               const double* __restrict__ z, const int64_t* __restrict__ off,
                               const uint2* __restrict__ map, const int* __restrict__ poff,
-                              double* __restrict__ part, int* status) {
-    __shared__ double s[6][kBoxThreads / 32];
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+                              unsigned long long* __restrict__ part, int* status) {
+    __shared__ unsigned long long s[6][kBoxThreads / 32];
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
     bool bad = false;
     int q, j, nbq;
     int64_t slot;
@@ -52,12 +64,14 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
     }
     const int64_t e = off[q + 1];
     for (int64_t i = off[q] + (int64_t)j * blockDim.x + threadIdx.x; i < e; i += (int64_t)nbq * blockDim.x) {
-        double v[3] = {x[i], y[i], z[i]};
+        const double v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            bad |= !isfinite(v[a]);
-            mn[a] = fmin(mn[a], v[a]);
-            mx[a] = fmax(mx[a], v[a]);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v[a]);
+            bad |= ((b >> 52) & 0x7ffu) == 0x7ffu;  // infinity or NaN
+            const unsigned long long k = ord_of(v[a]);
+            mn[a] = min(mn[a], k);
+            mx[a] = max(mx[a], k);
         }
     }
     if (bad) atomicOr(status, kStatNonFinite);
@@ -72,10 +86,10 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
     }
     __syncthreads();
     if (threadIdx.x < 6) {
-        double r = s[threadIdx.x][0];
+        unsigned long long r = s[threadIdx.x][0];
         for (int k = 1; k < kBoxThreads / 32; ++k)
-            r = threadIdx.x < 3 ? fmin(r, s[threadIdx.x][k]) : fmax(r, s[threadIdx.x][k]);
-        part[6 * slot + threadIdx.x] = r;
+            r = threadIdx.x < 3 ? min(r, s[threadIdx.x][k]) : max(r, s[threadIdx.x][k]);
+        part[6 * slot + threadIdx.x] = r;  // (as the ordered integer; a block with no particle keeps the identity)
     }
 }
 
@@ -83,17 +97,17 @@ __global__ void k_box_partial(const double* __restrict__ x, const double* __rest
 // blocks poff[q] .. poff[q + 1] - 1): {lo_x, lo_y, lo_z, L, S} at box + 8 q.
 // Cylindrical frame (cyl): every particle must be off the axis (r > 0), else
 // kStatAxis.
-__global__ void k_box_final(const double* __restrict__ part_all, int nb, const int* __restrict__ poff,
+__global__ void k_box_final(const unsigned long long* __restrict__ part_all, int nb, const int* __restrict__ poff,
                             double* box_all, int cyl, int* status) {
-    const double* part = part_all + 6 * (poff ? (int64_t)poff[blockIdx.x] : (int64_t)blockIdx.x * nb);
+    const unsigned long long* part = part_all + 6 * (poff ? (int64_t)poff[blockIdx.x] : (int64_t)blockIdx.x * nb);
     if (poff) nb = poff[blockIdx.x + 1] - poff[blockIdx.x];
     double* box = box_all + 8 * blockIdx.x;
     __shared__ double r[6];
     if (threadIdx.x < 6) {
-        double v = part[threadIdx.x];
+        unsigned long long v = part[threadIdx.x];
         for (int b = 1; b < nb; ++b)
-            v = threadIdx.x < 3 ? fmin(v, part[6 * b + threadIdx.x]) : fmax(v, part[6 * b + threadIdx.x]);
-        r[threadIdx.x] = v;
+            v = threadIdx.x < 3 ? min(v, part[6 * b + threadIdx.x]) : max(v, part[6 * b + threadIdx.x]);
+        r[threadIdx.x] = val_of(v);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -165,11 +179,15 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
     return x;
 }
 
+// min(max(floor((v - lo) * S), 0), 2^21 - 1) with one FP64 subtraction, one
+// product and one truncating conversion (truncation = floor for t >= 0); the
+// clamps read the sign and the exponent of t.
 __device__ __forceinline__ uint32_t quantise(double v, double lo, double S) {
-    double t = floor(__dmul_rn(__dsub_rn(v, lo), S));
-    t = fmax(t, 0.0);
-    t = fmin(t, (double)kQMax);
-    return (uint32_t)t;
+    const double t = __dmul_rn(__dsub_rn(v, lo), S);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    if (b >> 63) return 0u;                                         // t < 0 (or -0)
+    if (((b >> 52) & 0x7ffu) >= 1023u + kLevels) return kQMax;      // t >= 2^21 (infinities and NaN too)
+    return min(__double2uint_rz(t), kQMax);
 }
 
 // Keys of every particle on its patch's grid (patch by binary search of the
