@@ -412,7 +412,7 @@ int64_t orc_groups(int64_t n_nodes, const uint32_t* begin, const uint32_t* end,
     for (int64_t k = 0; k < n_nodes; ++k) {
         int64_t cnt = (int64_t)end[k] - begin[k];
         int small = (cnt <= n_g) || (nchild[k] == 0);
-        int top = (k == 0) || ((int64_t)end[parent[k]] - begin[parent[k]] > n_g);
+        int top = (parent[k] < 0) || ((int64_t)end[parent[k]] - begin[parent[k]] > n_g);  /* a root */
         if (small && top) groups[ng++] = (int32_t)k;
     }
     orc_grp_begin = begin;

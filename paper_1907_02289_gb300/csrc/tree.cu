@@ -523,11 +523,9 @@ __global__ void k_group_mark(int64_t nn, const unsigned long long* __restrict__ 
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cnt = end[k] - begin[k];
         const bool small = cnt <= (uint32_t)n_g || nchild[k] == 0;
-        bool top = (k == 0);
-        if (!top) {
-            const int32_t p = parent[k];
-            top = (end[p] - begin[p]) > (uint32_t)n_g;
-        }
+        // a root (of any patch: parent -1) or the child of a node above n_g
+        const int32_t p = parent[k];
+        const bool top = p < 0 || (end[p] - begin[p]) > (uint32_t)n_g;
         if (small && top) gmark[begin[k]] = (int32_t)k;
     }
 }
