@@ -134,7 +134,7 @@ struct Ctx {
     int key_cur = 0;           // buffer holding the sorted keys / perm
     DBuf<uint32_t> sort_hist;
     DBuf<uint32_t> digit_hist; // 8 x 256 global digit counts
-    DBuf<double> pscratch;     // permutation scratch (8 bytes per particle)
+    DBuf<double> pscratch;     // permutation scratch (8 arrays x 8 bytes per particle)
     DBuf<double> cyl;          // cylindrical frame: phi[n], r[n]
     DBuf<unsigned long long> box_part;  // root-box partials (6 per block, as ordered integers)
     DBuf<uint8_t> scan_tmp;

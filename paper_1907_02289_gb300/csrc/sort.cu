@@ -381,15 +381,30 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(
     }
 }
 
-__global__ void k_gather8(const unsigned long long* __restrict__ src, unsigned long long* __restrict__ dst,
-                          const uint32_t* __restrict__ perm, int64_t n, int* status) {
+// All particle arrays (8-byte elements) gathered into key order in one pass:
+// the permutation is read once and every array's load is in flight at once;
+// dst[a] = scratch + a n (copied back by the caller).
+struct Gather8 {
+    const unsigned long long* src[8];
+    int na;
+};
+
+__global__ void k_gather_all(Gather8 G, unsigned long long* __restrict__ scratch, const uint32_t* __restrict__ perm,
+                             int64_t n, int* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t j = perm[i];
-    if (j < n)
-        dst[i] = src[j];
-    else
+    if (j >= n) {
         atomicOr(status, kStatBounds);
+        return;
+    }
+    unsigned long long v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+        if (a < G.na) v[a] = G.src[a][j];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+        if (a < G.na) scratch[(int64_t)a * n + i] = v[a];
 }
 
 }  // namespace
@@ -483,19 +498,26 @@ int stage_sort(Ctx* c) {
 
 int stage_permute(Ctx* c, bh_particles* p) {
     const int64_t n = c->n;
-    BH_TRY(grow(c, c->pscratch, (size_t)n, "particle scratch"));
+    BH_TRY(grow(c, c->pscratch, 8 * (size_t)n, "particle scratch"));
     unsigned long long* arrs[8] = {(unsigned long long*)p->x,  (unsigned long long*)p->y,
                                    (unsigned long long*)p->z,  (unsigned long long*)p->vx,
                                    (unsigned long long*)p->vy, (unsigned long long*)p->vz,
                                    (unsigned long long*)p->m,  (unsigned long long*)p->id};
     const uint32_t* perm = c->idx[c->key_cur].p;
-    for (int a = 0; a < 8; ++a) {
-        if (!arrs[a]) continue;
-        k_gather8<<<blocks_for(n, 256), 256, 0, c->stream>>>(arrs[a], (unsigned long long*)c->pscratch.p, perm, n,
-                                                                c->d_status);
-        BH_LAUNCH(c);
-        BH_CUDA(c, cudaMemcpyAsync(arrs[a], c->pscratch.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    }
+    Gather8 G;
+    unsigned long long* dst[8];
+    G.na = 0;
+    for (int a = 0; a < 8; ++a)
+        if (arrs[a]) {
+            dst[G.na] = arrs[a];
+            G.src[G.na++] = arrs[a];
+        }
+    unsigned long long* scratch = (unsigned long long*)c->pscratch.p;
+    k_gather_all<<<blocks_for(n, 256), 256, 0, c->stream>>>(G, scratch, perm, n, c->d_status);
+    BH_LAUNCH(c);
+    for (int a = 0; a < G.na; ++a)
+        BH_CUDA(c, cudaMemcpyAsync(dst[a], scratch + (int64_t)a * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   c->stream));
     return BH_OK;
 }
 

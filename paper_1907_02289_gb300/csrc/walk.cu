@@ -329,8 +329,24 @@ __global__ void k_unstash(int64_t ng, const unsigned long long* __restrict__ dng
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < ng; k += wstride) {
         const int64_t p0 = pp_off[k], np = pp_off[k + 1] - p0, c0 = pc_off[k], nc = pc_off[k + 1] - c0;
         if (slots >= 0 && !(k < slots && np <= capP && nc <= capC)) continue;
-        for (int64_t t = lane; t < np; t += 32) P[p0 + t] = sP[k * capP + t];
-        for (int64_t t = lane; t < nc; t += 32) C[c0 + t] = sC[k * capC + t];
+        // four loads in flight per lane
+        auto copy = [&](int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t cnt) {
+            for (int64_t t0 = 0; t0 < cnt; t0 += 128) {
+                int32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t t = t0 + 32 * u + lane;
+                    v[u] = t < cnt ? src[t] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t t = t0 + 32 * u + lane;
+                    if (t < cnt) dst[t] = v[u];
+                }
+            }
+        };
+        copy(P + p0, sP + k * capP, np);
+        copy(C + c0, sC + k * capC, nc);
     }
 }
 
