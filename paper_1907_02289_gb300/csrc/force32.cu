@@ -10,11 +10,11 @@
 // (x_hi,j - x_hi,i) + (x_lo,j - x_lo,i): exact to an FP32 rounding of the
 // separation itself, however wide the group is.  List cells, which the
 // opening test keeps at least a cell size away, use the hi part alone, and
-// so do "far" list particles (beyond contact reach and at least a quarter of
-// the group's largest side away; the list expansion puts them after the
-// near ones): their separation is the difference of the two rounded FP32
-// coordinates, as in Sec. 4.7, correct to a few FP32 roundings of itself
-// at that distance, and they need no contact test.
+// so do "far" list particles (beyond contact reach of every particle of the
+// group; the list expansion puts them after the near ones): their separation
+// is the difference of the two rounded FP32 coordinates, as in Sec. 4.7,
+// off by a few roundings of coordinates of the size of the group's extent,
+// and they need no contact test.
 //
 // Gravity inside r_coll (Eq. 1) is G m_j r / (r_coll^2 + eps^2)^(3/2), so
 // max(r^2, r_coll^2) + eps^2 in the fast loop gives it for every pair (and
@@ -125,7 +125,6 @@ struct Smem32 {
         float4 c[kTileC][3];
     } raw;
     uint32_t raw_id[kTileJ];
-    uint8_t trig[kTileJ / 2];  // list pairs of the current tile with a contact candidate
     uint32_t q_i[kQueueCap];   // contact candidates (i, j) waiting for the global list
     uint32_t q_j[kQueueCap];
     float2 acc[32 * kSlots][3];  // compensated sums (G-free): (hi, lo), one 8-byte access each
@@ -493,13 +492,15 @@ __device__ __forceinline__ void put_cell(Smem32& S, int u, bool real, const floa
 }
 
 // ---- tile loops --------------------------------------------------------------
-// The hot loops note (warp-uniformly) which list pairs had a contact
-// candidate; the candidates are queued after the loop.
+// The hot loops note, per lane and without branching, which list pairs of
+// the tile had a contact candidate (bit q of a mask); one reduction over the
+// warp after the loop gives the pairs whose candidates are queued.
+static_assert(kTileJ / 2 <= 32, "one mask bit per list pair of a tile");
 template <int MODE, int R, bool TAIL, bool SELF>
 __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>& K, int npair, int J, int tj,
                                         int& qn, int lane) {
     if constexpr (R > 0) {
-        int ntrig = 0;
+        uint32_t hit = 0;
 #pragma unroll kUnrollPP
         for (int q = 0; q < npair; ++q) {
             const JPair P = S.t.p.jp[q];
@@ -507,16 +508,14 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
             bool any = false;
 #pragma unroll
             for (int r = 0; r < R; ++r) any |= pp_body<MODE, SELF>(A, P, jid, K.iv[r], K.nh[r], K.nl[r], K.g[r]);
-            if (has_contact(MODE) && __any_sync(0xffffffffu, any)) {
-                if (lane == 0) S.trig[ntrig] = (uint8_t)q;
-                ++ntrig;
-            }
+            if (has_contact(MODE)) hit |= (uint32_t)any << q;
         }
         if (has_contact(MODE)) {
-            __syncwarp();
+            uint32_t all = __reduce_or_sync(0xffffffffu, hit);
 #pragma unroll 1
-            for (int t = 0; t < ntrig; ++t) {
-                const int q = S.trig[t];
+            while (all) {
+                const int q = __ffs(all) - 1;
+                all &= all - 1u;
                 queue_pair<SELF, R, TAIL>(A, S, qn, S.t.p.jp[q], &S.t.p.jid[2 * q], K, 0, R, false, lane);
                 if (qn >= 32) flush_queue(A, S, qn, lane);
             }
@@ -524,23 +523,22 @@ __device__ __forceinline__ void pp_tile(const Args& A, Smem32& S, Chunk<R, TAIL>
     }
     if constexpr (TAIL) {
         const int trips = (npair + J - 1) / J;
-        int ntrig = 0;
+        uint32_t hit = 0;
 #pragma unroll 1
         for (int u = 0; u < trips; ++u) {
             const int q = u * J + tj;
             bool any = false;
             if (q < npair)
                 any = pp_body<MODE, SELF>(A, S.t.p.jp[q], &S.t.p.jid[2 * q], K.iv[R], K.nh[R], K.nl[R], K.g[R]);
-            if (has_contact(MODE) && __any_sync(0xffffffffu, any)) {
-                if (lane == 0) S.trig[ntrig] = (uint8_t)u;
-                ++ntrig;
-            }
+            if (has_contact(MODE)) hit |= (uint32_t)any << u;
         }
         if (has_contact(MODE)) {
-            __syncwarp();
+            uint32_t all = __reduce_or_sync(0xffffffffu, hit);
 #pragma unroll 1
-            for (int t = 0; t < ntrig; ++t) {
-                const int q = S.trig[t] * J + tj;
+            while (all) {
+                const int u = __ffs(all) - 1;
+                all &= all - 1u;
+                const int q = u * J + tj;
                 const bool ok = q < npair;
                 queue_pair<SELF, R, TAIL>(A, S, qn, S.t.p.jp[ok ? q : 0], &S.t.p.jid[ok ? 2 * q : 0], K, R, R + 1, ok,
                                           lane);
