@@ -158,9 +158,10 @@ typedef struct {
     int64_t n_launches; /* CUDA kernels launched by this context                  */
     int64_t n_contacts; /* contact candidates of the last FP32 force evaluation   */
     int64_t n_pp_far;   /* FP32 path: the part of n_pp whose list particle is "far"
-                         * (beyond contact reach of the group's box), evaluated
-                         * with a single FP32 separation relative to the group
-                         * origin; 0 on the FP64 path                          */
+                         * (beyond contact reach and at least an eighth of the
+                         * group's largest side away), evaluated with a single
+                         * FP32 separation relative to the group origin; 0 on
+                         * the FP64 path                                       */
     int64_t n_one_walk_builds; /* list builds whose lists came from a single tree
                          * walk into per-group slots (sized from the previous
                          * build's longest lists) instead of a count walk and a

@@ -21,12 +21,11 @@
 //
 // For the FP32 kernel the expansion puts a group's list particles in two
 // runs: "near" leaves first, then "far" leaves, far meaning beyond contact
-// reach with a margin (so no pair in them can touch).  The kernel forms far
-// separations from single FP32 coordinates relative to the group origin (the
-// arithmetic of Sec. 4.7) and skips the contact test for them; such a
-// separation is off by a few roundings of coordinates no larger than the
-// group's and the leaf's extent plus their gap, which the gap of at least a
-// contact reach keeps small against the separation itself.
+// reach with a margin (so no pair in them can touch) and a gap of at least an
+// eighth of the group's largest side.  The kernel forms far separations from
+// single FP32 coordinates relative to the group origin (the arithmetic of
+// Sec. 4.7), whose error relative to the separation is then bounded by a
+// few FP32 roundings, and skips the contact test for them.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -244,12 +243,14 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
         const uint32_t gb = begin[g], ge = end[g];
         const int64_t e0 = pp_off[k], e1 = pp_off[k + 1];
         int glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
-        long long rfar = 0;
+        long long rfar = 0, ext2 = 0;
         int period = 0;
         if (SPLIT) {
             const WalkNode G = wn[g];
             glo[0] = (int)(G.a.x & kQMax); glo[1] = (int)(G.a.y & kQMax); glo[2] = (int)G.a.z;
             ghi[0] = (int)G.b.x; ghi[1] = (int)G.b.y; ghi[2] = (int)G.b.z;
+            const long long ext = max(ghi[0] - glo[0], max(ghi[1] - glo[1], ghi[2] - glo[2])) + 1;
+            ext2 = ext * ext;
             const int root = patch_of(wp, gb);
             rfar = wp.rfar[root];
             period = (int)wp.period[root];
@@ -269,7 +270,7 @@ __global__ void k_expand(int64_t ng, const unsigned long long* __restrict__ dng,
                 if (b >= gb && b < ge) cnt = 0;
                 if (SPLIT && cnt > 0) {
                     const long long d2 = box_gap2(R, glo, ghi, period);
-                    far = d2 > rfar;
+                    far = d2 > rfar && 64 * d2 >= ext2;
                 }
             }
         };

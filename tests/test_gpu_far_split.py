@@ -7,7 +7,8 @@ oracle in the parity tests):
 * the count of far interactions the library reports equals the one
   recomputed on the host from the stated rule: a leaf is far for a group
   when its squared whole-cell gap d2 to the group box exceeds the widened
-  contact reach ((a (1 + 1e-5) + 2)^2, a the contact reach in cells);
+  contact reach ((a (1 + 1e-5) + 2)^2, a the contact reach in cells) and
+  64 d2 >= (largest group side in cells)^2;
 * no pair closer than r_coll ever has its j in a leaf that is far for i's
   group (brute force over all close pairs), also across the phi seam of a
   whole ring in the cylindrical frame;
@@ -94,8 +95,9 @@ def _far_leaves(ctx, prm):
     for k, g in enumerate(grp):
         lv = lst["P"][lst["pp_off"][k]:lst["pp_off"][k + 1]]
         lv = lv[~((b[lv] >= b[g]) & (b[lv] < e[g]))]
+        ext = int((qhi[g] - qlo[g]).max()) + 1
         d2 = _gap2(qlo[lv], qhi[lv], qlo[g], qhi[g], period)
-        far = d2 > rfar
+        far = (d2 > rfar) & (64 * d2 >= ext * ext)
         n_far += int(e[g] - b[g]) * int((e[lv[far]] - b[lv[far]]).sum())
         out.append((lv, far))
     return t, grp, out, n_far
@@ -137,9 +139,9 @@ def test_far_count_and_close_pairs(frame):
     t, grp, leaves, n_far = _far_leaves(ctx, prm)
     c = ctx.bh_get_counters()
     assert c["n_pp_far"] == n_far
-    # most list particles are beyond contact reach; the near ones include
-    # every particle that can touch one of the group's
-    assert 0.2 * c["n_pp"] < n_far < c["n_pp"]
+    # groups of the thin whole ring are long in phi, so few leaves clear an
+    # eighth of their largest side; the sector has many far leaves
+    assert (0.2 if frame == 0 else 0.0) * c["n_pp"] < n_far < c["n_pp"]
     _check_no_close_pair_is_far(D, prm, t, grp, leaves)
 
 
