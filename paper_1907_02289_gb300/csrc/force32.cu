@@ -13,8 +13,8 @@
 // so do "far" list particles (beyond contact reach and at least an eighth of
 // the group's largest side away; the list expansion puts them after the
 // near ones): their separation is the difference of the two rounded FP32
-// coordinates, as in Sec. 4.7, correct to a few FP32 roundings of itself
-// at that distance, and they need no contact test.
+// coordinates, as in Sec. 4.7, correct to about 30 FP32 unit roundings of
+// itself at most at that distance, and they need no contact test.
 //
 // Gravity inside r_coll (Eq. 1) is G m_j r / (r_coll^2 + eps^2)^(3/2), so
 // max(r^2, r_coll^2) + eps^2 in the fast loop gives it for every pair (and

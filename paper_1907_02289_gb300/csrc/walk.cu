@@ -24,8 +24,10 @@
 // reach with a margin (so no pair in them can touch) and a gap of at least an
 // eighth of the group's largest side.  The kernel forms far separations from
 // single FP32 coordinates relative to the group origin (the arithmetic of
-// Sec. 4.7), whose error relative to the separation is then bounded by a
-// few FP32 roundings, and skips the contact test for them.
+// Sec. 4.7), whose error relative to the separation s is then at most about
+// 2 u (1 + E / s) (E the group's extent from its centre, at most sqrt(3)
+// times its side; u = 2^-24), i.e. 2 u (1 + 8 sqrt(3)) ~ 30 u, and skips the
+// contact test for them.
 #include <algorithm>
 #include <cmath>
 #include <vector>
